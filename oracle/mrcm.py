@@ -1,0 +1,255 @@
+"""MRCM-OS as a preconditioner T (Sec. 2.1 and Sec. 3).
+
+Set-up (MRCM-OS steps 1-3, with the preconditioner's homogeneous boundary conditions):
+
+1. Informed multiplier spaces (Eq. 15, definition of phi_i^k):
+   for every Robin side k of the oversampled region hat-Omega_s solve the homogeneous Robin problem
+   with Robin data lambda^k = 1 on the faces of side k and 0 elsewhere.  On each face f of Gamma_s
+   (inside cell c in Omega_s, outside cell c' in hat-Omega_s) take the discrete normal flux
+   F = T_f (q_c - q_c'), the velocity u = F/|f|, the face pressure pi = q_c - F/tau_c and
+   phi_s^k(f) = -beta_f u + pi.  With l = 0 the faces of Gamma_s lie on the Robin boundary, the
+   Robin trace identity gives phi_s^k = lambda^k exactly, and that value is used.
+2. Multiscale basis functions (MBF): psi_sk = (A^R_{Omega_s})^-1 (t_R phi_s^k on Gamma_s), with
+   Robin traces F_sk(f) = t_R (psi_sk,c - phi_s^k(f)) and |f| P_sk(f) = |f| phi_s^k(f) + beta F_sk(f).
+3. Coupling system (Eq. 13-14) with piecewise-constant M_H, V_H on each interface Gamma_{s,s'}
+   (s the lower, s' the upper subdomain along axis a):
+     flux row     sum_f F_s(f) + F_s'(f) = 0,
+     pressure row sum_f |f| (P_s(f) - P_s'(f)) = 0,
+   with F_s = F_s0 + sum_k c_sk F_sk and likewise P_s.  The matrix G is square (2E x 2E) and is
+   factored by LU with partial pivoting (dense LAPACK getrf; SuperLU beyond 4096 unknowns).
+4. Dirichlet restrictions A[hat-Omega_s, hat-Omega_s] for the smoothing sweeps.
+
+Apply z = T r (the modified MRCM-O of Sec. 3: homogeneous conditions, source r):
+  psi_s0 = (A^R_{Omega_s})^-1 r|Omega_s with traces F_s0 = t_R psi_s0,c, |f| P_s0 = beta F_s0;
+  G c = -g0 where g0 collects the particular traces row by row;
+  z|Omega_s = psi_s0 + sum_k c_sk psi_sk;
+  then ``smooth_steps`` restricted additive Schwarz sweeps: rho = r - A z,
+  delta_s = A[hat-Omega_s, hat-Omega_s]^-1 rho|hat-Omega_s, z|Omega_s += delta_s|Omega_s.
+
+Pinned by (tests/test_oracle_mrcm.py): one subdomain gives T = A^-1; l = 0 gives indicator phi;
+a monolithic dense solve of the whole coupled MRCM system equals the superposition; per-cell mass
+balance and weak flux / pressure continuity of the MRCM reconstruction; exactness of P0 Robin
+coupling on a field that is constant along the interfaces; linearity of T; the smoothing sweep
+leaves A^-1 r unchanged.
+"""
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .grid import transmissibilities, matvec
+from .local import BoxOperator, robin_face
+from .partition import Partition
+
+
+class _Sub:
+    pass
+
+
+class MRCMOS:
+    def __init__(self, K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0):
+        K = np.asarray(K, dtype=np.float64)
+        self.K, self.h, self.dim = K, [float(v) for v in h], dim
+        self.shape = K.shape
+        n = [K.shape[2], K.shape[1], K.shape[0]]
+        self.n = n
+        self.sub = [int(v) for v in sub]
+        self.l = int(l)
+        self.smooth_steps = int(smooth_steps)
+        self.alpha = float(alpha)
+        self.degree = int(iface_degree)
+        self.nq = 1 + self.degree * (dim - 1)  # polynomial functions per side
+        self.T = transmissibilities(K, self.h, dim, bc_kind)
+        self.part = P = Partition(dim, n, self.sub, self.l)
+        self.subs = []
+        for s in range(P.S):
+            self.subs.append(self._setup_subdomain(s))
+        self._assemble_coarse()
+
+    # ---------------------------------------------------------------- polynomial side functions
+    def side_poly(self, q, pos, side, lo, hi):
+        """Value at the face ``pos`` of polynomial function q on ``side`` of the box [lo, hi):
+        q = 0 is the constant, q = 1 (and q = 2 in 3-D) the linear function of the first (second)
+        in-plane axis, scaled to [-1, 1] over the box side."""
+        if q == 0:
+            return 1.0
+        a = side // 2
+        b = [x for x in range(3) if x != a][q - 1]
+        return 2.0 * (pos[b] + 0.5 - lo[b]) / (hi[b] - lo[b]) - 1.0
+
+    # ---------------------------------------------------------------- set-up, per subdomain
+    def _setup_subdomain(self, s):
+        P, K, T, h, dim, nq = self.part, self.K, self.T, self.h, self.dim, self.nq
+        d = _Sub()
+        d.s = s
+        d.op = BoxOperator(K, T, h, dim, self.n, P.box[s, 0], P.box[s, 1], True, self.alpha, self.sub)
+        # Gamma_s faces, in side order (identical to the Robin faces of the Omega_s operator)
+        d.gamma = d.op.robin_faces
+        d.gamma_side = np.array([f[0] for f in d.gamma], dtype=np.int64)
+        d.gamma_li = np.array([f[1] for f in d.gamma], dtype=np.int64)
+        d.tau = np.array([f[2] for f in d.gamma])
+        d.beta = np.array([f[3] for f in d.gamma])
+        d.t_r = np.array([f[4] for f in d.gamma])
+        d.area = np.array([f[5] for f in d.gamma])
+        d.t_f = np.array([f[6] for f in d.gamma])
+        sides = [k for k in range(6) if P.robin[s, k]]
+        d.sides = sides
+        funcs = [(k, q) for k in sides for q in range(nq)]  # basis of Lambda_H^s, side-major
+        d.funcs = funcs
+        N = len(funcs)
+        ng = len(d.gamma)
+        gpos = [f[0] for k in sides for f in P.gamma_faces(s, k)]
+        blo, bhi = P.box[s, 0], P.box[s, 1]
+        # test-function values of M_H, V_H on every Gamma_s face: (nq, ng)
+        d.test = np.array([[self.side_poly(q, gpos[i], int(d.gamma_side[i]), blo, bhi)
+                            for i in range(ng)] for q in range(nq)]).reshape(nq, ng)
+        # step 1: informed multiplier space
+        phi = np.zeros((N, ng))
+        if N > 0:
+            if self.l == 0:
+                for j, (k, q) in enumerate(funcs):
+                    m = d.gamma_side == k
+                    phi[j, m] = d.test[q, m]
+            else:
+                olo, ohi = P.obox[s, 0], P.obox[s, 1]
+                oop = BoxOperator(K, T, h, dim, self.n, olo, ohi, True, self.alpha, self.sub)
+                ofaces = {k: oop_f for k, oop_f in ((k, P.side_faces(olo, ohi, k)) for k in sides)}
+                rhs = np.zeros((oop.n_loc, N))
+                for j, (k, q) in enumerate(funcs):
+                    for (pos, inside, outside) in ofaces[k]:
+                        a = k // 2
+                        _tau, _beta, t_r, _area = robin_face(K, h, a, inside, outside, self.alpha, self.sub)
+                        rhs[oop.local_index(inside), j] += t_r * self.side_poly(q, pos, k, olo, ohi)
+                q_sol = oop.solve(rhs)
+                fi = 0  # Gamma_s faces come in the same side / in-plane order as d.gamma
+                for k in sides:
+                    for (pos, inside, outside) in P.gamma_faces(s, k):
+                        a = k // 2
+                        t_f = self.T[a][pos[2], pos[1], pos[0]]
+                        tau, beta, _tr, area = robin_face(K, h, a, inside, outside, self.alpha, self.sub)
+                        qc = q_sol[oop.local_index(inside)]
+                        qo = q_sol[oop.local_index(outside)]
+                        F = t_f * (qc - qo)
+                        pi = qc - F / tau
+                        phi[:, fi] = -beta * F / area + pi
+                        fi += 1
+                assert fi == ng
+        d.phi = phi
+        # step 2: multiscale basis functions and their side moments
+        rhs = np.zeros((d.op.n_loc, N))
+        for j in range(N):
+            np.add.at(rhs[:, j], d.gamma_li, d.t_r * phi[j])
+        d.psi = d.op.solve(rhs) if N > 0 else np.zeros((d.op.n_loc, 0))
+        F = d.t_r[None, :] * (d.psi[d.gamma_li, :].T - phi)           # (N, ng)
+        Pw = d.area[None, :] * phi + d.beta[None, :] * F              # |f| P
+        # Fbar[side, q, j] = sum over faces of side of test_q F_j ; Pbar likewise with |f| P
+        d.Fbar = np.zeros((6, nq, N))
+        d.Pbar = np.zeros((6, nq, N))
+        for k in sides:
+            m = d.gamma_side == k
+            d.Fbar[k] = d.test[:, m] @ F[:, m].T
+            d.Pbar[k] = d.test[:, m] @ Pw[:, m].T
+        # step 4 (set-up part): Dirichlet restriction on the oversampled region
+        d.schwarz = None
+        if self.smooth_steps > 0:
+            d.schwarz = BoxOperator(K, T, h, dim, self.n, P.obox[s, 0], P.obox[s, 1], False, self.alpha, self.sub)
+            inner = []
+            for a in range(3):
+                inner.append(slice(int(P.box[s, 0, a] - P.obox[s, 0, a]), int(P.box[s, 1, a] - P.obox[s, 0, a])))
+            d.inner = (inner[2], inner[1], inner[0])
+        return d
+
+    # ---------------------------------------------------------------- set-up, coupling system
+    def _assemble_coarse(self):
+        P, nq = self.part, self.nq
+        n_rows = P.E2 * nq
+        self.n_coarse = n_rows
+        self.coff = P.off * nq  # first coarse unknown of each subdomain
+        G = np.zeros((n_rows, n_rows))
+        for e, (a, s, s2) in enumerate(P.interfaces):
+            lo_side, hi_side = 2 * a + 1, 2 * a  # +a side of s, -a side of s'
+            d, d2 = self.subs[s], self.subs[s2]
+            cs = self.coff[s] + np.arange(len(d.funcs))
+            cs2 = self.coff[s2] + np.arange(len(d2.funcs))
+            for q in range(nq):
+                rf = 2 * nq * e + q          # flux rows of interface e
+                rp = 2 * nq * e + nq + q     # pressure rows of interface e
+                G[rf, cs] += d.Fbar[lo_side, q]
+                G[rf, cs2] += d2.Fbar[hi_side, q]
+                G[rp, cs] += d.Pbar[lo_side, q]
+                G[rp, cs2] -= d2.Pbar[hi_side, q]
+        self.G = G
+        self._lu = None
+        self._splu = None
+        if n_rows == 0:
+            return
+        if n_rows <= 4096:
+            self._lu = sla.lu_factor(G)
+        else:
+            self._splu = spla.splu(sp.csc_matrix(G), permc_spec="COLAMD", diag_pivot_thresh=1.0)
+
+    def coarse_solve(self, rhs):
+        if self.n_coarse == 0:
+            return np.zeros(0)
+        if self._lu is not None:
+            return sla.lu_solve(self._lu, rhs)
+        return self._splu.solve(rhs)
+
+    # ---------------------------------------------------------------- apply
+    def particular(self, r):
+        """psi_s0 for every subdomain and the coarse right-hand side g0."""
+        P, nq = self.part, self.nq
+        psi0 = []
+        F0 = np.zeros((P.S, 6, nq))
+        P0 = np.zeros((P.S, 6, nq))
+        for d in self.subs:
+            x = d.op.solve(d.op.restrict(r))
+            psi0.append(x)
+            F = d.t_r * x[d.gamma_li]
+            Pw = d.beta * F
+            for k in d.sides:
+                m = d.gamma_side == k
+                F0[d.s, k] = d.test[:, m] @ F[m]
+                P0[d.s, k] = d.test[:, m] @ Pw[m]
+        g0 = np.zeros(self.n_coarse)
+        for e, (a, s, s2) in enumerate(P.interfaces):
+            for q in range(nq):
+                g0[2 * nq * e + q] = F0[s, 2 * a + 1, q] + F0[s2, 2 * a, q]
+                g0[2 * nq * e + nq + q] = P0[s, 2 * a + 1, q] - P0[s2, 2 * a, q]
+        return psi0, g0
+
+    def reconstruct(self, psi0, c):
+        z = np.zeros(self.shape)
+        for d in self.subs:
+            o = self.coff[d.s]
+            zs = psi0[d.s] + d.psi @ c[o:o + len(d.funcs)]
+            z[d.op.sl] = zs.reshape(d.op.w[2], d.op.w[1], d.op.w[0])
+        return z
+
+    def sweep(self, r, z):
+        """One restricted additive Schwarz sweep on A z = r."""
+        rho = r - matvec(self.T, z, self.dim)
+        z_new = z.copy()
+        for d in self.subs:
+            w = d.schwarz.w
+            delta = d.schwarz.solve(d.schwarz.restrict(rho)).reshape(w[2], w[1], w[0])
+            z_new[d.op.sl] += delta[d.inner]
+        return z_new
+
+    def apply_parts(self, r):
+        r = np.asarray(r, dtype=np.float64).reshape(self.shape)
+        psi0, g0 = self.particular(r)
+        c = self.coarse_solve(-g0)
+        z = self.reconstruct(psi0, c)
+        out = {"psi0": psi0, "g0": g0, "c": c, "z_mrcm": z.copy()}
+        for _ in range(self.smooth_steps):
+            z = self.sweep(r, z)
+        out["z"] = z
+        return out
+
+    def apply(self, r):
+        return self.apply_parts(r)["z"]
+
+    def Av(self, v):
+        return matvec(self.T, np.asarray(v, dtype=np.float64).reshape(self.shape), self.dim)

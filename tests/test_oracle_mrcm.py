@@ -1,0 +1,216 @@
+"""Pins of the oracle's MRCM-OS preconditioner T (Sec. 2.1, Sec. 3, Eq. 11-15)."""
+
+import numpy as np
+import pytest
+
+from oracle import grid
+from oracle.mrcm import MRCMOS
+from paper_2606_08883_gb300 import workloads as W
+
+
+def _pre(prob, sub, l, s, degree=0, alpha=10.0):
+    return MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, sub, l, s, alpha, degree)
+
+
+def _dense_A(pre):
+    return grid.dense_matrix(pre.T, pre.dim, pre.shape)
+
+
+@pytest.mark.parametrize("smooth", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_single_subdomain_is_exact_inverse(dim, smooth):
+    n = (10, 8, 1) if dim == 2 else (6, 5, 4)
+    prob = W.random_problem(n, dim=dim, seed=2, contrast=1e4)
+    pre = _pre(prob, n, 0, smooth)
+    r = np.random.default_rng(0).standard_normal(prob.K.shape)
+    z = pre.apply(r)
+    assert pre.part.E2 == 0
+    ref = np.linalg.solve(_dense_A(pre), r.ravel()).reshape(r.shape)
+    assert np.linalg.norm(z - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("degree", [0, 1])
+def test_zero_oversampling_gives_side_polynomials(degree):
+    prob = W.random_problem((12, 12, 1), seed=5, contrast=1e3)
+    pre = _pre(prob, (4, 4, 1), 0, 0, degree)
+    for d in pre.subs:
+        for j, (k, q) in enumerate(d.funcs):
+            on = d.gamma_side == k
+            assert np.array_equal(d.phi[j, ~on], np.zeros((~on).sum()))
+            assert np.array_equal(d.phi[j, on], d.test[q, on])
+            if q == 0:
+                assert (d.phi[j, on] == 1.0).all()
+
+
+def _monolithic(pre, r):
+    """Solve Eq. 11-14 (homogeneous data, source r) as one dense system: every subdomain's local
+    pressures plus the multiplier coefficients, with the flux and pressure continuity rows."""
+    P = pre.part
+    offs = np.concatenate([[0], np.cumsum([d.op.n_loc for d in pre.subs])])
+    nz = offs[-1]
+    nc = pre.n_coarse
+    M = np.zeros((nz + nc, nz + nc))
+    rhs = np.zeros(nz + nc)
+    for d in pre.subs:
+        o = offs[d.s]
+        M[o:o + d.op.n_loc, o:o + d.op.n_loc] = d.op.dense()
+        rhs[o:o + d.op.n_loc] = d.op.restrict(r)
+        for j in range(len(d.funcs)):
+            col = nz + pre.coff[d.s] + j
+            np.add.at(M[:, col], o + d.gamma_li, -d.t_r * d.phi[j])
+    nq = pre.nq
+
+    def face_terms(d, side):
+        """Rows expressing F(f) and |f| P(f) on the faces of ``side`` as linear forms."""
+        m = d.gamma_side == side
+        idx = np.nonzero(m)[0]
+        o = offs[d.s]
+        Fz = np.zeros((len(idx), nz + nc))
+        for t, i in enumerate(idx):
+            Fz[t, o + d.gamma_li[i]] += d.t_r[i]
+            for j in range(len(d.funcs)):
+                Fz[t, nz + pre.coff[d.s] + j] -= d.t_r[i] * d.phi[j, i]
+        lam = np.zeros((len(idx), nz + nc))
+        for t, i in enumerate(idx):
+            for j in range(len(d.funcs)):
+                lam[t, nz + pre.coff[d.s] + j] += d.phi[j, i]
+        Pw = d.area[idx, None] * lam + d.beta[idx, None] * Fz
+        return Fz, Pw, d.test[:, m]
+
+    for e, (a, s, s2) in enumerate(P.interfaces):
+        F1, P1, t1 = face_terms(pre.subs[s], 2 * a + 1)
+        F2, P2, t2 = face_terms(pre.subs[s2], 2 * a)
+        assert np.array_equal(t1, t2)
+        for q in range(nq):
+            M[nz + 2 * nq * e + q] = t1[q] @ (F1 + F2)
+            M[nz + 2 * nq * e + nq + q] = t1[q] @ (P1 - P2)
+    x = np.linalg.solve(M, rhs)
+    z = np.zeros(pre.shape)
+    for d in pre.subs:
+        z[d.op.sl] = x[offs[d.s]:offs[d.s] + d.op.n_loc].reshape(d.op.w[2], d.op.w[1], d.op.w[0])
+    return z, x[nz:]
+
+
+@pytest.mark.parametrize("l,degree,dim", [(0, 0, 2), (1, 0, 2), (2, 0, 2), (2, 1, 2), (1, 0, 3)])
+def test_superposition_equals_monolithic_dense_solve(l, degree, dim):
+    if dim == 2:
+        prob = W.random_problem((12, 12, 1), seed=11, contrast=1e3)
+        sub = (4, 4, 1)
+    else:
+        prob = W.random_problem((6, 6, 4), dim=3, seed=11, contrast=1e3, bc_kind=[0, 0, 1, 1, 1, 1])
+        sub = (3, 3, 2)
+    pre = _pre(prob, sub, l, 0, degree)
+    r = np.random.default_rng(3).standard_normal(prob.K.shape)
+    parts = pre.apply_parts(r)
+    z_ref, c_ref = _monolithic(pre, r)
+    assert np.linalg.norm(parts["z_mrcm"] - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
+    assert np.linalg.norm(parts["c"] - c_ref) <= 1e-9 * np.linalg.norm(c_ref)
+
+
+def test_mass_balance_and_weak_continuity():
+    prob = W.random_problem((16, 12, 1), seed=8, contrast=1e4)
+    pre = _pre(prob, (4, 4, 1), 2, 0)
+    r = np.random.default_rng(9).standard_normal(prob.K.shape)
+    parts = pre.apply_parts(r)
+    z, c = parts["z_mrcm"], parts["c"]
+    P = pre.part
+    Fside, Pside = {}, {}
+    for d in pre.subs:
+        zs = d.op.restrict(z)
+        lam = d.phi.T @ c[pre.coff[d.s]:pre.coff[d.s] + len(d.funcs)]
+        # per-cell mass balance inside the subdomain: A^R z_s - t_R lambda = r
+        res = d.op.dense() @ zs
+        np.add.at(res, d.gamma_li, -d.t_r * lam)
+        assert np.allclose(res, d.op.restrict(r), rtol=0, atol=1e-10 * np.abs(r).max())
+        F = d.t_r * (zs[d.gamma_li] - lam)
+        Pw = d.area * lam + d.beta * F
+        for k in d.sides:
+            m = d.gamma_side == k
+            Fside[(d.s, k)] = F[m].sum()
+            Pside[(d.s, k)] = Pw[m].sum()
+    scale = max(abs(v) for v in Fside.values())
+    pscale = max(abs(v) for v in Pside.values())
+    for (a, s, s2) in P.interfaces:
+        assert abs(Fside[(s, 2 * a + 1)] + Fside[(s2, 2 * a)]) <= 1e-10 * scale      # Eq. 13
+        assert abs(Pside[(s, 2 * a + 1)] - Pside[(s2, 2 * a)]) <= 1e-10 * pscale     # Eq. 14
+
+
+@pytest.mark.parametrize("l,smooth", [(0, 0), (1, 0), (2, 1), (3, 2)])
+def test_exact_on_fields_constant_along_interfaces(l, smooth):
+    # stripes along x spanning the whole y range; K and the target pressure depend on x only, so
+    # the true Robin data is constant on every interface and lies in the P0 multiplier space
+    rng = np.random.default_rng(21)
+    nx, ny = 20, 6
+    kx = 10.0 ** rng.uniform(-2, 2, size=nx)
+    prob = W.Problem(2, (nx, ny, 1), (1.0 / nx, 1.0 / ny, 1.0), np.tile(kx, (ny, 1))[None],
+                     [0, 0, 1, 1, 1, 1])
+    pre = _pre(prob, (4, ny, 1), l, smooth)
+    p_star = np.tile(rng.standard_normal(nx), (ny, 1))[None]
+    r = pre.Av(p_star)
+    z = pre.apply(r)
+    assert np.linalg.norm(z - p_star) <= 1e-10 * np.linalg.norm(p_star)
+
+
+def test_linearity():
+    prob = W.random_problem((16, 16, 1), seed=12, contrast=1e5)
+    pre = _pre(prob, (4, 4, 1), 2, 2)
+    rng = np.random.default_rng(13)
+    r1, r2 = rng.standard_normal(prob.K.shape), rng.standard_normal(prob.K.shape)
+    lhs = pre.apply(2.0 * r1 - 3.0 * r2)
+    rhs = 2.0 * pre.apply(r1) - 3.0 * pre.apply(r2)
+    assert np.linalg.norm(lhs - rhs) <= 1e-11 * np.linalg.norm(rhs)
+
+
+def test_schwarz_sweep_matches_dense_restricted_additive_schwarz():
+    prob = W.random_problem((12, 10, 1), seed=14, contrast=1e3)
+    pre = _pre(prob, (4, 5, 1), 2, 1)
+    A = _dense_A(pre)
+    rng = np.random.default_rng(15)
+    r, z = rng.standard_normal(prob.K.shape), rng.standard_normal(prob.K.shape)
+    n = pre.n
+    rho = r.ravel() - A @ z.ravel()
+    z_ref = z.ravel().copy()
+    for s in range(pre.part.S):
+        lo, hi = pre.part.box[s, 0], pre.part.box[s, 1]
+        olo = np.maximum(lo - 2, 0)
+        ohi = np.minimum(hi + 2, n)
+        ohi[2], olo[2] = 1, 0
+        cells = [i + n[0] * j for j in range(olo[1], ohi[1]) for i in range(olo[0], ohi[0])]
+        delta = np.linalg.solve(A[np.ix_(cells, cells)], rho[cells])
+        for t, c in enumerate(cells):
+            i, j = c % n[0], c // n[0]
+            if lo[0] <= i < hi[0] and lo[1] <= j < hi[1]:
+                z_ref[c] += delta[t]
+    z_new = pre.sweep(r, z)
+    assert np.allclose(z_new.ravel(), z_ref, rtol=1e-11, atol=1e-11)
+    # a fixed point of the sweep: the exact solution is left unchanged
+    z_star = np.linalg.solve(A, r.ravel()).reshape(r.shape)
+    assert np.linalg.norm(pre.sweep(r, z_star) - z_star) <= 1e-11 * np.linalg.norm(z_star)
+
+
+@pytest.mark.parametrize("l,degree,dim", [(1, 0, 2), (3, 0, 2), (2, 1, 2), (1, 0, 3)])
+def test_basis_equals_restricted_oversampled_solution(l, degree, dim):
+    # Eq. 15 and the Robin condition: phi_s^k is the Robin trace of q^k on Gamma_s, so the local
+    # Robin solve with data phi_s^k reproduces q^k on Omega_s exactly.
+    from oracle.local import BoxOperator, robin_face
+    if dim == 2:
+        prob = W.random_problem((16, 12, 1), seed=31, contrast=1e4)
+        sub = (4, 4, 1)
+    else:
+        prob = W.random_problem((6, 6, 4), dim=3, seed=31, contrast=1e3, bc_kind=[0, 0, 1, 1, 1, 1])
+        sub = (3, 3, 2)
+    pre = _pre(prob, sub, l, 0, degree)
+    P = pre.part
+    for d in pre.subs:
+        olo, ohi = P.obox[d.s, 0], P.obox[d.s, 1]
+        oop = BoxOperator(prob.K, pre.T, prob.h, dim, pre.n, olo, ohi, True, 10.0, sub)
+        M = oop.dense()
+        for j, (k, q) in enumerate(d.funcs):
+            rhs = np.zeros(oop.n_loc)
+            for (pos, inside, outside) in P.side_faces(olo, ohi, k):
+                _tau, _beta, t_r, _area = robin_face(prob.K, prob.h, k // 2, inside, outside, 10.0, sub)
+                rhs[oop.local_index(inside)] += t_r * pre.side_poly(q, pos, k, olo, ohi)
+            qk = np.linalg.solve(M, rhs).reshape(oop.w[2], oop.w[1], oop.w[0])
+            inner = tuple(slice(int(P.box[d.s, 0, a] - olo[a]), int(P.box[d.s, 1, a] - olo[a])) for a in (2, 1, 0))
+            ref = qk[inner].ravel()
+            assert np.allclose(d.psi[:, j], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
