@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark: MRCM-OS-preconditioned GMRES solves on GB300.
+
+One step = one complete solve of a synthetic problem whose inputs are already resident in HBM:
+mrcm_factor_local (transmissibilities, informed spaces, local factors, basis functions, coupling
+LU, Schwarz factors) followed by mrcm_gmres_solve from p0 = 0 to relative residual 1e-8.
+
+Default workload: 512 x 512 cells, binary channelised permeability (30 % fill, contrast 1e6), 16 x 16
+subdomains of 32 x 32, oversampling 4, 2 smoothing sweeps, plain FP64 on the GPU, GMRES(200).
+Multi-GPU: one process per GPU (torchrun), each solving its own seeded problem (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and the max over ranks is
+reported.
+
+--impl reference runs the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (rank 0 only).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solves/s at rel. residual 1e-8"
+UNIT = "solves/s"
+NOMINAL_FP64_TFLOPS = 1.25      # GB300 dense FP64, recipe table (all SMs at 2070 MHz)
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mrcm", choices=["mrcm", "reference"])
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=8, help="GMRES iterations per reference-arm sample")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2606_08883_gb300 import workloads as W
+    prob, q = W.channels(args.N, seed=1 + rank, prec=W.PREC_FP32 if args.prec == "fp32" else W.PREC_FP64)
+    q.restart = args.restart
+    q.max_iter = 3 * args.restart
+    return prob, q
+
+
+def config_dict(args, prob, q):
+    return {"workload": f"channels-{args.N}x{args.N}-contrast1e6-fill0.30", "cells": prob.cells,
+            "subdomains": f"{prob.n[0] // q.sub[0]}x{prob.n[1] // q.sub[1]} of {q.sub[0]}x{q.sub[1]}",
+            "oversample": q.oversample, "smooth_steps": q.smooth_steps, "alpha": q.alpha, "restart": q.restart,
+            "tol_relative": q.tol, "local_prec": args.prec, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single-gpu"}
+
+
+# ----------------------------------------------------------------------------------- oracle
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_2606_08883_gb300 import workloads as W
+from oracle.solve import build, solve
+prob, q = W.channels({N}, seed=1)
+t0 = time.perf_counter()
+pre = build(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha)
+t1 = time.perf_counter()
+p, info, _ = solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub, l=q.oversample,
+                   smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol, restart={restart}, max_iter={iters},
+                   pre=pre)
+t2 = time.perf_counter()
+print(json.dumps({{"setup_s": t1 - t0, "iter_s": t2 - t1, "iters": info["iterations"],
+                  "converged": info["status"] == 0}}))
+"""
+
+
+def run_oracle_sample(N, restart, iters, timeout=900):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, N=N, restart=restart, iters=iters)
+    r = subprocess.run([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                       env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_rate(sample, iters_needed):
+    """solves/s of the oracle: measured set-up + measured per-iteration time scaled to the
+    iteration count a full solve needs."""
+    per_it = sample["iter_s"] / max(sample["iters"], 1)
+    t = sample["setup_s"] + per_it * iters_needed
+    return 1.0 / t, t
+
+
+# ----------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------- roofline
+def phase_model(prob, q, prec):
+    """Algorithmic work per launch of each phase: (flops, bytes)."""
+    S = (prob.n[0] // q.sub[0]) * (prob.n[1] // q.sub[1])
+    elt = 4 if prec == "fp32" else 8
+    wl, hl = q.sub[0], q.sub[1]
+    wo, ho = wl + 2 * q.oversample, hl + 2 * q.oversample
+
+    def packed(w):
+        return (w * (w + 1) // 2 + 3) // 4 * 4
+
+    def factor(w, h):  # per line: Schur update + Cholesky + triangular inverse = w^3 / 2 FMA
+        return S * h * w ** 3, S * h * packed(w) * elt
+
+    def solve(w, h, nr):  # forward + backward: 4 triangular products of w^2/2 FMA per line
+        return S * h * 4 * w * w * nr, S * (2 * h * packed(w) * elt + 2 * w * h * 8 * nr)
+
+    n = prob.cells
+    return {
+        "factor_ohat_robin": factor(wo, ho), "factor_omega": factor(wl, hl), "factor_ohat_dirichlet": factor(wo, ho),
+        "informed": solve(wo, ho, 4), "basis": solve(wl, hl, 4), "particular": solve(wl, hl, 1),
+        "schwarz": solve(wo, ho, 1), "residual": (9 * n, 40 * n), "reconstruct": (8 * n, 56 * n),
+    }
+
+
+def roofline(prof, prob, q, prec, peaks):
+    model = phase_model(prob, q, prec)
+    cands = {k: v for k, v in prof.items() if k in model and v[1] > 0}
+    if not cands:
+        return None, None
+    name = max(cands, key=lambda k: cands[k][0])
+    ms, launches = cands[name]
+    per_launch_s = ms / 1e3 / launches
+    flops, nbytes = model[name]
+    if name in ("residual", "reconstruct") or (prec == "fp32" and name in ("schwarz", "particular")):
+        achieved = nbytes / per_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return name, {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                      "traffic": None, "kernel": name, "launch_ms": per_launch_s * 1e3,
+                      "algorithmic_bytes_per_launch": nbytes, "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
+    peak = NOMINAL_FP32_TFLOPS if prec == "fp32" else NOMINAL_FP64_TFLOPS
+    achieved = flops / per_launch_s / 1e12
+    return name, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                  "traffic": None, "kernel": name, "launch_ms": per_launch_s * 1e3,
+                  "algorithmic_flops_per_launch": flops,
+                  "peak_source": ("FP32 FMA lanes x 2 x 2070 MHz x 152 SMs" if prec == "fp32" else
+                                  "nominal GB300 dense FP64 1.25 TFLOP/s at 2070 MHz")}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+# ----------------------------------------------------------------------------------- arms
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rates = []
+    for step in range(args.warmup + args.steps):
+        s = run_oracle_sample(args.N, args.restart, args.ref_iters)
+        if step >= args.warmup:
+            rates.append(s)
+    need = ORACLE_FULL_ITERS.get((args.N, args.restart), None)
+    iters_needed = need if need else rates[-1]["iters"]
+    vals = [oracle_rate(s, iters_needed)[0] for s in rates]
+    v = statistics.median(vals)
+    prob, q = workload(args)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(args, prob, q),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: oracle set-up + {args.ref_iters} GMRES iterations, per-iteration "
+                                       f"time scaled to the {iters_needed} iterations a full solve needs"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# iterations the FP64 oracle needs for a full solve of the default workload (measured, GMRES(200))
+ORACLE_FULL_ITERS = {(512, 200): 178}
+
+
+def mrcm_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any CUDA call: the oracle runs in its own process on the host cores
+        try:
+            cpu = run_oracle_sample(args.N, args.restart, args.ref_iters)
+        except Exception as exc:  # reported, never silently replaced
+            cpu = {"error": str(exc)[:300]}
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2606_08883_gb300 import mrcm
+    prob, q = workload(args, rank)
+    solver = mrcm.Solver(prob, q, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    info = None
+    for _ in range(args.warmup):
+        solver.factor()
+        p, info = solver.solve()
+    torch.cuda.synchronize(dev)
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = getattr(props, "uuid", None)
+    clocks = ClockSampler(f"GPU-{gpu_id}" if gpu_id is not None else local)
+    clocks.start()
+    launches0 = mrcm.mrcm_launch_count()
+    times, iters = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.factor()
+        p, info = solver.solve()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        iters.append(info["iterations"])
+    launches = mrcm.mrcm_launch_count() - launches0
+    clk = clocks.stop()
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    # set-up / solve split from one profiled-free step
+    torch.cuda.synchronize(dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    solver.factor()
+    e[1].record(stream)
+    solver.solve()
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    setup_ms, solve_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    # end to end through the C ABI with host buffers (K in, p out, pinned)
+    e2e = None
+    if not args.no_e2e:
+        K_host = torch.as_tensor(prob.K.ravel()).pin_memory()
+        p_host = torch.empty(prob.cells, dtype=torch.float64).pin_memory()
+        solver.solve_host(K_host, p_host)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        barrier()
+        for _ in range(args.steps):
+            solver.solve_host(K_host, p_host)
+        torch.cuda.synchronize(dev)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.cells,
+               "d2h_bytes_per_step": 8 * prob.cells}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    dom, roof = roofline(prof, prob, q, args.prec, peaks)
+    lat = sorted(times)
+    cpu_line = None
+    if cpu is not None and "error" not in cpu:
+        v, t = oracle_rate(cpu, statistics.median(iters))
+        cpu_line = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": f"oracle set-up + {cpu['iters']} GMRES iterations on the same workload, "
+                              f"per-iteration time scaled to {int(statistics.median(iters))} iterations"}
+    elif cpu is not None:
+        cpu_line = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu["error"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic", "config": config_dict(args, prob, q),
+        "mcells_per_s": value * prob.cells / 1e6, "iterations": int(statistics.median(iters)),
+        "rel_res": info["rel_res"], "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "setup_ms": setup_ms, "solve_ms": solve_ms,
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+        "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        mrcm_arm(args)
+
+
+if __name__ == "__main__":
+    main()

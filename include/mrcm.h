@@ -1,0 +1,191 @@
+/*
+ * libmrcm -- MRCM-OS right-preconditioned restarted GMRES for Darcy pressure problems on one GPU.
+ *
+ * C ABI.  Every entry point takes plain pointers and sizes; device pointers are CUDA device
+ * addresses of the calling process's current device, host pointers are ordinary CPU memory, and
+ * `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  No entry point
+ * aborts or traps: each returns an mrcm_status and, for a handle, keeps a message readable with
+ * mrcm_last_error().  Work is enqueued on `stream` in order; calls that return results to the host
+ * (mrcm_gmres_solve, mrcm_solve_host, mrcm_debug_get, mrcm_factor_local's status check) synchronise
+ * that stream.
+ *
+ * The library allocates no device memory.  The caller sizes one workspace with mrcm_footprint(),
+ * allocates it (e.g. from PyTorch's caching allocator) and passes it to mrcm_setup(); the handle
+ * carves every internal array out of it.  The workspace must stay allocated, untouched by the
+ * caller and at least 256-byte aligned until mrcm_destroy().  Host-side tables live in ordinary
+ * heap memory owned by the handle.
+ *
+ * Method (Sec. 2.1 and Sec. 3 of "Accelerating GMRES with Matrix-Free Multiscale Robin
+ * Preconditioners"): the fine operator A is the cell-centred two-point-flux form of the statically
+ * condensed lowest-order Raviart-Thomas system (Sec. 3); T is the MRCM-OS operator with homogeneous
+ * boundary conditions and the residual as source (Sec. 3), built from informed multiplier spaces on
+ * oversampled regions (Eq. 15), multiscale basis functions, the weak coupling conditions (Eq. 13-14)
+ * and overlapping-Schwarz smoothing sweeps; the Krylov solver is Algorithm 1 (restarted GMRES with
+ * right preconditioning, storing Z).
+ *
+ * Grid layout: cell (i, j, k) of an nx x ny x nz grid is element i + nx*(j + ny*k) (x fastest).
+ * Face arrays of axis x have (nx+1) entries along x: entry i separates cells i-1 and i (likewise for
+ * y and z).  Sides are numbered -x, +x, -y, +y, -z, +z.  2-D problems have dim = 2, n[2] = 1 and
+ * h[2] = slab thickness (face areas are products of the two other cell sizes).
+ *
+ * Supported on the GPU path: dim = 2, subdomain width sub[0] + 2*oversample <= 64.  Other valid
+ * inputs return MRCM_ERR_UNSUPPORTED.
+ */
+#ifndef MRCM_H
+#define MRCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MRCM_OK = 0,
+  MRCM_ERR_INVALID_ARG = 1,   /* bad sizes, non-positive / non-finite data, null required pointer */
+  MRCM_ERR_OOM = 2,           /* workspace smaller than mrcm_footprint() */
+  MRCM_ERR_SINGULAR = 3,      /* zero or non-finite pivot in a local or coupling factorisation */
+  MRCM_ERR_NOT_CONVERGED = 4, /* max_iter reached; the best iterate and result are still written */
+  MRCM_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  MRCM_ERR_CUDA = 6,          /* a CUDA runtime call failed (message in mrcm_last_error) */
+  MRCM_ERR_BUSY = 7,
+  MRCM_ERR_UNSUPPORTED = 8    /* valid input outside what the GPU path implements */
+} mrcm_status;
+
+enum { MRCM_BC_DIRICHLET = 0, MRCM_BC_NEUMANN = 1 };
+enum { MRCM_PREC_FP64 = 0, MRCM_PREC_FP32 = 1 };
+
+/* The elliptic mixed problem of Eq. 1a-1d on a Cartesian grid. */
+typedef struct mrcm_problem {
+  int32_t dim;              /* 2 or 3 */
+  int32_t n[3];             /* cells per axis */
+  double h[3];              /* cell size per axis (> 0) */
+  const double* K;          /* device, n0*n1*n2 scalar permeabilities, > 0 and finite */
+  int32_t bc_kind[6];       /* per side: MRCM_BC_DIRICHLET (p = g) or MRCM_BC_NEUMANN (u.n = z) */
+  const double* bc_val[6];  /* device per side, or NULL for zero data: one value per boundary face,
+                               laid out like the layer of cells touching the side (x fastest among
+                               the remaining axes): Dirichlet pressure g or outward velocity z */
+  const double* f;          /* device, cell-integrated source per cell, or NULL for zero */
+} mrcm_problem;
+
+/* Method and solver parameters (Table 1 notation: oversampling l*h, k smoothing steps). */
+typedef struct mrcm_params {
+  int32_t sub[3];           /* cells per subdomain per axis; must divide n (sub[2] = 1 in 2-D) */
+  int32_t oversample;       /* l, cells: 0 <= l < sub[a] on every active axis */
+  int32_t smooth_steps;     /* Schwarz sweeps after the multiscale solve, >= 0 */
+  double alpha;             /* Robin parameter of Eq. 6, > 0 (the paper uses 10) */
+  double tol;               /* GMRES tolerance on ||b - A p||_2, > 0 */
+  int32_t tol_relative;     /* 1: ||b - A p|| <= tol ||b||; 0: absolute (as in the paper's tables) */
+  int32_t restart;          /* Krylov dimension m, 1..256 */
+  int32_t max_iter;         /* cap on preconditioner applications, >= 1 */
+  int32_t local_prec;       /* MRCM_PREC_FP64 or MRCM_PREC_FP32 (local factors and solves) */
+} mrcm_params;
+
+typedef struct mrcm_result {
+  int32_t iterations;       /* applications of T */
+  int32_t restarts;         /* completed cycles that did not meet the tolerance */
+  int32_t status;           /* MRCM_OK or MRCM_ERR_NOT_CONVERGED */
+  int32_t history_len;      /* entries written to history */
+  double abs_res;           /* final true residual ||b - A p||_2 */
+  double rel_res;           /* abs_res / ||b|| (0 when b = 0) */
+  double bnorm;             /* ||b||_2 */
+  double* history;          /* host, optional: initial residual, |g_{j+1}| per step, true residual
+                               after each cycle; NULL to skip */
+  int32_t history_cap;      /* capacity of history */
+} mrcm_result;
+
+typedef struct mrcm_ctx* mrcm_handle;
+
+/* Device workspace bytes needed by mrcm_setup() for this grid and parameters (Sec. 2.1 layout:
+ * local factors per subdomain, basis functions, coupling system, Krylov basis).  Host only;
+ * problem->K and the other device pointers are not read. */
+mrcm_status mrcm_footprint(const mrcm_problem* problem, const mrcm_params* params, size_t* bytes);
+
+/* Partition the grid (MRCM-OS step 1), carve the workspace and enqueue copies of K, the boundary
+ * data and the source into it.  The caller may free or reuse its own K / bc_val / f buffers once
+ * `stream` has passed this call.  No factorisation happens here.  On success *out owns the
+ * host tables; release it with mrcm_destroy(). */
+mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, void* workspace,
+                       size_t workspace_bytes, void* stream, mrcm_handle* out);
+
+/* Replace K, boundary data and source (same grid and parameters) by enqueueing copies into the
+ * workspace.  The next mrcm_factor_local() uses them. */
+mrcm_status mrcm_update_problem(mrcm_handle h, const mrcm_problem* problem, void* stream);
+
+/* Set-up of T (MRCM-OS steps 1-3 and the smoothing factors): face transmissibilities and b
+ * (Sec. 3), oversampled Robin solves and informed spaces (Eq. 15), local Robin factors and
+ * multiscale basis functions, coupling system (Eq. 13-14) and its LU factors, Dirichlet factors of
+ * the oversampled regions.  Synchronises `stream` to report MRCM_ERR_SINGULAR. */
+mrcm_status mrcm_factor_local(mrcm_handle h, void* stream);
+
+/* z = T r (Sec. 3: the modified MRCM-O with homogeneous conditions and source r, followed by the
+ * smoothing sweeps).  r and z are device arrays of n0*n1*n2 doubles; they may not overlap. */
+mrcm_status mrcm_apply_precond(mrcm_handle h, const double* r, double* z, void* stream);
+
+/* w = A v, the matrix-free fine operator (Sec. 3) with homogeneous boundary data; device arrays. */
+mrcm_status mrcm_apply_operator(mrcm_handle h, const double* v, double* w, void* stream);
+
+/* b of A p = b (Sec. 3): source plus boundary terms, into a device array of n cells. */
+mrcm_status mrcm_rhs(mrcm_handle h, double* b, void* stream);
+
+/* Algorithm 1: restarted right-preconditioned GMRES.  b: device rhs, or NULL to use the assembled
+ * b; p: device, initial guess on entry (zero it for p0 = 0), solution on return.  ux, uy, uz:
+ * device face-velocity outputs (face arrays of each axis, positive along +axis) or NULL.  result:
+ * host, required.  Returns MRCM_ERR_NOT_CONVERGED (with p and result written) if max_iter is hit. */
+mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* ux, double* uy,
+                             double* uz, mrcm_result* result, void* stream);
+
+/* End-to-end solve from host memory: copy K_host (n cells; NULL keeps the resident field) to the
+ * device, run mrcm_factor_local and mrcm_gmres_solve from p0 = 0, copy p back to p_host (n
+ * doubles).  Use pinned host memory for asynchronous copies. */
+mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host, mrcm_result* result,
+                            void* stream);
+
+void mrcm_destroy(mrcm_handle h);
+const char* mrcm_status_string(mrcm_status s);
+const char* mrcm_last_error(mrcm_handle h);
+
+/* Integer partition tables of MRCM-OS step 1, computed on the host without a GPU, as a flat int32
+ * array: header {dim, n0, n1, n2, sub0, sub1, sub2, l, S, 2E, E}; per subdomain {box lo[3] hi[3],
+ * oversampled box lo[3] hi[3] (clipped to the grid), Robin side mask, N_s, coarse offset}; per
+ * interface {axis, lower s, upper s}; per subdomain and Robin side {face count, face ids}.  A face
+ * id is its flat index in the face array of its axis plus the sizes of the preceding axes' face
+ * arrays.  Writes min(cap, total) entries; *len receives the total. */
+mrcm_status mrcm_plan_export(const mrcm_problem* problem, const mrcm_params* params, int32_t* buf,
+                             size_t cap, size_t* len);
+
+/* Debug / parity access to internal device arrays, copied to host (synchronises `stream`):
+ *   MRCM_DBG_TRANS   face transmissibilities, x faces then y faces
+ *   MRCM_DBG_PHI     informed spaces, [S][4 functions][4 sides][max(sub0, sub1)]
+ *   MRCM_DBG_PSI     basis functions, [4 sides][n cells] (global layout)
+ *   MRCM_DBG_MOMENTS side moments of the basis traces, [S][4 sides][4 functions][F, |f|P]
+ *   MRCM_DBG_G       coupling matrix G, dense 2E x 2E row-major in the canonical row order
+ *   MRCM_DBG_COARSE  coefficients c of the last apply, [2E]
+ *   MRCM_DBG_ZMRCM   last apply's multiscale solution before smoothing, [n cells]
+ * *len receives the element count; at most cap doubles are written. */
+enum { MRCM_DBG_TRANS = 0, MRCM_DBG_PHI = 1, MRCM_DBG_PSI = 2, MRCM_DBG_MOMENTS = 3, MRCM_DBG_G = 4,
+       MRCM_DBG_COARSE = 5, MRCM_DBG_ZMRCM = 6 };
+mrcm_status mrcm_debug_get(mrcm_handle h, int32_t what, double* host_out, size_t cap, size_t* len,
+                           void* stream);
+
+/* Per-phase device time.  While enabled, the library records a pair of CUDA events on the caller's
+ * stream around every kernel group of a phase (events are created on the first use and reused).
+ * mrcm_profile_read() synchronises `stream`, adds the elapsed times of all recorded pairs to the
+ * per-phase totals, and copies min(cap, MRCM_PHASES) totals (milliseconds) and launch counts to the
+ * host arrays (either may be NULL); reset != 0 clears the totals afterwards.  Phases: */
+enum { MRCM_PH_ASSEMBLE = 0, MRCM_PH_FACTOR_OHAT_ROBIN = 1, MRCM_PH_INFORMED = 2, MRCM_PH_FACTOR_OMEGA = 3,
+       MRCM_PH_BASIS = 4, MRCM_PH_COARSE_FACTOR = 5, MRCM_PH_FACTOR_OHAT_DIRICHLET = 6,
+       MRCM_PH_PARTICULAR = 7, MRCM_PH_COARSE_SOLVE = 8, MRCM_PH_RECONSTRUCT = 9, MRCM_PH_RESIDUAL = 10,
+       MRCM_PH_SCHWARZ = 11, MRCM_PH_KRYLOV = 12, MRCM_PHASES = 13 };
+mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable);
+mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int32_t cap, int32_t reset,
+                              void* stream);
+
+/* Total kernels this library has launched in the process (all handles), for launch accounting. */
+int64_t mrcm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCM_H */

@@ -1,0 +1,76 @@
+"""Build libmrcm in-tree: every CUDA translation unit for sm_103a in parallel, then one shared
+library at ``paper_2606_08883_gb300/_lib/libmrcm.so``.  No cmake; nvcc and g++ only."""
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIBDIR = os.path.join(HERE, "_lib")
+OBJDIR = os.path.join(ROOT, "_build", "libmrcm")
+LIB = os.path.join(LIBDIR, "libmrcm.so")
+
+CUDA_SOURCES = ["api.cu", "k_grid.cu", "k_local.cu", "k_coarse.cu", "k_krylov.cu"]
+CXX_SOURCES = ["plan.cpp"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmrcm")
+
+
+def _cuda_home(nvcc):
+    return os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+
+
+def _run(cmd):
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("build step failed:\n" + " ".join(cmd) + "\n" + r.stdout)
+    return r.stdout
+
+
+def _stale(lib, sources):
+    if not os.path.exists(lib):
+        return True
+    t = os.path.getmtime(lib)
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "mrcm.h")]
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def build(force=False, verbose=False):
+    """Compile and link libmrcm.so for sm_103a; returns its path."""
+    if not force and not _stale(LIB, CUDA_SOURCES):
+        return LIB
+    nvcc = _nvcc()
+    cuda = _cuda_home(nvcc)
+    os.makedirs(OBJDIR, exist_ok=True)
+    os.makedirs(LIBDIR, exist_ok=True)
+    jobs = []
+    for src in CUDA_SOURCES:
+        obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
+                     os.path.join(CSRC, src), "-o", obj])
+    for src in CXX_SOURCES:
+        obj = os.path.join(OBJDIR, src.replace(".cpp", ".o"))
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I" + os.path.join(cuda, "include"), "-c",
+                     os.path.join(CSRC, src), "-o", obj])
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        outs = list(ex.map(_run, jobs))
+    if verbose:
+        print("".join(outs))
+    objs = [os.path.join(OBJDIR, s.rsplit(".", 1)[0] + ".o") for s in CUDA_SOURCES + CXX_SOURCES]
+    tmp = LIB + ".tmp"
+    _run([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

@@ -1,0 +1,636 @@
+// libmrcm C ABI: set-up, MRCM-OS preconditioner application and restarted GMRES (Algorithm 1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <atomic>
+
+#include "internal.h"
+
+using namespace mrcm;
+
+namespace mrcm {
+static std::atomic<long long> g_launches{0};
+void count_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+}  // namespace mrcm
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Phase brackets: a (start, stop) event pair per kernel group while profiling is enabled.
+struct Phase {
+  mrcm_handle h;
+  int ph;
+  cudaStream_t st;
+  long long l0;
+  Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
+    if (!h->prof) return;
+    const size_t need = 2 * (h->ev_used + 1);
+    while (h->ev_pool.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        h->prof = false;
+        return;
+      }
+      h->ev_pool.push_back(e);
+    }
+    if (h->ev_phase.size() < h->ev_used + 1) h->ev_phase.resize(h->ev_used + 1);
+    h->ev_phase[h->ev_used] = ph;
+    cudaEventRecord(h->ev_pool[2 * h->ev_used], st);
+  }
+  ~Phase() {
+    if (!h->prof) return;
+    cudaEventRecord(h->ev_pool[2 * h->ev_used + 1], st);
+    h->ph_launch[ph] += g_launches.load() - l0;
+    h->ev_used++;
+  }
+};
+
+mrcm_status fail(mrcm_handle h, mrcm_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+#define CK(h, x)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess) return fail((h), MRCM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+T* at(mrcm_handle h, size_t off) {
+  return reinterpret_cast<T*>(h->ws + off);
+}
+
+struct Tables {
+  int* iface;
+  int* home;
+  int* off;
+  int* rank;
+  int* cidx;
+};
+
+Tables tables(mrcm_handle h) {
+  const Plan& P = h->plan;
+  int* base = at<int>(h, h->lay.tab);
+  Tables t;
+  t.iface = base;
+  t.home = t.iface + 3 * P.E;
+  t.off = t.home + P.E2;
+  t.rank = t.off + P.S;
+  t.cidx = t.rank + 6 * P.S;
+  return t;
+}
+
+Geo geo(mrcm_handle h) {
+  Geo g;
+  const Plan& P = h->plan;
+  g.nx = P.n[0];
+  g.ny = P.n[1];
+  g.sx = P.sub[0];
+  g.sy = P.sub[1];
+  g.mx = P.m[0];
+  g.my = P.m[1];
+  g.l = P.l;
+  g.smax = h->lay.smax;
+  g.hx = h->h[0];
+  g.hy = h->h[1];
+  g.hz = h->h[2];
+  g.alpha = h->prm.alpha;
+  g.K = at<double>(h, h->lay.K);
+  g.Tx = at<double>(h, h->lay.Tx);
+  g.Ty = at<double>(h, h->lay.Ty);
+  return g;
+}
+
+CoarseDev coarse(mrcm_handle h) {
+  CoarseDev c;
+  const Plan& P = h->plan;
+  Tables t = tables(h);
+  c.n = P.E2;
+  c.kl = P.kl;
+  c.ku = P.ku;
+  c.ldab = h->lay.ldab;
+  c.ab = at<double>(h, h->lay.G);
+  c.ipiv = at<int>(h, h->lay.ipiv);
+  c.g = at<double>(h, h->lay.gc);
+  c.iface = t.iface;
+  c.home = t.home;
+  c.off = t.off;
+  c.rank = t.rank;
+  return c;
+}
+
+size_t ncell(mrcm_handle h) { return (size_t)h->n[0] * h->n[1] * h->n[2]; }
+
+std::string supported(const mrcm_problem& p, const mrcm_params& q) {
+  if (p.dim != 2) return "the GPU path implements dim == 2";
+  if (q.sub[0] + 2 * q.oversample > 64 || q.sub[1] + 2 * q.oversample > 64)
+    return "the GPU path needs sub + 2 * oversample <= 64 on x and y";
+  return std::string();
+}
+
+mrcm_status copy_problem(mrcm_handle h, const mrcm_problem* p, cudaStream_t st) {
+  const size_t n = ncell(h);
+  if (!p->K) return fail(h, MRCM_ERR_INVALID_ARG, "problem->K is null");
+  CK(h, cudaMemcpyAsync(at<double>(h, h->lay.K), p->K, 8 * n, cudaMemcpyDeviceToDevice, st));
+  h->has_f = p->f != nullptr;
+  if (p->f) CK(h, cudaMemcpyAsync(at<double>(h, h->lay.f), p->f, 8 * n, cudaMemcpyDeviceToDevice, st));
+  const size_t len = std::max(h->n[0], h->n[1]);
+  double* bcv = at<double>(h, h->lay.bcv);
+  for (int s = 0; s < 4; ++s) {
+    h->has_bc[s] = p->bc_val[s] != nullptr;
+    const size_t cnt = s < 2 ? (size_t)h->n[1] : (size_t)h->n[0];
+    if (p->bc_val[s]) CK(h, cudaMemcpyAsync(bcv + s * len, p->bc_val[s], 8 * cnt, cudaMemcpyDeviceToDevice, st));
+  }
+  h->factored = false;
+  return MRCM_OK;
+}
+
+__global__ void k_check_positive(const double* K, size_t n, int* flags) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = K[i];
+    if (!(v > 0.0) || !isfinite(v)) atomicOr(flags, FLAG_NONFINITE);
+  }
+}
+
+__global__ void k_set(double* p, double v) { *p = v; }
+
+void bc_ptrs(mrcm_handle h, const double* ptrs[4]) {
+  const size_t len = std::max(h->n[0], h->n[1]);
+  const double* bcv = at<double>(h, h->lay.bcv);
+  for (int s = 0; s < 4; ++s) ptrs[s] = h->has_bc[s] ? bcv + s * len : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mrcm_status_string(mrcm_status s) {
+  switch (s) {
+    case MRCM_OK: return "ok";
+    case MRCM_ERR_INVALID_ARG: return "invalid argument";
+    case MRCM_ERR_OOM: return "workspace too small";
+    case MRCM_ERR_SINGULAR: return "singular factorisation";
+    case MRCM_ERR_NOT_CONVERGED: return "not converged";
+    case MRCM_ERR_TIMEOUT: return "device wait timed out";
+    case MRCM_ERR_CUDA: return "CUDA error";
+    case MRCM_ERR_BUSY: return "busy";
+    case MRCM_ERR_UNSUPPORTED: return "unsupported on the GPU path";
+  }
+  return "unknown status";
+}
+
+const char* mrcm_last_error(mrcm_handle h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+mrcm_status mrcm_plan_export(const mrcm_problem* problem, const mrcm_params* params, int32_t* buf, size_t cap,
+                             size_t* len) {
+  if (!problem || !params || !len) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
+  Plan P;
+  std::string why = make_plan(*problem, *params, P);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_INVALID_ARG, why);
+  std::vector<int32_t> out = export_plan(P);
+  *len = out.size();
+  if (buf) std::memcpy(buf, out.data(), sizeof(int32_t) * std::min(cap, out.size()));
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_footprint(const mrcm_problem* problem, const mrcm_params* params, size_t* bytes) {
+  if (!problem || !params || !bytes) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
+  Plan P;
+  std::string why = make_plan(*problem, *params, P);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_INVALID_ARG, why);
+  why = supported(*problem, *params);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_UNSUPPORTED, why);
+  *bytes = make_layout(P, *params).total;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, void* workspace, size_t workspace_bytes,
+                       void* stream, mrcm_handle* out) {
+  if (!problem || !params || !out) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  Plan P;
+  std::string why = make_plan(*problem, *params, P);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_INVALID_ARG, why);
+  why = supported(*problem, *params);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_UNSUPPORTED, why);
+  Layout L = make_layout(P, *params);
+  if (!workspace) return fail(nullptr, MRCM_ERR_INVALID_ARG, "workspace is null");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(nullptr, MRCM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total)
+    return fail(nullptr, MRCM_ERR_OOM, "workspace smaller than mrcm_footprint(): need " + std::to_string(L.total) + " bytes");
+  mrcm_handle h = new (std::nothrow) mrcm_ctx();
+  if (!h) return fail(nullptr, MRCM_ERR_OOM, "host allocation failed");
+  h->plan = P;
+  h->lay = L;
+  h->prm = *params;
+  h->dim = problem->dim;
+  for (int a = 0; a < 3; ++a) {
+    h->n[a] = problem->n[a];
+    h->h[a] = problem->h[a];
+  }
+  for (int s = 0; s < 6; ++s) h->bc_kind[s] = problem->bc_kind[s];
+  h->ws = static_cast<char*>(workspace);
+  h->ws_bytes = workspace_bytes;
+  h->coarse_n = P.E2;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mrcm_status rc = copy_problem(h, problem, st);
+  if (rc != MRCM_OK) {
+    g_last_error = h->err;
+    delete h;
+    return rc;
+  }
+  // plan tables to the device
+  std::vector<int> tab;
+  tab.insert(tab.end(), P.iface.begin(), P.iface.end());
+  tab.insert(tab.end(), P.row_home.begin(), P.row_home.end());
+  tab.insert(tab.end(), P.off.begin(), P.off.end());
+  tab.insert(tab.end(), P.rank.begin(), P.rank.end());
+  for (int s = 0; s < P.S; ++s)
+    for (int k = 0; k < 4; ++k) tab.push_back(P.rank[6 * s + k] >= 0 ? P.off[s] + P.rank[6 * s + k] : -1);
+  h->tab_host = tab;
+  cudaError_t e = cudaMemcpyAsync(at<int>(h, L.tab), h->tab_host.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<unsigned char>(h, L.red), 0, 8 * 4 * RED_BLOCKS + 64, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<int>(h, L.flags), 0, 4 * 64, st);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("set-up copies: ") + cudaGetErrorString(e);
+    delete h;
+    return MRCM_ERR_CUDA;
+  }
+  *out = h;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_update_problem(mrcm_handle h, const mrcm_problem* problem, void* stream) {
+  if (!h || !problem) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (problem->dim != h->dim) return fail(h, MRCM_ERR_INVALID_ARG, "dimension differs from set-up");
+  for (int a = 0; a < 3; ++a)
+    if (problem->n[a] != h->n[a] || problem->h[a] != h->h[a]) return fail(h, MRCM_ERR_INVALID_ARG, "grid differs from set-up");
+  for (int s = 0; s < 6; ++s)
+    if (problem->bc_kind[s] != h->bc_kind[s]) return fail(h, MRCM_ERR_INVALID_ARG, "boundary kinds differ from set-up");
+  return copy_problem(h, problem, static_cast<cudaStream_t>(stream));
+}
+
+mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
+  if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout& L = h->lay;
+  const Plan& P = h->plan;
+  const bool fp32 = h->prm.local_prec == MRCM_PREC_FP32;
+  int* flags = at<int>(h, L.flags);
+  CK(h, cudaMemsetAsync(flags, 0, 4 * 64, st));
+  const size_t n = ncell(h);
+  k_check_positive<<<256, 256, 0, st>>>(at<double>(h, L.K), n, flags);
+  CK(h, cudaGetLastError());
+  Geo g = geo(h);
+  const double* bcp[4];
+  bc_ptrs(h, bcp);
+  {
+    Phase ph(h, MRCM_PH_ASSEMBLE, st);
+    CK(h, launch_assemble(g, h->bc_kind, bcp, h->has_f ? at<double>(h, L.f) : nullptr, at<double>(h, L.Tx),
+                          at<double>(h, L.Ty), at<double>(h, L.b), st));
+  }
+  // MRCM-OS step 2: informed multiplier spaces from the oversampled Robin problems (Eq. 15)
+  CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * L.smax, st));
+  if (P.l > 0) {
+    Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
+    CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
+  }
+  {
+    Phase ph(h, MRCM_PH_INFORMED, st);
+    CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), st));
+  }
+  // MRCM-OS step 3: local Robin factors and multiscale basis functions
+  {
+    Phase ph(h, MRCM_PH_FACTOR_OMEGA, st);
+    CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, st));
+  }
+  {
+    Phase ph(h, MRCM_PH_BASIS, st);
+    CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), at<double>(h, L.psi),
+                       at<double>(h, L.mom), st));
+  }
+  // coupling system (Eq. 13-14)
+  CoarseDev c = coarse(h);
+  {
+    Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
+    CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
+    CK(h, launch_coarse_factor(c, flags, st));
+  }
+  // smoothing: Dirichlet factors of the oversampled regions
+  if (h->prm.smooth_steps > 0) {
+    Phase ph(h, MRCM_PH_FACTOR_OHAT_DIRICHLET, st);
+    CK(h, launch_factor(g, BOX_OHAT_DIRICHLET, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_d), fp32, flags, st));
+  }
+  int hf = 0;
+  CK(h, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (hf & FLAG_NONFINITE) return fail(h, MRCM_ERR_INVALID_ARG, "K must be positive and finite");
+  if (hf & FLAG_SINGULAR_LOCAL) return fail(h, MRCM_ERR_SINGULAR, "non-positive pivot in a local factorisation");
+  if (hf & FLAG_SINGULAR_COARSE) return fail(h, MRCM_ERR_SINGULAR, "zero pivot in the coupling system");
+  h->factored = true;
+  return MRCM_OK;
+}
+
+static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream_t st) {
+  const Layout& L = h->lay;
+  const Plan& P = h->plan;
+  const bool fp32 = h->prm.local_prec == MRCM_PREC_FP32;
+  Geo g = geo(h);
+  // particular solutions and their side moments
+  {
+    Phase ph(h, MRCM_PH_PARTICULAR, st);
+    CK(h, launch_particular(g, at<void>(h, L.Linv_loc), L.LSl, fp32, r, at<double>(h, L.psi0), at<double>(h, L.mom0), st));
+  }
+  // coupling system
+  CoarseDev c = coarse(h);
+  {
+    Phase ph(h, MRCM_PH_COARSE_SOLVE, st);
+    CK(h, launch_coarse_rhs(c, at<double>(h, L.mom0), P.E, st));
+    CK(h, launch_coarse_solve(c, st));
+  }
+  // reconstruction
+  {
+    Phase ph(h, MRCM_PH_RECONSTRUCT, st);
+    CK(h, launch_reconstruct(g, at<double>(h, L.psi0), at<double>(h, L.psi), tables(h).cidx, at<double>(h, L.gc), z, st));
+  }
+  if (h->keep_z0) CK(h, cudaMemcpyAsync(at<double>(h, L.z0), z, 8 * ncell(h), cudaMemcpyDeviceToDevice, st));
+  // smoothing sweeps (restricted additive Schwarz)
+  for (int it = 0; it < h->prm.smooth_steps; ++it) {
+    {
+      Phase ph(h, MRCM_PH_RESIDUAL, st);
+      CK(h, launch_residual(g, r, z, at<double>(h, L.rho), st));
+    }
+    Phase ph(h, MRCM_PH_SCHWARZ, st);
+    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, at<double>(h, L.rho), z, st));
+  }
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_apply_precond(mrcm_handle h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "mrcm_factor_local has not completed");
+  if (r == z) return fail(h, MRCM_ERR_INVALID_ARG, "r and z must not overlap");
+  return apply_T(h, r, z, static_cast<cudaStream_t>(stream));
+}
+
+mrcm_status mrcm_apply_operator(mrcm_handle h, const double* v, double* w, void* stream) {
+  if (!h || !v || !w) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "mrcm_factor_local has not completed");
+  CK(h, launch_matvec(geo(h), v, w, static_cast<cudaStream_t>(stream)));
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_rhs(mrcm_handle h, double* b, void* stream) {
+  if (!h || !b) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "mrcm_factor_local has not completed");
+  CK(h, cudaMemcpyAsync(b, at<double>(h, h->lay.b), 8 * ncell(h), cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* ux, double* uy, double* uz,
+                             mrcm_result* result, void* stream) {
+  if (!h || !p || !result) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "mrcm_factor_local has not completed");
+  (void)uz;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout& L = h->lay;
+  const size_t n = ncell(h);
+  const int m = h->prm.restart, ldh = m + 1;
+  Geo g = geo(h);
+  const double* bb = b ? b : at<double>(h, L.b);
+  double* V = at<double>(h, L.V);
+  double* Z = at<double>(h, L.Z);
+  double* w = at<double>(h, L.w);
+  double* Hs = at<double>(h, L.Hs);
+  double* H = Hs;
+  double* cs = H + (size_t)ldh * m;
+  double* sn = cs + m;
+  double* gv = sn + m;
+  double* out = gv + (m + 1);        // [0..3]
+  double* wn2 = out + 4;
+  double* beta_d = wn2 + 1;
+  double* bnorm_d = beta_d + 1;
+  double* partials = at<double>(h, L.red);
+  unsigned* counter = reinterpret_cast<unsigned*>(partials + 4 * RED_BLOCKS);
+  std::vector<double> hist;
+  result->iterations = 0;
+  result->restarts = 0;
+  result->status = MRCM_OK;
+  double hb[2] = {0, 0};
+  CK(h, launch_norm2(bb, n, partials, counter, bnorm_d, st));
+  CK(h, cudaMemcpyAsync(hb, bnorm_d, 8, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const double bnorm = hb[0];
+  result->bnorm = bnorm;
+  const bool rel = h->prm.tol_relative != 0;
+  if (rel && bnorm == 0.0) {
+    CK(h, cudaMemsetAsync(p, 0, 8 * n, st));
+    result->abs_res = result->rel_res = 0.0;
+    result->history_len = 0;
+    if (ux || uy) {
+      const double* bcp[4];
+      bc_ptrs(h, bcp);
+      CK(h, launch_fluxes(g, h->bc_kind, bcp, p, ux, uy, st));
+    }
+    CK(h, cudaStreamSynchronize(st));
+    return MRCM_OK;
+  }
+  const double tol_abs = rel ? h->prm.tol * bnorm : h->prm.tol;
+  CK(h, launch_residual_norm(g, bb, p, V, partials, counter, beta_d, st));
+  double beta = 0.0;
+  CK(h, cudaMemcpyAsync(&beta, beta_d, 8, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  hist.push_back(beta);
+  int it = 0;
+  mrcm_status status = MRCM_OK;
+  while (true) {
+    if (beta <= tol_abs) break;
+    if (it >= h->prm.max_iter) {
+      status = MRCM_ERR_NOT_CONVERGED;
+      break;
+    }
+    CK(h, launch_scale(V, beta_d, n, V, st));
+    CK(h, cudaMemsetAsync(gv, 0, 8 * (m + 1), st));
+    k_set<<<1, 1, 0, st>>>(gv, beta);
+    CK(h, cudaGetLastError());
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* zj = Z + (size_t)j * n;
+      mrcm_status rc = apply_T(h, vj, zj, st);
+      if (rc != MRCM_OK) return rc;
+      ++it;
+      double* col = H + (size_t)j * ldh;
+      {
+        Phase ph(h, MRCM_PH_KRYLOV, st);
+        CK(h, launch_matvec_dot(g, zj, V, w, partials, counter, col, st));
+        // launch_matvec_dot writes (w, v0) to col[0] and ||w||^2 to col[1]; move the latter
+        CK(h, cudaMemcpyAsync(wn2, col + 1, 8, cudaMemcpyDeviceToDevice, st));
+        for (int i = 1; i <= j; ++i)
+          CK(h, launch_mgs_pass(V + (size_t)(i - 1) * n, col + (i - 1), V + (size_t)i * n, n, w, partials, counter,
+                                col + i, 0, st));
+        CK(h, launch_mgs_pass(V + (size_t)j * n, col + j, nullptr, n, w, partials, counter, col + j + 1, 1, st));
+        CK(h, launch_givens(H, cs, sn, gv, j, ldh, wn2, out, st));
+      }
+      double ho[3];
+      CK(h, cudaMemcpyAsync(ho, out, 24, cudaMemcpyDeviceToHost, st));
+      CK(h, cudaStreamSynchronize(st));
+      hist.push_back(ho[0]);
+      k = j + 1;
+      const bool breakdown = ho[1] <= 1e-14 * ho[2];
+      if (ho[0] <= tol_abs || breakdown || it >= h->prm.max_iter) break;
+      CK(h, launch_scale(w, col + j + 1, n, V + (size_t)(j + 1) * n, st));
+    }
+    CK(h, launch_update(p, Z, n, H, gv, k, ldh, st));
+    CK(h, launch_residual_norm(g, bb, p, V, partials, counter, beta_d, st));
+    CK(h, cudaMemcpyAsync(&beta, beta_d, 8, cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    hist.push_back(beta);
+    if (beta <= tol_abs) break;
+    if (it >= h->prm.max_iter) {
+      status = MRCM_ERR_NOT_CONVERGED;
+      break;
+    }
+    result->restarts++;
+  }
+  if (ux || uy) {
+    const double* bcp[4];
+    bc_ptrs(h, bcp);
+    CK(h, launch_fluxes(g, h->bc_kind, bcp, p, ux, uy, st));
+    CK(h, cudaStreamSynchronize(st));
+  }
+  result->iterations = it;
+  result->status = status;
+  result->abs_res = beta;
+  result->rel_res = bnorm > 0 ? beta / bnorm : 0.0;
+  const int cap = result->history ? result->history_cap : 0;
+  const int nh = (int)hist.size();
+  for (int i = 0; i < nh && i < cap; ++i) result->history[i] = hist[i];
+  result->history_len = nh < cap ? nh : cap;
+  if (status != MRCM_OK) fail(h, status, "max_iter reached before the tolerance");
+  return status;
+}
+
+mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host, mrcm_result* result, void* stream) {
+  if (!h || !p_host || !result) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n = ncell(h);
+  if (K_host) CK(h, cudaMemcpyAsync(at<double>(h, h->lay.K), K_host, 8 * n, cudaMemcpyHostToDevice, st));
+  mrcm_status rc = mrcm_factor_local(h, stream);
+  if (rc != MRCM_OK) return rc;
+  double* p = at<double>(h, h->lay.tmpv);
+  CK(h, cudaMemsetAsync(p, 0, 8 * n, st));
+  rc = mrcm_gmres_solve(h, nullptr, p, nullptr, nullptr, nullptr, result, stream);
+  if (rc != MRCM_OK && rc != MRCM_ERR_NOT_CONVERGED) return rc;
+  CK(h, cudaMemcpyAsync(p_host, p, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return rc;
+}
+
+void mrcm_destroy(mrcm_handle h) { delete h; }
+
+int64_t mrcm_launch_count(void) { return g_launches.load(); }
+
+mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable) {
+  if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
+  h->prof = enable != 0;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int32_t cap, int32_t reset, void* stream) {
+  if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
+  CK(h, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float t = 0.f;
+    CK(h, cudaEventElapsedTime(&t, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+    h->ph_ms[h->ev_phase[i]] += t;
+  }
+  h->ev_used = 0;
+  const int nc = cap < MRCM_PHASES ? cap : MRCM_PHASES;
+  for (int i = 0; i < nc; ++i) {
+    if (ms) ms[i] = h->ph_ms[i];
+    if (launches) launches[i] = h->ph_launch[i];
+  }
+  if (reset)
+    for (int i = 0; i < MRCM_PHASES; ++i) {
+      h->ph_ms[i] = 0.0;
+      h->ph_launch[i] = 0;
+    }
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_debug_get(mrcm_handle h, int32_t what, double* host_out, size_t cap, size_t* len, void* stream) {
+  if (!h || !len) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Layout& L = h->lay;
+  const Plan& P = h->plan;
+  const size_t n = ncell(h);
+  size_t off = 0, cnt = 0;
+  switch (what) {
+    case MRCM_DBG_TRANS: {
+      const size_t nx = h->n[0], ny = h->n[1];
+      *len = (nx + 1) * ny + nx * (ny + 1);
+      if (!host_out) return MRCM_OK;
+      const size_t c1 = std::min(cap, (nx + 1) * ny);
+      CK(h, cudaMemcpyAsync(host_out, at<double>(h, L.Tx), 8 * c1, cudaMemcpyDeviceToHost, st));
+      if (cap > c1)
+        CK(h, cudaMemcpyAsync(host_out + c1, at<double>(h, L.Ty), 8 * std::min(cap - c1, nx * (ny + 1)), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaStreamSynchronize(st));
+      return MRCM_OK;
+    }
+    case MRCM_DBG_PHI: off = L.phi; cnt = (size_t)P.S * 16 * L.smax; break;
+    case MRCM_DBG_PSI: off = L.psi; cnt = 4 * n; break;
+    case MRCM_DBG_MOMENTS: off = L.mom; cnt = (size_t)P.S * 32; break;
+    case MRCM_DBG_COARSE: off = L.gc; cnt = P.E2; break;
+    case MRCM_DBG_ZMRCM:
+      if (!host_out) {
+        h->keep_z0 = true;  // capture the multiscale solution from now on
+        *len = n;
+        return MRCM_OK;
+      }
+      off = L.z0;
+      cnt = n;
+      break;
+    case MRCM_DBG_G: {
+      const size_t E2 = P.E2;
+      *len = E2 * E2;
+      if (!host_out) return MRCM_OK;
+      std::vector<double> mom((size_t)P.S * 32);
+      CK(h, cudaMemcpyAsync(mom.data(), at<double>(h, L.mom), 8 * mom.size(), cudaMemcpyDeviceToHost, st));
+      CK(h, cudaStreamSynchronize(st));
+      std::vector<double> G(E2 * E2, 0.0);
+      for (int e = 0; e < P.E; ++e) {
+        const int a = P.iface[3 * e], s = P.iface[3 * e + 1], s2 = P.iface[3 * e + 2];
+        for (int r = 0; r < 4; ++r) {
+          if (P.rank[6 * s + r] >= 0) {
+            const size_t col = P.off[s] + P.rank[6 * s + r];
+            G[(2 * e) * E2 + col] += mom[(((size_t)s * 4 + 2 * a + 1) * 4 + r) * 2];
+            G[(2 * e + 1) * E2 + col] += mom[(((size_t)s * 4 + 2 * a + 1) * 4 + r) * 2 + 1];
+          }
+          if (P.rank[6 * s2 + r] >= 0) {
+            const size_t col = P.off[s2] + P.rank[6 * s2 + r];
+            G[(2 * e) * E2 + col] += mom[(((size_t)s2 * 4 + 2 * a) * 4 + r) * 2];
+            G[(2 * e + 1) * E2 + col] -= mom[(((size_t)s2 * 4 + 2 * a) * 4 + r) * 2 + 1];
+          }
+        }
+      }
+      std::memcpy(host_out, G.data(), 8 * std::min(cap, G.size()));
+      return MRCM_OK;
+    }
+    default: return fail(h, MRCM_ERR_INVALID_ARG, "unknown debug array");
+  }
+  *len = cnt;
+  if (!host_out) return MRCM_OK;
+  CK(h, cudaMemcpyAsync(host_out, h->ws + off, 8 * std::min(cap, cnt), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return MRCM_OK;
+}
+
+}  // extern "C"

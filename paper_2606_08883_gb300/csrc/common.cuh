@@ -1,0 +1,75 @@
+// Device helpers shared by the libmrcm kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace mrcm {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over a block (blockDim.x multiple of 32, <= 1024).  Every thread receives the total.
+// Deterministic: fixed order for a fixed block size.
+__device__ __forceinline__ double block_sum(double v, double* smem32) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) smem32[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = lane < nw ? smem32[lane] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+
+// Grid-wide deterministic reduction of NV values per thread.  Each block writes its partial sums
+// to partials[v * gridDim.x + blockIdx.x]; the last block to finish (atomic ticket) adds the
+// partials in block order and writes *outs[v] (the square root for entries with the sqrt bit set
+// in sqrt_mask); the ticket counter is reset for the next launch.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], double* partials, unsigned* counter,
+                                            double* const (&outs)[NV], double* smem32, int sqrt_mask = 0) {
+  __shared__ bool last;
+  for (int k = 0; k < NV; ++k) {
+    double t = block_sum(v[k], smem32);
+    if (threadIdx.x == 0) partials[k * gridDim.x + blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned ticket = atomicAdd(counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int k = 0; k < NV; ++k) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      acc += *((volatile double*)&partials[k * gridDim.x + b]);
+    double t = block_sum(acc, smem32);
+    if (threadIdx.x == 0) *outs[k] = ((sqrt_mask >> k) & 1) ? sqrt(t) : t;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Two-point-flux pieces (Sec. 3): half transmissibility tau = 2 K |f| / h_a.
+__device__ __forceinline__ double half_trans(double k, double area, double ha) { return 2.0 * k * area / ha; }
+
+// Robin face coefficient t_R = (1/tau_in + beta/|f|)^-1, beta = alpha H / K_H (Eq. 5-6).
+__device__ __forceinline__ double robin_tr(double k_in, double k_out, double area, double ha, double Hs,
+                                           double alpha, double* beta_out, double* tau_out) {
+  const double tau = half_trans(k_in, area, ha);
+  const double kh = 2.0 * k_in * k_out / (k_in + k_out);
+  const double beta = alpha * Hs / kh;
+  if (beta_out) *beta_out = beta;
+  if (tau_out) *tau_out = tau;
+  return 1.0 / (1.0 / tau + beta / area);
+}
+
+}  // namespace mrcm

@@ -1,0 +1,181 @@
+// Internal declarations of libmrcm: host plan, workspace layout, handle, kernel launchers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mrcm.h"
+
+#include <cuda_runtime_api.h>
+
+namespace mrcm {
+
+// ------------------------------------------------------------------------------------------
+// Host plan: partition and coupling-system numbering (MRCM-OS step 1), integer only.
+// ------------------------------------------------------------------------------------------
+struct Plan {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  int sub[3] = {1, 1, 1};
+  int m[3] = {1, 1, 1};     // subdomains per axis
+  int l = 0;
+  int S = 0;                // subdomains
+  int E = 0;                // interfaces
+  int E2 = 0;               // coarse unknowns = 2E
+  std::vector<int> box;     // [S][6] lo[3] hi[3]
+  std::vector<int> obox;    // [S][6] oversampled box clipped to the grid
+  std::vector<int> mask;    // [S] Robin side bits
+  std::vector<int> N;       // [S]
+  std::vector<int> off;     // [S] first coarse unknown
+  std::vector<int> rank;    // [S][6] rank among the Robin sides, -1 if not Robin
+  std::vector<int> iface;   // [E][3] axis, lower s, upper s
+  // coupling rows in the banded "home" order: the flux row of interface e sits at the unknown of
+  // the lower subdomain's +axis side, the pressure row at the upper subdomain's -axis side
+  std::vector<int> row_home;   // [2E] canonical row -> banded row
+  int kl = 0, ku = 0;          // band widths of G in the banded order
+};
+
+// Returns an empty string on success, else the reason the input is invalid.
+std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& plan);
+std::vector<int32_t> export_plan(const Plan& plan);
+
+// ------------------------------------------------------------------------------------------
+// Workspace layout (byte offsets, 256-byte aligned).
+// ------------------------------------------------------------------------------------------
+struct Layout {
+  size_t K, Tx, Ty, b, f, bcv;            // problem data (bcv: 4 side arrays in 2-D)
+  size_t Linv_loc, Linv_ohat_r, Linv_ohat_d;   // line-block inverse factors
+  size_t phi, psi, mom, psi0, z0, mom0;   // informed spaces, basis, side moments, apply scratch
+  size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
+  size_t rho, zt;                         // smoothing residual, apply output scratch
+  size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
+  size_t tab;                             // device copies of the plan tables
+  size_t total;
+  // sizes
+  int wl, wo;             // line width of the Omega and hat-Omega boxes
+  int hl, ho;             // line count (box height)
+  int LSl, LSo;           // packed line-block stride (elements) for each box kind
+  int ldab;               // leading dimension of the coupling band
+  int smax;               // max(sub0, sub1)
+  int m;                  // restart length
+  int nred;               // reduction partial count
+  size_t elt;             // bytes per local-factor element
+};
+Layout make_layout(const Plan& plan, const mrcm_params& q);
+
+// ------------------------------------------------------------------------------------------
+// Device-side geometry passed by value to kernels (2-D).
+// ------------------------------------------------------------------------------------------
+struct Geo {
+  int nx, ny;
+  int sx, sy;              // subdomain size
+  int mx, my;              // subdomain counts
+  int l;                   // oversampling
+  int smax;
+  double hx, hy, hz;
+  double alpha;
+  const double* K;
+  const double* Tx;        // ny x (nx+1)
+  const double* Ty;        // (ny+1) x nx
+};
+
+// ------------------------------------------------------------------------------------------
+// Device scratch for deterministic reductions: per-block partials + a completion counter.
+// ------------------------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 608;   // 152 SMs x 4
+constexpr int RED_THREADS = 256;
+
+// flag word bits (device status)
+enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4 };
+
+}  // namespace mrcm
+
+// The handle.
+struct mrcm_ctx {
+  mrcm::Plan plan;
+  mrcm::Layout lay;
+  mrcm_params prm;
+  int dim;
+  int n[3];
+  double h[3];
+  int bc_kind[6];
+  int has_bc[6];
+  int has_f;
+  char* ws;           // workspace base (device)
+  size_t ws_bytes;
+  bool factored = false;
+  std::string err;
+  int coarse_n;       // 2E
+  std::vector<int> tab_host;  // plan tables uploaded to the device
+  bool keep_z0 = false;       // keep the last multiscale solution for debug reads
+  // phase profiler
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;   // phase of each recorded (start, stop) pair, in pool order
+  size_t ev_used = 0;          // pairs recorded since the last read
+  double ph_ms[MRCM_PHASES] = {0};
+  long long ph_launch[MRCM_PHASES] = {0};
+  ~mrcm_ctx() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+};
+
+namespace mrcm {
+void count_launch(int kernels);
+// kernel launchers (k_*.cu)
+cudaError_t launch_assemble(const Geo& g, const int* bc_kind, const double* const* bcv, const double* f,
+                            double* Tx, double* Ty, double* b, cudaStream_t st);
+cudaError_t launch_matvec(const Geo& g, const double* v, double* w, cudaStream_t st);
+cudaError_t launch_residual(const Geo& g, const double* r, const double* z, double* rho, cudaStream_t st);
+cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const* bcv, const double* p,
+                          double* ux, double* uy, cudaStream_t st);
+
+// local factor / solve (k_local.cu)
+enum BoxKind : int { BOX_OMEGA_ROBIN = 0, BOX_OHAT_ROBIN = 1, BOX_OHAT_DIRICHLET = 2 };
+cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
+                          cudaStream_t st);
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, cudaStream_t st);
+cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
+                         double* mom, cudaStream_t st);
+cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
+                              double* mom0, cudaStream_t st);
+cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* rho, double* z,
+                           cudaStream_t st);
+cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
+                               const double* c, double* z, cudaStream_t st);
+size_t factor_smem_bytes(int w, bool fp32);
+
+// coupling system (k_coarse.cu)
+struct CoarseDev {
+  int n;            // 2E
+  int kl, ku, ldab;
+  double* ab;       // band LU storage, column-major, ldab x n
+  int* ipiv;
+  double* g;        // rhs / solution (banded row order in, canonical unknowns out)
+  const int* iface; // [E][3]
+  const int* home;  // [2E] canonical row -> banded row
+  const int* off;   // [S]
+  const int* rank;  // [S][6]
+};
+cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st);
+cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st);
+cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
+cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st);
+
+// Krylov helpers (k_krylov.cu)
+cudaError_t launch_norm2(const double* x, size_t n, double* partials, unsigned* counter, double* out,
+                         cudaStream_t st);
+cudaError_t launch_scale(const double* x, const double* denom, size_t n, double* y, cudaStream_t st);
+cudaError_t launch_matvec_dot(const Geo& g, const double* z, const double* v0, double* w, double* partials,
+                              unsigned* counter, double* out2, cudaStream_t st);
+cudaError_t launch_mgs_pass(const double* vprev, const double* hprev, const double* vnext, size_t n, double* w,
+                            double* partials, unsigned* counter, double* hout, int want_norm, cudaStream_t st);
+cudaError_t launch_givens(double* H, double* cs, double* sn, double* gv, int j, int ldh, double* hnorm0,
+                          double* out, cudaStream_t st);
+cudaError_t launch_update(double* p, const double* Z, size_t n, const double* H, const double* gv, int k, int ldh,
+                          cudaStream_t st);
+cudaError_t launch_residual_norm(const Geo& g, const double* b, const double* p, double* r, double* partials,
+                                 unsigned* counter, double* out, cudaStream_t st);
+}  // namespace mrcm

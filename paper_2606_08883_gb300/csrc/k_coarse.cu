@@ -1,0 +1,190 @@
+// Coupling system of MRCM-O (Eq. 13-14) with piecewise-constant M_H, V_H on each interface.
+//
+// Unknowns c_{s,k}: one per Robin side of each subdomain (canonical order: subdomain, then side).
+// Rows: per interface e = (axis a, lower s, upper s'), the flux row
+//   sum_f F_s(f) + F_s'(f) = 0  and the pressure row  sum_f |f| (P_s(f) - P_s'(f)) = 0,
+// with the side moments of the basis traces (from the basis solves) as coefficients and the
+// particular traces as right-hand side.  Rows are placed at a "home" position next to the unknowns
+// they mostly depend on (flux row at (s, +a), pressure row at (s', -a)), which makes G banded with
+// half-bandwidth about 4 m_x; it is factored by band LU with partial pivoting (row interchanges
+// only) in LAPACK band layout: A(i, j) at ab[kv + i - j + j * ldab], kv = kl + ku, ldab = 2 kl + ku + 1.
+#include "common.cuh"
+
+namespace mrcm {
+
+// G entries from the side moments mom[s][side][function][F, |f|P]; ab must be zeroed.
+__global__ void k_coarse_assemble(CoarseDev c, const double* __restrict__ mom, int E) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int kv = c.kl + c.ku;
+  const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
+  const int rf = c.home[2 * e], rp = c.home[2 * e + 1];
+  const int ks = 2 * a + 1, ks2 = 2 * a;  // +a side of s, -a side of s'
+  for (int r = 0; r < 4; ++r) {
+    const int q = c.rank[6 * s + r];
+    if (q >= 0) {
+      const int col = c.off[s] + q;
+      c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = mom[(((size_t)s * 4 + ks) * 4 + r) * 2];
+      c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = mom[(((size_t)s * 4 + ks) * 4 + r) * 2 + 1];
+    }
+    const int q2 = c.rank[6 * s2 + r];
+    if (q2 >= 0) {
+      const int col = c.off[s2] + q2;
+      c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = mom[(((size_t)s2 * 4 + ks2) * 4 + r) * 2];
+      c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = -mom[(((size_t)s2 * 4 + ks2) * 4 + r) * 2 + 1];
+    }
+  }
+}
+
+__global__ void k_coarse_rhs(CoarseDev c, const double* __restrict__ mom0, int E) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
+  const int ks = 2 * a + 1, ks2 = 2 * a;
+  const double F = mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2];
+  const double P = mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1];
+  c.g[c.home[2 * e]] = -F;
+  c.g[c.home[2 * e + 1]] = -P;
+}
+
+// Unblocked band LU with partial pivoting, one CTA.
+__global__ void __launch_bounds__(512) k_gbtf2(CoarseDev c, int* flags) {
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  double* ab = c.ab;
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_jp, s_ju, s_ok;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  int ju = 0;
+  for (int j = 0; j < n; ++j) {
+    const int km = min(kl, n - 1 - j);
+    // pivot: first index of the largest magnitude in column j, rows j..j+km
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i <= km; i += nt) {
+      const double v = fabs(ab[(size_t)(kv + i) + (size_t)j * ld]);
+      if (v > best || (v == best && i < bi)) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[wid] = best;
+      si[wid] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b2 = -1.0;
+      int i2 = 0x7fffffff;
+      for (int w = 0; w < nt / 32; ++w)
+        if (sv[w] > b2 || (sv[w] == b2 && si[w] < i2)) {
+          b2 = sv[w];
+          i2 = si[w];
+        }
+      const double piv = ab[(size_t)(kv + i2) + (size_t)j * ld];
+      s_ok = (piv != 0.0 && isfinite(piv)) ? 1 : 0;
+      if (!s_ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
+      s_jp = i2;
+      c.ipiv[j] = j + i2;
+      s_ju = max(ju, min(j + ku + i2, n - 1));
+    }
+    __syncthreads();
+    const int jp = s_jp;
+    if (!s_ok) {
+      __syncthreads();
+      continue;
+    }
+    ju = s_ju;
+    if (jp != 0) {
+      for (int col = j + tid; col <= ju; col += nt) {
+        double* a1 = ab + (size_t)(kv + j - col) + (size_t)col * ld;
+        double* a2 = ab + (size_t)(kv + j + jp - col) + (size_t)col * ld;
+        const double t = *a1;
+        *a1 = *a2;
+        *a2 = t;
+      }
+      __syncthreads();
+    }
+    const double piv = ab[(size_t)kv + (size_t)j * ld];
+    const double rp = 1.0 / piv;
+    for (int i = 1 + tid; i <= km; i += nt) ab[(size_t)(kv + i) + (size_t)j * ld] *= rp;
+    __syncthreads();
+    const int ncol = ju - j;
+    for (int t = tid; t < ncol * km; t += nt) {
+      const int col = j + 1 + t / km, i = 1 + t % km;
+      const double lij = ab[(size_t)(kv + i) + (size_t)j * ld];
+      const double ujc = ab[(size_t)(kv + j - col) + (size_t)col * ld];
+      ab[(size_t)(kv + j + i - col) + (size_t)col * ld] -= lij * ujc;
+    }
+    __syncthreads();
+  }
+}
+
+// Solve with the band LU factors (no transpose), one CTA; rhs in c.g, solution written back.
+__global__ void __launch_bounds__(256) k_gbtrs(CoarseDev c) {
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const double* ab = c.ab;
+  double* b = c.g;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < n; ++j) {
+    const int lm = min(kl, n - 1 - j);
+    const int l = c.ipiv[j];
+    if (tid == 0 && l != j) {
+      const double t = b[l];
+      b[l] = b[j];
+      b[j] = t;
+    }
+    __syncthreads();
+    const double bj = b[j];
+    for (int i = 1 + tid; i <= lm; i += nt) b[j + i] -= ab[(size_t)(kv + i) + (size_t)j * ld] * bj;
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    if (tid == 0) b[j] = b[j] / ab[(size_t)kv + (size_t)j * ld];
+    __syncthreads();
+    const double bj = b[j];
+    const int i0 = max(0, j - kv);
+    for (int i = i0 + tid; i < j; i += nt) b[i] -= ab[(size_t)(kv + i - j) + (size_t)j * ld] * bj;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st) {
+  if (E == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(c.ab, 0, sizeof(double) * (size_t)c.ldab * c.n, st);
+  if (e != cudaSuccess) return e;
+  k_coarse_assemble<<<(E + 127) / 128, 128, 0, st>>>(c, mom, E);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  k_gbtf2<<<1, 512, 0, st>>>(c, flags);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st) {
+  if (E == 0) return cudaSuccess;
+  k_coarse_rhs<<<(E + 127) / 128, 128, 0, st>>>(c, mom0, E);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  k_gbtrs<<<1, 256, 0, st>>>(c);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mrcm

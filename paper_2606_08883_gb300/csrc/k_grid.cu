@@ -1,0 +1,184 @@
+// Fine-grid kernels (Sec. 3): face transmissibilities and b, the matrix-free operator A v, the
+// residual r - A z and the face velocities.  Two-point flux form of the statically condensed RT0
+// system; 2-D, cells x-fastest, one thread per cell or face, coalesced along x.
+#include "common.cuh"
+
+namespace mrcm {
+
+struct BcDev {
+  int kind[4];
+  const double* val[4];   // NULL = zero data
+};
+
+__global__ void k_trans_x(Geo g, BcDev bc, double* Tx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // face index along x, 0..nx
+  const int j = blockIdx.y;
+  if (i > g.nx || j >= g.ny) return;
+  const double area = g.hy * g.hz;
+  const double* K = g.K + (size_t)j * g.nx;
+  double t;
+  if (i == 0) {
+    t = bc.kind[0] == MRCM_BC_DIRICHLET ? half_trans(K[0], area, g.hx) : 0.0;
+  } else if (i == g.nx) {
+    t = bc.kind[1] == MRCM_BC_DIRICHLET ? half_trans(K[g.nx - 1], area, g.hx) : 0.0;
+  } else {
+    const double tl = half_trans(K[i - 1], area, g.hx), tr = half_trans(K[i], area, g.hx);
+    t = 1.0 / (1.0 / tl + 1.0 / tr);
+  }
+  Tx[(size_t)j * (g.nx + 1) + i] = t;
+}
+
+__global__ void k_trans_y(Geo g, BcDev bc, double* Ty) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;  // face index along y, 0..ny
+  if (i >= g.nx || j > g.ny) return;
+  const double area = g.hx * g.hz;
+  double t;
+  if (j == 0) {
+    t = bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(g.K[i], area, g.hy) : 0.0;
+  } else if (j == g.ny) {
+    t = bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(g.K[(size_t)(g.ny - 1) * g.nx + i], area, g.hy) : 0.0;
+  } else {
+    const double tl = half_trans(g.K[(size_t)(j - 1) * g.nx + i], area, g.hy);
+    const double tr = half_trans(g.K[(size_t)j * g.nx + i], area, g.hy);
+    t = 1.0 / (1.0 / tl + 1.0 / tr);
+  }
+  Ty[(size_t)j * g.nx + i] = t;
+}
+
+// b = f + sum over Dirichlet faces of tau g - sum over Neumann faces of |f| z.
+__global__ void k_rhs(Geo g, BcDev bc, const double* f, double* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const size_t c = (size_t)j * g.nx + i;
+  double v = f ? f[c] : 0.0;
+  const double k = g.K[c];
+  const double ax = g.hy * g.hz, ay = g.hx * g.hz;
+  // same side order as the oracle: x sides, then y sides
+  if (i == 0 && bc.val[0]) v += bc.kind[0] == MRCM_BC_DIRICHLET ? half_trans(k, ax, g.hx) * bc.val[0][j] : -(ax * bc.val[0][j]);
+  if (i == g.nx - 1 && bc.val[1]) v += bc.kind[1] == MRCM_BC_DIRICHLET ? half_trans(k, ax, g.hx) * bc.val[1][j] : -(ax * bc.val[1][j]);
+  if (j == 0 && bc.val[2]) v += bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(k, ay, g.hy) * bc.val[2][i] : -(ay * bc.val[2][i]);
+  if (j == g.ny - 1 && bc.val[3]) v += bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(k, ay, g.hy) * bc.val[3][i] : -(ay * bc.val[3][i]);
+  b[c] = v;
+}
+
+__device__ __forceinline__ double apply_A(const Geo& g, const double* __restrict__ v, int i, int j) {
+  const size_t c = (size_t)j * g.nx + i;
+  const double vc = v[c];
+  const double vw = i > 0 ? v[c - 1] : 0.0;
+  const double ve = i < g.nx - 1 ? v[c + 1] : 0.0;
+  const double vs = j > 0 ? v[c - g.nx] : 0.0;
+  const double vn = j < g.ny - 1 ? v[c + g.nx] : 0.0;
+  const double* Tx = g.Tx + (size_t)j * (g.nx + 1) + i;
+  const double* Ty = g.Ty + (size_t)j * g.nx + i;
+  const double wx = Tx[1] * (vc - ve) - Tx[0] * (vw - vc);
+  const double wy = Ty[g.nx] * (vc - vn) - Ty[0] * (vs - vc);
+  return wx + wy;
+}
+
+__global__ void k_matvec(Geo g, const double* __restrict__ v, double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= g.nx) return;
+  w[(size_t)j * g.nx + i] = apply_A(g, v, i, j);
+}
+
+__global__ void k_residual(Geo g, const double* __restrict__ r, const double* __restrict__ z, double* __restrict__ rho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= g.nx) return;
+  const size_t c = (size_t)j * g.nx + i;
+  rho[c] = r[c] - apply_A(g, z, i, j);
+}
+
+// Face velocities u_f (positive along +axis).
+__global__ void k_flux_x(Geo g, BcDev bc, const double* __restrict__ p, double* __restrict__ ux) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i > g.nx) return;
+  const double area = g.hy * g.hz;
+  const double T = g.Tx[(size_t)j * (g.nx + 1) + i];
+  const double* pr = p + (size_t)j * g.nx;
+  double u;
+  if (i == 0) {
+    if (bc.kind[0] == MRCM_BC_DIRICHLET) u = T * ((bc.val[0] ? bc.val[0][j] : 0.0) - pr[0]) / area;
+    else u = -(bc.val[0] ? bc.val[0][j] : 0.0);
+  } else if (i == g.nx) {
+    if (bc.kind[1] == MRCM_BC_DIRICHLET) u = T * (pr[g.nx - 1] - (bc.val[1] ? bc.val[1][j] : 0.0)) / area;
+    else u = bc.val[1] ? bc.val[1][j] : 0.0;
+  } else {
+    u = T * (pr[i - 1] - pr[i]) / area;
+  }
+  ux[(size_t)j * (g.nx + 1) + i] = u;
+}
+
+__global__ void k_flux_y(Geo g, BcDev bc, const double* __restrict__ p, double* __restrict__ uy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= g.nx) return;
+  const double area = g.hx * g.hz;
+  const double T = g.Ty[(size_t)j * g.nx + i];
+  double u;
+  if (j == 0) {
+    if (bc.kind[2] == MRCM_BC_DIRICHLET) u = T * ((bc.val[2] ? bc.val[2][i] : 0.0) - p[i]) / area;
+    else u = -(bc.val[2] ? bc.val[2][i] : 0.0);
+  } else if (j == g.ny) {
+    if (bc.kind[3] == MRCM_BC_DIRICHLET) u = T * (p[(size_t)(g.ny - 1) * g.nx + i] - (bc.val[3] ? bc.val[3][i] : 0.0)) / area;
+    else u = bc.val[3] ? bc.val[3][i] : 0.0;
+  } else {
+    u = T * (p[(size_t)(j - 1) * g.nx + i] - p[(size_t)j * g.nx + i]) / area;
+  }
+  uy[(size_t)j * g.nx + i] = u;
+}
+
+static BcDev make_bc(const int* kind, const double* const* val) {
+  BcDev b;
+  for (int s = 0; s < 4; ++s) {
+    b.kind[s] = kind[s];
+    b.val[s] = val[s];
+  }
+  return b;
+}
+
+static dim3 row_grid(int cols, int rows, int threads) { return dim3((cols + threads - 1) / threads, rows); }
+
+cudaError_t launch_assemble(const Geo& g, const int* bc_kind, const double* const* bcv, const double* f, double* Tx,
+                            double* Ty, double* b, cudaStream_t st) {
+  const BcDev bc = make_bc(bc_kind, bcv);
+  k_trans_x<<<row_grid(g.nx + 1, g.ny, 128), 128, 0, st>>>(g, bc, Tx);
+  count_launch(1);
+  k_trans_y<<<row_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(g, bc, Ty);
+  count_launch(1);
+  k_rhs<<<row_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, bc, f, b);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(const Geo& g, const double* v, double* w, cudaStream_t st) {
+  k_matvec<<<row_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, v, w);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Geo& g, const double* r, const double* z, double* rho, cudaStream_t st) {
+  k_residual<<<row_grid(g.nx, g.ny, 128), 128, 0, st>>>(g, r, z, rho);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const* bcv, const double* p, double* ux,
+                          double* uy, cudaStream_t st) {
+  const BcDev bc = make_bc(bc_kind, bcv);
+  if (ux) {
+    k_flux_x<<<row_grid(g.nx + 1, g.ny, 128), 128, 0, st>>>(g, bc, p, ux);
+    count_launch(1);
+  }
+  if (uy) {
+    k_flux_y<<<row_grid(g.nx, g.ny + 1, 128), 128, 0, st>>>(g, bc, p, uy);
+    count_launch(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mrcm

@@ -1,0 +1,604 @@
+// Local Robin / Dirichlet problems on subdomain boxes (Eq. 5-6, Eq. 11-12, Eq. 15) and the
+// overlapping-Schwarz local solves.  One CTA per subdomain.
+//
+// A box of width w (x) and height h (lines along x, x fastest) has a block-tridiagonal operator:
+// tridiagonal line blocks D_J and diagonal couplings -E_J between lines J-1 and J.  Its Cholesky
+// factor is block bidiagonal with L_{J,J-1} = -E_J L_{J-1}^-T, so only the inverse diagonal
+// blocks Linv_J = L_JJ^-1 are stored (packed lower triangle, one line block per line):
+//   factor  S_0 = D_0, S_J = D_J - E_J (Linv_{J-1}^T Linv_{J-1}) E_J, L_JJ = chol(S_J)
+//   forward y_J = Linv_J (b_J + E_J Linv_{J-1}^T y_{J-1})
+//   back    x_J = Linv_J^T (y_J + Linv_J E_{J+1} x_{J+1})
+// Each solve streams every line block once forward and once backward (cp.async double buffer),
+// with four threads per row in the triangular matrix-vector products.
+//
+// Oversampled boxes are padded to the full (sub + 2l)^2 size; cells outside the grid get identity
+// rows with zero couplings and zero data, which leaves the clipped region's solution unchanged.
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace mrcm {
+
+struct Box {
+  int ox, oy, w, h;
+};
+
+__device__ __forceinline__ Box box_of(const Geo& g, int s, bool ohat) {
+  const int I = s % g.mx, J = s / g.mx;
+  Box b;
+  const int l = ohat ? g.l : 0;
+  b.ox = I * g.sx - l;
+  b.oy = J * g.sy - l;
+  b.w = g.sx + 2 * l;
+  b.h = g.sy + 2 * l;
+  return b;
+}
+
+__device__ __forceinline__ bool active(const Geo& g, int gx, int gy) {
+  return gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
+}
+
+__device__ __forceinline__ double Kc(const Geo& g, int gx, int gy) { return g.K[(size_t)gy * g.nx + gx]; }
+
+// Robin coefficient t_R of the face between (gx, gy) inside and its neighbour along axis a / dir.
+__device__ __forceinline__ double face_tr(const Geo& g, int gx, int gy, int a, int dir, double* beta, double* tau) {
+  const int nx2 = gx + (a == 0 ? dir : 0), ny2 = gy + (a == 1 ? dir : 0);
+  const double area = a == 0 ? g.hy * g.hz : g.hx * g.hz;
+  const double ha = a == 0 ? g.hx : g.hy;
+  const double Hs = a == 0 ? g.sx * g.hx : g.sy * g.hy;
+  return robin_tr(Kc(g, gx, gy), Kc(g, nx2, ny2), area, ha, Hs, g.alpha, beta, tau);
+}
+
+// Line-block coefficients at local (x, J): diagonal, coupling to x+1 (value T, entry -T),
+// coupling to line J-1 (value T, entry -T).
+__device__ __forceinline__ void line_coeffs(const Geo& g, const Box& b, bool robin, int J, int x, double& diag,
+                                            double& offr, double& eup) {
+  const int gx = b.ox + x, gy = b.oy + J;
+  if (!active(g, gx, gy)) {
+    diag = 1.0;
+    offr = 0.0;
+    eup = 0.0;
+    return;
+  }
+  const double* Tx = g.Tx + (size_t)gy * (g.nx + 1);
+  const double tw = Tx[gx], te = Tx[gx + 1];
+  const double ts = g.Ty[(size_t)gy * g.nx + gx], tn = g.Ty[(size_t)(gy + 1) * g.nx + gx];
+  double d = (tw + te) + (ts + tn);
+  if (robin) {
+    if (x == 0 && gx - 1 >= 0) d += face_tr(g, gx, gy, 0, -1, nullptr, nullptr) - tw;
+    if (x == b.w - 1 && gx + 1 < g.nx) d += face_tr(g, gx, gy, 0, +1, nullptr, nullptr) - te;
+    if (J == 0 && gy - 1 >= 0) d += face_tr(g, gx, gy, 1, -1, nullptr, nullptr) - ts;
+    if (J == b.h - 1 && gy + 1 < g.ny) d += face_tr(g, gx, gy, 1, +1, nullptr, nullptr) - tn;
+  }
+  diag = d;
+  offr = (x + 1 < b.w && active(g, gx + 1, gy)) ? te : 0.0;
+  eup = (J > 0 && active(g, gx, gy - 1)) ? ts : 0.0;
+}
+
+// packed lower-triangle row index of linear position k (row i holds i+1 entries)
+__device__ __forceinline__ int tri_row(int k) {
+  int i = (int)((sqrtf(8.0f * (float)k + 1.0f) - 1.0f) * 0.5f);
+  while (i * (i + 1) / 2 > k) --i;
+  while ((i + 1) * (i + 2) / 2 <= k) ++i;
+  return i;
+}
+
+// ============================================================================================
+// Factor: one CTA per subdomain box; dense w x w working arrays in shared memory.
+// ============================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __restrict__ Linv, int* flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = blockIdx.x;
+  const bool ohat = kind != BOX_OMEGA_ROBIN;
+  const bool robin = kind != BOX_OHAT_DIRICHLET;
+  const Box b = box_of(g, s, ohat);
+  const int w = b.w;
+  T* Sm = reinterpret_cast<T*>(smem_raw);  // Schur complement, then inverse work rows
+  T* Lm = Sm + w * w;                      // Cholesky factor of the line block
+  T* Lc = Lm + w * w;                      // Linv of the current line
+  T* Lp = Lc + w * w;                      // Linv of the previous line
+  T* ev = Lp + w * w;                      // couplings to the previous line
+  T* rinv = ev + w;                        // reciprocal diagonal of Lm
+  __shared__ int bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) bad = 0;
+  T* out = Linv + (size_t)s * b.h * LS;
+  const int npk = w * (w + 1) / 2;
+  for (int J = 0; J < b.h; ++J) {
+    // (1) S_J = D_J - E_J (Lp^T Lp) E_J, lower triangle
+    for (int i = tid; i < w; i += nt) {
+      double d, o, e;
+      line_coeffs(g, b, robin, J, i, d, o, e);
+      ev[i] = (T)e;
+      Sm[i * w + i] = (T)d;
+      if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
+    }
+    __syncthreads();
+    for (int k = tid; k < npk; k += nt) {
+      const int i = tri_row(k), j = k - i * (i + 1) / 2;
+      T v = (i == j || i == j + 1) ? Sm[i * w + j] : (T)0;
+      if (J > 0) {
+        T acc = 0;
+        for (int r = i; r < w; ++r) acc += Lp[r * w + i] * Lp[r * w + j];
+        v -= ev[i] * ev[j] * acc;
+      }
+      Sm[i * w + j] = v;
+    }
+    __syncthreads();
+    // (2) Cholesky of S_J: right-looking, column k of L written to Lm, trailing update in Sm
+    for (int k = 0; k < w; ++k) {
+      if (tid == 0) {
+        T p = Sm[k * w + k];
+        if (!(p > (T)0) || !isfinite((double)p)) {
+          bad = 1;
+          p = (T)1;
+        }
+        const T d = sqrt(p);
+        Lm[k * w + k] = d;
+        rinv[k] = (T)1 / d;
+      }
+      __syncthreads();
+      const T rd = rinv[k];
+      const int m = w - k - 1;
+      for (int i = tid; i < m; i += nt) Lm[(k + 1 + i) * w + k] = Sm[(k + 1 + i) * w + k] * rd;
+      const int nup = m * (m + 1) / 2;
+      for (int t = tid; t < nup; t += nt) {
+        const int ii = tri_row(t), jj = t - ii * (ii + 1) / 2;
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        Sm[i * w + j] -= (Sm[i * w + k] * rd) * (Sm[j * w + k] * rd);
+      }
+      __syncthreads();
+    }
+    // (3) Lc = Lm^-1 by right-looking elimination on the identity (work rows in Sm)
+    for (int k = tid; k < w * w; k += nt) {
+      const int i = k / w, j = k % w;
+      Sm[k] = (i == j) ? (T)1 : (T)0;
+    }
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+      const T rk = rinv[k];
+      for (int c = tid; c <= k; c += nt) Lc[k * w + c] = Sm[k * w + c] * rk;
+      const int rows = w - k - 1, cols = k + 1;
+      for (int t = tid; t < rows * cols; t += nt) {
+        const int i = k + 1 + t / cols, c = t % cols;
+        Sm[i * w + c] -= Lm[i * w + k] * (Sm[k * w + c] * rk);
+      }
+      __syncthreads();
+    }
+    // (4) store packed, keep as previous line
+    for (int k = tid; k < npk; k += nt) {
+      const int i = tri_row(k), j = k - i * (i + 1) / 2;
+      const T v = Lc[i * w + j];
+      out[(size_t)J * LS + k] = v;
+    }
+    for (int k = tid; k < w * w; k += nt) Lp[k] = Lc[k];
+    __syncthreads();
+  }
+  if (tid == 0 && bad) atomicOr(flags, FLAG_SINGULAR_LOCAL);
+}
+
+size_t factor_smem_bytes(int w, bool fp32) {
+  const size_t e = fp32 ? 4 : 8;
+  return e * (4 * (size_t)w * w + 2 * (size_t)w) + 16;
+}
+
+cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
+                          cudaStream_t st) {
+  (void)hgt;
+  const int S = g.mx * g.my;
+  const size_t sm = factor_smem_bytes(w, fp32);
+  if (fp32) {
+    cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_factor<float><<<S, 256, sm, st>>>(g, kind, LS, (float*)Linv, flags);
+    count_launch(1);
+  } else {
+    cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_factor<double><<<S, 256, sm, st>>>(g, kind, LS, (double*)Linv, flags);
+    count_launch(1);
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================================================
+// Solve: forward / backward sweeps over the line blocks, with mode-specific data in and out.
+// ============================================================================================
+enum SolveMode : int { MODE_INFORMED = 0, MODE_BASIS = 1, MODE_PARTICULAR = 2, MODE_SCHWARZ = 3 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void fetch_line(T* dst, const T* src, int LS) {
+  const int nch = LS * (int)sizeof(T) / 16;
+  for (int c = threadIdx.x; c < nch; c += blockDim.x)
+    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * c, reinterpret_cast<const unsigned char*>(src) + 16 * c);
+  cp_async_commit();
+}
+
+// out[i][r] = sum_{c <= i} L[i][c] in[c][r]  (lower) -- 4 threads per row, rows < w
+template <typename T, int NR>
+__device__ __forceinline__ void gemv_lower(const T* L, const T* in, T* out, int w, bool accumulate) {
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = 0;
+  if (i < w) {
+    const T* row = L + i * (i + 1) / 2;
+    for (int c = q; c <= i; c += 4) {
+      const T lv = row[c];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] += lv * in[c * NR + r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
+  }
+  if (i < w && q == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[i * NR + r] = accumulate ? out[i * NR + r] + acc[r] : acc[r];
+  }
+}
+
+// out[c][r] = sum_{i >= c} L[i][c] in[i][r]  (upper = transpose of the packed lower)
+template <typename T, int NR>
+__device__ __forceinline__ void gemv_upper(const T* L, const T* in, T* out, int w) {
+  const int c = threadIdx.x >> 2, q = threadIdx.x & 3;
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = 0;
+  if (c < w) {
+    for (int i = c + q; i < w; i += 4) {
+      const T lv = L[i * (i + 1) / 2 + c];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] += lv * in[i * NR + r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
+  }
+  if (c < w && q == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[c * NR + r] = acc[r];
+  }
+}
+
+// coupling value (T > 0) between local lines J-1 and J at x, 0 if absent
+__device__ __forceinline__ double couple_up(const Geo& g, const Box& b, int J, int x) {
+  const int gx = b.ox + x, gy = b.oy + J;
+  if (J <= 0 || J >= b.h || !active(g, gx, gy) || !active(g, gx, gy - 1)) return 0.0;
+  return g.Ty[(size_t)gy * g.nx + gx];
+}
+
+struct SolveArgs {
+  const void* Linv;
+  int LS;
+  const double* in;    // particular: r; schwarz: rho; basis: phi
+  double* out;         // particular: psi0; schwarz: z; basis: psi; informed: phi
+  double* mom;         // particular: mom0 [S][4][2]; basis: mom [S][4][4][2]
+};
+
+// Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.
+__device__ __forceinline__ void gamma_face(const Geo& g, int s, int k, int t, int& gx, int& gy, int& ox2, int& oy2,
+                                           double& Tf) {
+  const int I = s % g.mx, J = s / g.mx;
+  const int x0 = I * g.sx, y0 = J * g.sy;
+  switch (k) {
+    case 0: gx = x0; gy = y0 + t; ox2 = gx - 1; oy2 = gy; Tf = g.Tx[(size_t)gy * (g.nx + 1) + x0]; break;
+    case 1: gx = x0 + g.sx - 1; gy = y0 + t; ox2 = gx + 1; oy2 = gy; Tf = g.Tx[(size_t)gy * (g.nx + 1) + x0 + g.sx]; break;
+    case 2: gx = x0 + t; gy = y0; ox2 = gx; oy2 = gy - 1; Tf = g.Ty[(size_t)y0 * g.nx + gx]; break;
+    default: gx = x0 + t; gy = y0 + g.sy - 1; ox2 = gx; oy2 = gy + 1; Tf = g.Ty[(size_t)(y0 + g.sy) * g.nx + gx]; break;
+  }
+}
+
+__device__ __forceinline__ bool robin_side(const Geo& g, int s, int k) {
+  const int I = s % g.mx, J = s / g.mx;
+  switch (k) {
+    case 0: return I > 0;
+    case 1: return I < g.mx - 1;
+    case 2: return J > 0;
+    default: return J < g.my - 1;
+  }
+}
+
+template <typename T, int MODE, int NR>
+__global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = blockIdx.x;
+  const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
+  const Box b = box_of(g, s, ohat);
+  const int w = b.w, hgt = b.h, LS = a.LS;
+  T* Lb0 = reinterpret_cast<T*>(smem_raw);
+  T* Lb1 = Lb0 + LS;
+  T* Y = Lb1 + LS;                 // [hgt][w][NR]
+  T* tv = Y + (size_t)hgt * w * NR; // [w][NR]
+  T* vv = tv + w * NR;              // [w][NR]
+  __shared__ double red[8][4][2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * hgt * LS;
+  fetch_line(Lb0, Lg, LS);  // overlap the first line block with the right-hand side set-up
+
+  // ---------------- right-hand sides into Y
+  for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
+  __syncthreads();
+  if (MODE == MODE_PARTICULAR || MODE == MODE_SCHWARZ) {
+    for (int k = tid; k < hgt * w; k += nt) {
+      const int J = k / w, x = k % w;
+      const int gx = b.ox + x, gy = b.oy + J;
+      if (active(g, gx, gy)) Y[k * NR] = (T)a.in[(size_t)gy * g.nx + gx];
+    }
+  } else if (MODE == MODE_INFORMED) {
+    // lambda^r = 1 on the faces of Robin side r of the oversampled box
+    for (int r = 0; r < 4; ++r) {
+      if (!robin_side(g, s, r)) continue;
+      const int len = (r < 2) ? hgt : w;
+      for (int t = tid; t < len; t += nt) {
+        int x, J, ax, dir;
+        switch (r) {
+          case 0: x = 0; J = t; ax = 0; dir = -1; break;
+          case 1: x = w - 1; J = t; ax = 0; dir = +1; break;
+          case 2: x = t; J = 0; ax = 1; dir = -1; break;
+          default: x = t; J = hgt - 1; ax = 1; dir = +1; break;
+        }
+        const int gx = b.ox + x, gy = b.oy + J;
+        if (!active(g, gx, gy)) continue;
+        Y[(J * w + x) * NR + r] += (T)face_tr(g, gx, gy, ax, dir, nullptr, nullptr);
+      }
+      __syncthreads();
+    }
+  } else {  // MODE_BASIS: t_R phi^r on the Gamma faces of each Robin side
+    for (int k = 0; k < 4; ++k) {
+      if (!robin_side(g, s, k)) continue;
+      const int len = (k < 2) ? g.sy : g.sx;
+      for (int t = tid; t < len; t += nt) {
+        int gx, gy, ox2, oy2;
+        double Tf;
+        gamma_face(g, s, k, t, gx, gy, ox2, oy2, Tf);
+        const double tr = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, nullptr, nullptr);
+        const int x = gx - b.ox, J = gy - b.oy;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const double ph = a.in[(((size_t)s * 4 + r) * 4 + k) * g.smax + t];
+          Y[(J * w + x) * NR + r] += (T)(tr * ph);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+
+  // ---------------- forward sweep
+  for (int J = 0; J < hgt; ++J) {
+    T* L = (J & 1) ? Lb1 : Lb0;
+    if (J + 1 < hgt) {
+      fetch_line((J & 1) ? Lb0 : Lb1, Lg + (size_t)(J + 1) * LS, LS);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    for (int k = tid; k < w * NR; k += nt) {
+      const int x = k / NR;
+      T v = Y[(size_t)J * w * NR + k];
+      if (J > 0) v += (T)couple_up(g, b, J, x) * vv[k];
+      tv[k] = v;
+    }
+    __syncthreads();
+    gemv_lower<T, NR>(L, tv, Y + (size_t)J * w * NR, w, false);
+    __syncthreads();
+    if (J + 1 < hgt) gemv_upper<T, NR>(L, Y + (size_t)J * w * NR, vv, w);
+    __syncthreads();
+  }
+  // ---------------- backward sweep
+  fetch_line(Lb0, Lg + (size_t)(hgt - 1) * LS, LS);
+  for (int J = hgt - 1, it = 0; J >= 0; --J, ++it) {
+    T* L = (it & 1) ? Lb1 : Lb0;
+    if (J > 0) {
+      fetch_line((it & 1) ? Lb0 : Lb1, Lg + (size_t)(J - 1) * LS, LS);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    T* yJ = Y + (size_t)J * w * NR;
+    if (J + 1 < hgt) {
+      const T* xn = Y + (size_t)(J + 1) * w * NR;
+      for (int k = tid; k < w * NR; k += nt) {
+        const int x = k / NR;
+        tv[k] = (T)couple_up(g, b, J + 1, x) * xn[k];
+      }
+      __syncthreads();
+      gemv_lower<T, NR>(L, tv, yJ, w, true);  // y_J + Linv_J E x_{J+1}
+      __syncthreads();
+    }
+    gemv_upper<T, NR>(L, yJ, vv, w);
+    __syncthreads();
+    for (int k = tid; k < w * NR; k += nt) yJ[k] = vv[k];
+    __syncthreads();
+  }
+
+  // ---------------- outputs
+  const int lane = tid & 31, wid = tid >> 5;
+  if (MODE == MODE_PARTICULAR) {
+    for (int k = tid; k < hgt * w; k += nt) {
+      const int J = k / w, x = k % w;
+      a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+    }
+    if (wid < 4) {
+      const int kside = wid;
+      double F = 0.0, Pw = 0.0;
+      if (robin_side(g, s, kside)) {
+        const int len = (kside < 2) ? g.sy : g.sx;
+        for (int t = lane; t < len; t += 32) {
+          int gx, gy, ox2, oy2;
+          double Tf, beta;
+          gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
+          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
+          const double fl = tr * (double)Y[(gy - b.oy) * w + (gx - b.ox)];
+          F += fl;
+          Pw += beta * fl;
+        }
+      }
+      F = warp_sum(F);
+      Pw = warp_sum(Pw);
+      if (lane == 0) {
+        a.mom[(size_t)s * 8 + kside * 2] = F;
+        a.mom[(size_t)s * 8 + kside * 2 + 1] = Pw;
+      }
+    }
+  } else if (MODE == MODE_SCHWARZ) {
+    for (int k = tid; k < g.sx * g.sy; k += nt) {
+      const int y = k / g.sx, x = k % g.sx;
+      const int gx = b.ox + g.l + x, gy = b.oy + g.l + y;
+      a.out[(size_t)gy * g.nx + gx] += (double)Y[(g.l + y) * w + g.l + x];
+    }
+  } else if (MODE == MODE_BASIS) {
+    for (int k = tid; k < hgt * w * NR; k += nt) {
+      const int r = k % NR, c = k / NR, J = c / w, x = c % w;
+      a.out[(size_t)r * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+    }
+    // moments: 16 (side, function) pairs over 8 warps
+    for (int pr = wid; pr < 16; pr += 8) {
+      const int kside = pr / 4, r = pr % 4;
+      double F = 0.0, Pw = 0.0;
+      if (robin_side(g, s, kside)) {
+        const int len = (kside < 2) ? g.sy : g.sx;
+        for (int t = lane; t < len; t += 32) {
+          int gx, gy, ox2, oy2;
+          double Tf, beta;
+          gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
+          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
+          const double ph = a.in[(((size_t)s * 4 + r) * 4 + kside) * g.smax + t];
+          const double fl = tr * ((double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r] - ph);
+          const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
+          F += fl;
+          Pw += area * ph + beta * fl;
+        }
+      }
+      F = warp_sum(F);
+      Pw = warp_sum(Pw);
+      if (lane == 0) {
+        a.mom[(((size_t)s * 4 + kside) * 4 + r) * 2] = F;
+        a.mom[(((size_t)s * 4 + kside) * 4 + r) * 2 + 1] = Pw;
+      }
+    }
+  } else {  // MODE_INFORMED: phi_s^r on every Gamma face
+    for (int k = 0; k < 4; ++k) {
+      const int len = (k < 2) ? g.sy : g.sx;
+      const bool rs = robin_side(g, s, k);
+      for (int t = tid; t < len * NR; t += nt) {
+        const int r = t % NR, f = t / NR;
+        double ph = 0.0;
+        if (rs && robin_side(g, s, r)) {
+          int gx, gy, ox2, oy2;
+          double Tf, beta, tau;
+          gamma_face(g, s, k, f, gx, gy, ox2, oy2, Tf);
+          face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, &beta, &tau);
+          const double qc = (double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r];
+          const double qo = (double)Y[((oy2 - b.oy) * w + (ox2 - b.ox)) * NR + r];
+          const double F = Tf * (qc - qo);
+          const double pi = qc - F / tau;
+          const double area = k < 2 ? g.hy * g.hz : g.hx * g.hz;
+          ph = -beta * F / area + pi;
+        }
+        a.out[(((size_t)s * 4 + r) * 4 + k) * g.smax + f] = ph;
+      }
+    }
+  }
+  (void)red;
+}
+
+template <typename T, int MODE, int NR>
+static cudaError_t run_solve(const Geo& g, const SolveArgs& a, bool ohat) {
+  return cudaSuccess;
+}
+
+template <typename T, int MODE, int NR>
+static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
+  const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
+  const size_t sm = sizeof(T) * (2 * (size_t)a.LS + (size_t)h * w * NR + 2 * (size_t)w * NR) + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_solve<T, MODE, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_solve<T, MODE, NR><<<g.mx * g.my, 256, sm, st>>>(g, a);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <int MODE, int NR>
+static cudaError_t launch_solve(const Geo& g, const SolveArgs& a, bool ohat, bool fp32, cudaStream_t st) {
+  return fp32 ? launch_solve_t<float, MODE, NR>(g, a, ohat, st) : launch_solve_t<double, MODE, NR>(g, a, ohat, st);
+}
+
+__global__ void k_phi_indicator(Geo g, double* phi) {
+  const int s = blockIdx.x;
+  for (int t = threadIdx.x; t < 16 * g.smax; t += blockDim.x) {
+    const int r = t / (4 * g.smax), k = (t / g.smax) % 4, f = t % g.smax;
+    const int len = (k < 2) ? g.sy : g.sx;
+    double v = 0.0;
+    if (r == k && f < len && robin_side(g, s, k)) v = 1.0;
+    phi[(size_t)s * 16 * g.smax + t] = v;
+  }
+}
+
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, cudaStream_t st) {
+  if (g.l == 0) {
+    k_phi_indicator<<<g.mx * g.my, 128, 0, st>>>(g, phi);
+    count_launch(1);
+    return cudaGetLastError();
+  }
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr};
+  return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
+}
+
+cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
+                         double* mom, cudaStream_t st) {
+  SolveArgs a{Linv, LS, phi, psi, mom};
+  return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
+}
+
+cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
+                              double* mom0, cudaStream_t st) {
+  SolveArgs a{Linv, LS, r, psi0, mom0};
+  return launch_solve<MODE_PARTICULAR, 1>(g, a, false, fp32, st);
+}
+
+cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* rho, double* z,
+                           cudaStream_t st) {
+  SolveArgs a{Linv, LS, rho, z, nullptr};
+  return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
+}
+
+// z = psi0 + sum over Robin sides k of c_{s,k} psi_k   (reconstruction, per cell)
+__global__ void k_reconstruct(Geo g, const double* __restrict__ psi0, const double* __restrict__ psi,
+                              const int* __restrict__ cidx, const double* __restrict__ c, double* __restrict__ z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= g.nx) return;
+  const int s = (j / g.sy) * g.mx + i / g.sx;
+  const size_t cell = (size_t)j * g.nx + i;
+  const size_t n = (size_t)g.nx * g.ny;
+  double v = psi0[cell];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int ci = cidx[s * 4 + k];
+    if (ci >= 0) v += c[ci] * psi[k * n + cell];
+  }
+  z[cell] = v;
+}
+
+cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* cidx, const double* c,
+                               double* z, cudaStream_t st) {
+  k_reconstruct<<<dim3((g.nx + 127) / 128, g.ny), 128, 0, st>>>(g, psi0, psi, cidx, c, z);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mrcm

@@ -1,0 +1,216 @@
+// Host planner: validation, partition and coupling numbering (MRCM-OS step 1, Sec. 2.1), workspace
+// layout.  Integer work only; the tables it exports match the oracle's bit for bit.
+#include <algorithm>
+#include <cmath>
+#include <sstream>
+
+#include "internal.h"
+
+namespace mrcm {
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
+  std::ostringstream why;
+  if (p.dim != 2 && p.dim != 3) return "dim must be 2 or 3";
+  for (int a = 0; a < 3; ++a) {
+    if (p.n[a] < 1) return "grid sizes must be >= 1";
+    if (!finite_pos(p.h[a])) return "cell sizes must be positive and finite";
+    if (q.sub[a] < 1 || p.n[a] % q.sub[a] != 0) return "subdomain size must divide the grid on every axis";
+  }
+  if (p.dim == 2 && (p.n[2] != 1 || q.sub[2] != 1)) return "2-D problems need n[2] == 1 and sub[2] == 1";
+  if ((long long)p.n[0] * p.n[1] * p.n[2] > (1LL << 31) - 1) return "grid too large";
+  for (int a = 0; a < p.dim; ++a)
+    if (q.oversample < 0 || q.oversample >= q.sub[a]) return "oversampling must satisfy 0 <= l < sub on every axis";
+  if (q.oversample < 0) return "oversampling must be >= 0";
+  if (q.smooth_steps < 0) return "smooth_steps must be >= 0";
+  if (!finite_pos(q.alpha)) return "alpha must be positive and finite";
+  if (!finite_pos(q.tol)) return "tol must be positive and finite";
+  if (q.restart < 1 || q.restart > 256) return "restart must be in 1..256";
+  if (q.max_iter < 1) return "max_iter must be >= 1";
+  if (q.local_prec != MRCM_PREC_FP64 && q.local_prec != MRCM_PREC_FP32) return "local_prec must be FP64 or FP32";
+  bool any_dirichlet = false;
+  for (int s = 0; s < 6; ++s) {
+    if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";
+    if (s / 2 < p.dim && p.bc_kind[s] == MRCM_BC_DIRICHLET) any_dirichlet = true;
+  }
+  if (!any_dirichlet) return "at least one Dirichlet side is required (pure Neumann is singular)";
+
+  P = Plan();
+  P.dim = p.dim;
+  for (int a = 0; a < 3; ++a) {
+    P.n[a] = p.n[a];
+    P.sub[a] = q.sub[a];
+    P.m[a] = p.n[a] / q.sub[a];
+  }
+  P.l = q.oversample;
+  P.S = P.m[0] * P.m[1] * P.m[2];
+  const int S = P.S;
+  P.box.assign(6 * S, 0);
+  P.obox.assign(6 * S, 0);
+  P.mask.assign(S, 0);
+  P.N.assign(S, 0);
+  P.off.assign(S, 0);
+  P.rank.assign(6 * S, -1);
+  std::vector<int> coord(3 * S);
+  for (int s = 0; s < S; ++s) {
+    const int idx[3] = {s % P.m[0], (s / P.m[0]) % P.m[1], s / (P.m[0] * P.m[1])};
+    for (int a = 0; a < 3; ++a) {
+      coord[3 * s + a] = idx[a];
+      const int lo = idx[a] * P.sub[a], hi = lo + P.sub[a];
+      P.box[6 * s + a] = lo;
+      P.box[6 * s + 3 + a] = hi;
+      if (a < P.dim) {
+        P.obox[6 * s + a] = std::max(lo - P.l, 0);
+        P.obox[6 * s + 3 + a] = std::min(hi + P.l, P.n[a]);
+        if (idx[a] > 0) P.mask[s] |= 1 << (2 * a);
+        if (idx[a] < P.m[a] - 1) P.mask[s] |= 1 << (2 * a + 1);
+      } else {
+        P.obox[6 * s + a] = lo;
+        P.obox[6 * s + 3 + a] = hi;
+      }
+    }
+    int r = 0;
+    for (int k = 0; k < 6; ++k)
+      if (P.mask[s] >> k & 1) P.rank[6 * s + k] = r++;
+    P.N[s] = r;
+  }
+  int acc = 0;
+  for (int s = 0; s < S; ++s) {
+    P.off[s] = acc;
+    acc += P.N[s];
+  }
+  P.E2 = acc;
+  const int stride[3] = {1, P.m[0], P.m[0] * P.m[1]};
+  for (int a = 0; a < P.dim; ++a)
+    for (int s = 0; s < S; ++s)
+      if (coord[3 * s + a] < P.m[a] - 1) {
+        P.iface.push_back(a);
+        P.iface.push_back(s);
+        P.iface.push_back(s + stride[a]);
+      }
+  P.E = (int)P.iface.size() / 3;
+  if (2 * P.E != P.E2) return "internal: coupling system is not square";
+  // banded home order and band widths of G
+  P.row_home.assign(P.E2, 0);
+  P.kl = P.ku = 0;
+  for (int e = 0; e < P.E; ++e) {
+    const int a = P.iface[3 * e], s = P.iface[3 * e + 1], s2 = P.iface[3 * e + 2];
+    const int rf = P.off[s] + P.rank[6 * s + 2 * a + 1];
+    const int rp = P.off[s2] + P.rank[6 * s2 + 2 * a];
+    P.row_home[2 * e] = rf;
+    P.row_home[2 * e + 1] = rp;
+    for (int row : {rf, rp}) {
+      for (int t : {s, s2}) {
+        const int c0 = P.off[t], c1 = P.off[t] + P.N[t] - 1;
+        P.kl = std::max(P.kl, row - c0);
+        P.ku = std::max(P.ku, c1 - row);
+      }
+    }
+  }
+  return std::string();
+}
+
+std::vector<int32_t> export_plan(const Plan& P) {
+  std::vector<int32_t> out = {P.dim, P.n[0], P.n[1], P.n[2], P.sub[0], P.sub[1], P.sub[2], P.l, P.S, P.E2, P.E};
+  for (int s = 0; s < P.S; ++s) {
+    for (int t = 0; t < 6; ++t) out.push_back(P.box[6 * s + t]);
+    for (int t = 0; t < 6; ++t) out.push_back(P.obox[6 * s + t]);
+    out.push_back(P.mask[s]);
+    out.push_back(P.N[s]);
+    out.push_back(P.off[s]);
+  }
+  for (int e = 0; e < P.E; ++e)
+    for (int t = 0; t < 3; ++t) out.push_back(P.iface[3 * e + t]);
+  // face arrays: axis a has n[a] + 1 entries along a
+  long long ext[3][3], size[3];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) ext[a][b] = P.n[b] + (a == b ? 1 : 0);
+    size[a] = ext[a][0] * ext[a][1] * ext[a][2];
+  }
+  const long long aoff[3] = {0, size[0], size[0] + size[1]};
+  for (int s = 0; s < P.S; ++s) {
+    const int* lo = &P.box[6 * s];
+    const int* hi = &P.box[6 * s + 3];
+    for (int k = 0; k < 6; ++k) {
+      if (!(P.mask[s] >> k & 1)) continue;
+      const int a = k / 2, d = k % 2;
+      int others[2], t = 0;
+      for (int b = 0; b < 3; ++b)
+        if (b != a) others[t++] = b;
+      const int b1 = others[0], b2 = others[1];
+      const int plane = d == 0 ? lo[a] : hi[a];
+      out.push_back((hi[b1] - lo[b1]) * (hi[b2] - lo[b2]));
+      for (int t2 = lo[b2]; t2 < hi[b2]; ++t2)
+        for (int t1 = lo[b1]; t1 < hi[b1]; ++t1) {
+          long long pos[3];
+          pos[a] = plane;
+          pos[b1] = t1;
+          pos[b2] = t2;
+          out.push_back((int32_t)(aoff[a] + pos[0] + ext[a][0] * (pos[1] + ext[a][1] * pos[2])));
+        }
+    }
+  }
+  return out;
+}
+
+static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(const Plan& P, const mrcm_params& q) {
+  Layout L{};
+  const size_t nx = P.n[0], ny = P.n[1];
+  const size_t n = nx * ny * P.n[2];
+  const size_t S = P.S;
+  L.elt = q.local_prec == MRCM_PREC_FP32 ? 4 : 8;
+  L.wl = P.sub[0];
+  L.hl = P.sub[1];
+  L.wo = P.sub[0] + 2 * P.l;
+  L.ho = P.sub[1] + 2 * P.l;
+  auto packed = [](int w) { return ((w * (w + 1) / 2) + 3) / 4 * 4; };
+  L.LSl = packed(L.wl);
+  L.LSo = packed(L.wo);
+  L.ldab = 2 * P.kl + P.ku + 1;
+  L.smax = std::max(P.sub[0], P.sub[1]);
+  L.m = q.restart;
+  L.nred = RED_BLOCKS;
+  const size_t E2 = P.E2;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = al(o + std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.K = take(8 * n);
+  L.Tx = take(8 * (nx + 1) * ny);
+  L.Ty = take(8 * nx * (ny + 1));
+  L.b = take(8 * n);
+  L.f = take(8 * n);
+  L.bcv = take(8 * 4 * std::max(nx, ny));
+  L.Linv_loc = take(L.elt * S * L.hl * L.LSl);
+  L.Linv_ohat_r = take(P.l > 0 ? L.elt * S * L.ho * L.LSo : 0);
+  L.Linv_ohat_d = take(q.smooth_steps > 0 ? L.elt * S * L.ho * L.LSo : 0);
+  L.phi = take(8 * S * 16 * L.smax);
+  L.psi = take(8 * 4 * n);
+  L.mom = take(8 * S * 32);
+  L.psi0 = take(8 * n);
+  L.z0 = take(8 * n);
+  L.mom0 = take(8 * S * 8);
+  L.G = take(8 * (size_t)L.ldab * E2);
+  L.ipiv = take(4 * E2);
+  L.gc = take(8 * E2);
+  L.rho = take(8 * n);
+  L.zt = take(8 * n);
+  L.V = take(8 * (size_t)(L.m + 1) * n);
+  L.Z = take(8 * (size_t)L.m * n);
+  L.w = take(8 * n);
+  L.Hs = take(8 * ((size_t)(L.m + 1) * L.m + 4 * (L.m + 1) + 64));
+  L.red = take(8 * 4 * RED_BLOCKS + 64);
+  L.flags = take(4 * 64);
+  L.tmpv = take(8 * n);
+  // device copies of the plan tables: iface[3E], home[2E], off[S], rank[6S], coff[S]
+  L.tab = take(4 * (3 * P.E + E2 + S + 6 * S + S + 16));
+  L.total = o;
+  return L;
+}
+
+}  // namespace mrcm

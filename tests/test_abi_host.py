@@ -1,0 +1,81 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol include/mrcm.h declares,
+and its host planner (MRCM-OS step 1) matches the oracle's integer tables bit for bit.  No compute
+entry point is called here."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.partition import Partition
+from paper_2606_08883_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_08883_gb300 import build
+    build.build()
+    from paper_2606_08883_gb300 import mrcm
+    return mrcm
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mrcm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrcm_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib._lib, name), name
+        assert name in lib.EXPORTED, name
+
+
+@pytest.mark.parametrize("n,sub,l", [((24, 16, 1), (8, 8, 1), 2), ((64, 64, 1), (16, 16, 1), 4),
+                                     ((40, 24, 1), (8, 12, 1), 7), ((10, 10, 1), (10, 10, 1), 0),
+                                     ((12, 8, 4), (4, 4, 2), 1)])
+def test_plan_export_matches_oracle_bit_exactly(lib, n, sub, l):
+    dim = 3 if n[2] > 1 else 2
+    prob = W.random_problem(n, dim=dim, seed=0)
+    q = W.Params(sub=sub, oversample=l)
+    got = lib.plan_export(prob, q)
+    want = Partition(dim, n, sub, l).export()
+    assert got.dtype == want.dtype and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("bad", [dict(sub=(5, 8, 1)), dict(oversample=8), dict(oversample=-1), dict(alpha=0.0),
+                                 dict(tol=-1.0), dict(restart=0), dict(max_iter=0), dict(local_prec=7)])
+def test_invalid_parameters_rejected(lib, bad):
+    prob = W.random_problem((24, 16, 1), seed=0)
+    kw = dict(sub=(8, 8, 1), oversample=2)
+    kw.update(bad)
+    with pytest.raises(lib.MRCMError) as ei:
+        lib.plan_export(prob, W.Params(**kw))
+    assert ei.value.status == lib.MRCM_ERR_INVALID_ARG
+
+
+def test_pure_neumann_rejected_and_3d_unsupported(lib):
+    prob = W.random_problem((16, 16, 1), seed=0, bc_kind=[1, 1, 1, 1, 1, 1])
+    with pytest.raises(lib.MRCMError) as ei:
+        lib.footprint(prob, W.Params(sub=(8, 8, 1)))
+    assert ei.value.status == lib.MRCM_ERR_INVALID_ARG
+    prob3 = W.random_problem((8, 8, 4), dim=3, seed=0)
+    with pytest.raises(lib.MRCMError) as ei:
+        lib.footprint(prob3, W.Params(sub=(4, 4, 2), oversample=1))
+    assert ei.value.status == lib.MRCM_ERR_UNSUPPORTED
+
+
+def test_footprint_grows_with_restart_and_smoothing(lib):
+    prob, params = W.channels(128, sub=32)
+    a = lib.footprint(prob, params)
+    params.restart = 60
+    b = lib.footprint(prob, params)
+    assert b > a and a % 256 == 0 and b % 256 == 0
+    params.smooth_steps = 0
+    c = lib.footprint(prob, params)
+    assert c < b

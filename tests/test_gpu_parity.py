@@ -1,0 +1,240 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle on the same seeded inputs,
+called through the C ABI.
+
+Tolerances (FP64 path): transmissibilities and b are the same closed formulas evaluated in a
+different association order, so they agree to a few ulps (1e-14 relative).  The local solves,
+coupling solve and Krylov recurrences use different (but backward-stable) elimination orders
+(block-line Cholesky and band LU on the GPU, LAPACK band Cholesky and dense LU in the oracle), so
+agreement is bounded by eps times the condition numbers involved: 1e-10 relative L2 on the
+moderate-contrast fields (K spread 1e3) used here, with iteration counts equal.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import grid
+from oracle.mrcm import MRCMOS
+from oracle.solve import solve as oracle_solve
+from paper_2606_08883_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mrcm():
+    from paper_2606_08883_gb300 import mrcm as m
+    return m
+
+
+def _rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _oracle(prob, q):
+    return MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha)
+
+
+CASES = {
+    "mrcm-48x40": (dict(n=(48, 40, 1), seed=1), dict(sub=(8, 8, 1), oversample=0, smooth_steps=0)),
+    "os-48x40": (dict(n=(48, 40, 1), seed=2), dict(sub=(8, 8, 1), oversample=2, smooth_steps=1)),
+    "os-96x64-l4s2": (dict(n=(96, 64, 1), seed=3), dict(sub=(16, 16, 1), oversample=4, smooth_steps=2)),
+    "ragged-60x36": (dict(n=(60, 36, 1), seed=4), dict(sub=(12, 9, 1), oversample=3, smooth_steps=1)),
+    "single-32": (dict(n=(32, 32, 1), seed=5), dict(sub=(32, 32, 1), oversample=0, smooth_steps=1)),
+    "widest-64": (dict(n=(64, 64, 1), seed=6), dict(sub=(32, 32, 1), oversample=16, smooth_steps=1)),
+    "stripes-128x64": (dict(n=(128, 64, 1), seed=7), dict(sub=(4, 32, 1), oversample=3, smooth_steps=1)),
+    "dirichlet-all": (dict(n=(48, 48, 1), seed=8, bc_kind=[0, 0, 0, 0, 1, 1]),
+                      dict(sub=(16, 12, 1), oversample=2, smooth_steps=2)),
+    "neumann-data": (dict(n=(40, 40, 1), seed=9, bc_kind=[0, 1, 1, 0, 1, 1]),
+                     dict(sub=(10, 8, 1), oversample=1, smooth_steps=1)),
+}
+
+
+def _case(name):
+    pk, qk = CASES[name]
+    prob = W.random_problem(pk["n"], seed=pk["seed"], contrast=1e3, bc_kind=pk.get("bc_kind"))
+    q = W.Params(**qk)
+    q.tol = 1e-10
+    return prob, q
+
+
+@pytest.mark.parametrize("name", ["os-48x40", "ragged-60x36", "dirichlet-all", "neumann-data"])
+def test_transmissibilities_rhs_operator(mrcm, name):
+    prob, q = _case(name)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
+    tr = s.debug(mrcm.MRCM_DBG_TRANS)
+    nx, ny = prob.n[0], prob.n[1]
+    assert _rel(tr[:(nx + 1) * ny], T[0]) < 1e-14
+    assert _rel(tr[(nx + 1) * ny:], T[1]) < 1e-14
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    assert _rel(s.rhs().cpu().numpy(), b) < 1e-14
+    v = np.random.default_rng(0).standard_normal(prob.K.shape)
+    w = s.apply_operator(torch.as_tensor(v.ravel(), device="cuda")).cpu().numpy()
+    assert _rel(w, grid.matvec(T, v, 2)) < 1e-13
+
+
+def _phi_gpu_layout(pre, s_idx, smax):
+    """Oracle phi of subdomain s in the library layout [4 functions][4 sides][smax]."""
+    d = pre.subs[s_idx]
+    out = np.zeros((4, 4, smax))
+    for jj, (r, _q) in enumerate(d.funcs):
+        off = 0
+        for k in d.sides:
+            ln = int((d.gamma_side == k).sum())
+            out[r, k, :ln] = d.phi[jj, off:off + ln]
+            off += ln
+    return out
+
+
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "stripes-128x64"])
+def test_informed_spaces_basis_moments_and_coupling_matrix(mrcm, name):
+    prob, q = _case(name)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    pre = _oracle(prob, q)
+    P = pre.part
+    smax = max(q.sub[0], q.sub[1])
+    phi = s.debug(mrcm.MRCM_DBG_PHI).reshape(P.S, 4, 4, smax)
+    psi = s.debug(mrcm.MRCM_DBG_PSI).reshape(4, -1)
+    mom = s.debug(mrcm.MRCM_DBG_MOMENTS).reshape(P.S, 4, 4, 2)
+    ref_phi = np.stack([_phi_gpu_layout(pre, i, smax) for i in range(P.S)])
+    assert _rel(phi, ref_phi) < 1e-11
+    nx = prob.n[0]
+    for d in pre.subs:
+        lo, hi = P.box[d.s, 0], P.box[d.s, 1]
+        cells = (np.arange(lo[1], hi[1])[:, None] * nx + np.arange(lo[0], hi[0])[None, :]).ravel()
+        for jj, (r, _q) in enumerate(d.funcs):
+            assert _rel(psi[r, cells], d.psi[:, jj]) < 1e-10
+            for k in d.sides:
+                assert np.isclose(mom[d.s, k, r, 0], d.Fbar[k, 0, jj], rtol=1e-9, atol=1e-12 * np.abs(d.Fbar).max())
+                assert np.isclose(mom[d.s, k, r, 1], d.Pbar[k, 0, jj], rtol=1e-9, atol=1e-12 * np.abs(d.Pbar).max())
+    G = s.debug(mrcm.MRCM_DBG_G).reshape(P.E2, P.E2)
+    assert _rel(G, pre.G) < 1e-10
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_precond_matches_oracle(mrcm, name):
+    prob, q = _case(name)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+    pre = _oracle(prob, q)
+    rng = np.random.default_rng(11)
+    for trial in range(2):
+        r = rng.standard_normal(prob.K.shape)
+        z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+        parts = pre.apply_parts(r)
+        assert _rel(s.debug(mrcm.MRCM_DBG_COARSE), parts["c"]) < 1e-9 if pre.part.E2 else True
+        assert _rel(s.debug(mrcm.MRCM_DBG_ZMRCM), parts["z_mrcm"]) < 1e-10
+        assert _rel(z, parts["z"]) < 1e-10, (name, trial, _rel(z, parts["z"]))
+
+
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "dirichlet-all"])
+def test_gmres_matches_oracle(mrcm, name):
+    prob, q = _case(name)
+    q.tol = 1e-9
+    q.restart = 8
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve(fluxes=True)
+    p_ref, info_ref, pre = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                        l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                        tol_relative=True, restart=q.restart, max_iter=q.max_iter)
+    assert info["status"] == 0 and info["rel_res"] <= q.tol
+    assert info["iterations"] == info_ref["iterations"]
+    assert info["restarts"] == info_ref["restarts"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-9
+    hist_ref = np.array(info_ref["history"])
+    assert len(info["history"]) == len(hist_ref)
+    assert np.allclose(info["history"], hist_ref, rtol=1e-6, atol=1e-12 * hist_ref[0])
+    ux, uy = info["u"]
+    assert _rel(ux.cpu().numpy(), info_ref["u"][0]) < 1e-9
+    assert _rel(uy.cpu().numpy(), info_ref["u"][1]) < 1e-9
+
+
+def test_fp32_local_solves_reach_fp64_tolerance(mrcm):
+    prob, q = _case("os-96x64-l4s2")
+    q.tol = 1e-8
+    p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                      l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                      restart=q.restart)
+    q.local_prec = W.PREC_FP32
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve()
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    assert info["iterations"] <= info_ref["iterations"] + 1
+    A = grid.dense_matrix(grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind), 2, prob.K.shape) \
+        if prob.cells <= 4096 else None
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-6
+
+
+def test_edge_cases(mrcm):
+    prob, q = _case("single-32")
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve()
+    assert info["iterations"] == 1 and info["rel_res"] <= q.tol
+    zero = torch.zeros(prob.cells, dtype=torch.float64, device="cuda")
+    p0, info0 = s.solve(b=zero)
+    assert info0["iterations"] == 0 and float(p0.abs().max()) == 0.0
+    prob, q = _case("os-48x40")
+    q.max_iter = 1
+    q.tol = 1e-14
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve(allow_not_converged=True)
+    assert info["status"] == mrcm.MRCM_ERR_NOT_CONVERGED and info["iterations"] == 1
+    with pytest.raises(mrcm.MRCMError) as ei:
+        s.solve()
+    assert ei.value.status == mrcm.MRCM_ERR_NOT_CONVERGED
+    bad = W.random_problem((48, 40, 1), seed=3)
+    bad.K = bad.K.copy()
+    bad.K[0, 3, 5] = -1.0
+    s = mrcm.Solver(bad, q)
+    with pytest.raises(mrcm.MRCMError) as ei:
+        s.factor()
+    assert ei.value.status == mrcm.MRCM_ERR_INVALID_ARG
+    with pytest.raises(mrcm.MRCMError) as ei:
+        s.apply_precond(torch.zeros(bad.cells, dtype=torch.float64, device="cuda"))
+    assert ei.value.status == mrcm.MRCM_ERR_INVALID_ARG
+
+
+def test_workspace_too_small_and_deterministic(mrcm):
+    import ctypes as C
+    prob, q = _case("os-48x40")
+    need = mrcm.footprint(prob, q)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    K = torch.as_tensor(prob.K.ravel(), device="cuda")
+    p = mrcm.make_problem(prob, K.data_ptr())
+    pq = mrcm.make_params(q)
+    h = C.c_void_p()
+    rc = mrcm.mrcm_setup(C.byref(p), C.byref(pq), C.c_void_p(ws.data_ptr()), need - 256, None, C.byref(h))
+    assert rc == mrcm.MRCM_ERR_OOM
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    a, _ = s.solve()
+    b, _ = s.solve()
+    assert torch.equal(a, b)
+
+
+def test_full_size_channels_512_matches_oracle(mrcm):
+    """The 512 x 512 channelised workload (contrast 1e6) in the configuration the benchmark times."""
+    prob, q = W.channels(512, seed=1)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    pre = _oracle(prob, q)
+    r = np.random.default_rng(5).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    zr = pre.apply(r)
+    # contrast 1e6: local condition numbers reach ~1e9, so two backward-stable elimination orders
+    # agree to about eps * cond
+    assert _rel(z, zr) < 1e-6
+    p, info = s.solve()
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    A_p = grid.matvec(pre.T, p.cpu().numpy().reshape(prob.K.shape), 2)
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    assert np.linalg.norm(b - A_p) <= 1.0001e-8 * np.linalg.norm(b)
