@@ -256,7 +256,7 @@ mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, v
     for (int k = 0; k < 4; ++k) tab.push_back(P.rank[6 * s + k] >= 0 ? P.off[s] + P.rank[6 * s + k] : -1);
   h->tab_host = tab;
   cudaError_t e = cudaMemcpyAsync(at<int>(h, L.tab), h->tab_host.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(at<unsigned char>(h, L.red), 0, 8 * 4 * RED_BLOCKS + 64, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<unsigned char>(h, L.red), 0, 8 * RED_DOUBLES + 64, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<int>(h, L.flags), 0, 4 * 64, st);
   if (e != cudaSuccess) {
     g_last_error = std::string("set-up copies: ") + cudaGetErrorString(e);
@@ -322,6 +322,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
     CK(h, launch_coarse_factor(c, flags, st));
+    if (P.E2 <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
   }
   // smoothing: Dirichlet factors of the oversampled regions
   if (h->prm.smooth_steps > 0) {
@@ -352,8 +353,12 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   CoarseDev c = coarse(h);
   {
     Phase ph(h, MRCM_PH_COARSE_SOLVE, st);
-    CK(h, launch_coarse_rhs(c, at<double>(h, L.mom0), P.E, st));
-    CK(h, launch_coarse_solve(c, st));
+    if (P.E2 <= COARSE_DENSE_MAX) {
+      CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
+    } else {
+      CK(h, launch_coarse_rhs(c, at<double>(h, L.mom0), P.E, st));
+      CK(h, launch_coarse_solve(c, st));
+    }
   }
   // reconstruction
   {
@@ -418,7 +423,11 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
   double* beta_d = wn2 + 1;
   double* bnorm_d = beta_d + 1;
   double* partials = at<double>(h, L.red);
-  unsigned* counter = reinterpret_cast<unsigned*>(partials + 4 * RED_BLOCKS);
+  double* apartials = partials + 4096;
+  unsigned* counter = reinterpret_cast<unsigned*>(partials + RED_DOUBLES);
+  unsigned* bar = counter + 1;
+  int* flags = at<int>(h, L.flags);
+  bool fused = true;  // fused Arnoldi kernel, unless the vector is too long for one co-resident wave
   std::vector<double> hist;
   result->iterations = 0;
   result->restarts = 0;
@@ -470,23 +479,36 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
       double* col = H + (size_t)j * ldh;
       {
         Phase ph(h, MRCM_PH_KRYLOV, st);
-        CK(h, launch_matvec_dot(g, zj, V, w, partials, counter, col, st));
-        // launch_matvec_dot writes (w, v0) to col[0] and ||w||^2 to col[1]; move the latter
-        CK(h, cudaMemcpyAsync(wn2, col + 1, 8, cudaMemcpyDeviceToDevice, st));
-        for (int i = 1; i <= j; ++i)
-          CK(h, launch_mgs_pass(V + (size_t)(i - 1) * n, col + (i - 1), V + (size_t)i * n, n, w, partials, counter,
-                                col + i, 0, st));
-        CK(h, launch_mgs_pass(V + (size_t)j * n, col + j, nullptr, n, w, partials, counter, col + j + 1, 1, st));
-        CK(h, launch_givens(H, cs, sn, gv, j, ldh, wn2, out, st));
+        cudaError_t ea = cudaErrorNotSupported;
+        if (fused) ea = launch_arnoldi(g, zj, V, j, n, H, ldh, cs, sn, gv, out, apartials, bar, flags, st);
+        if (ea == cudaErrorNotSupported) {
+          fused = false;
+          (void)cudaGetLastError();
+          CK(h, launch_matvec_dot(g, zj, V, w, partials, counter, col, st));
+          // launch_matvec_dot writes (w, v0) to col[0] and ||w||^2 to col[1]; move the latter
+          CK(h, cudaMemcpyAsync(wn2, col + 1, 8, cudaMemcpyDeviceToDevice, st));
+          for (int i = 1; i <= j; ++i)
+            CK(h, launch_mgs_pass(V + (size_t)(i - 1) * n, col + (i - 1), V + (size_t)i * n, n, w, partials, counter,
+                                  col + i, 0, st));
+          CK(h, launch_mgs_pass(V + (size_t)j * n, col + j, nullptr, n, w, partials, counter, col + j + 1, 1, st));
+          CK(h, launch_givens(H, cs, sn, gv, j, ldh, wn2, out, st));
+        } else {
+          CK(h, ea);
+        }
       }
       double ho[3];
+      int hflag = 0;
       CK(h, cudaMemcpyAsync(ho, out, 24, cudaMemcpyDeviceToHost, st));
+      CK(h, cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
+      if (hflag & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "grid barrier in the Arnoldi step timed out");
       hist.push_back(ho[0]);
       k = j + 1;
       const bool breakdown = ho[1] <= 1e-14 * ho[2];
       if (ho[0] <= tol_abs || breakdown || it >= h->prm.max_iter) break;
-      CK(h, launch_scale(w, col + j + 1, n, V + (size_t)(j + 1) * n, st));
+      // v_{j+1} = w / h_{j+1,j} (the fused kernel writes it itself); the rotation has already
+      // zeroed col[j+1], out[1] keeps the value
+      if (!fused) CK(h, launch_scale(w, out + 1, n, V + (size_t)(j + 1) * n, st));
     }
     CK(h, launch_update(p, Z, n, H, gv, k, ldh, st));
     CK(h, launch_residual_norm(g, bb, p, V, partials, counter, beta_d, st));

@@ -49,6 +49,7 @@ struct Layout {
   size_t Linv_loc, Linv_ohat_r, Linv_ohat_d;   // line-block inverse factors
   size_t phi, psi, mom, psi0, z0, mom0;   // informed spaces, basis, side moments, apply scratch
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
+  size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
@@ -86,9 +87,14 @@ struct Geo {
 // ------------------------------------------------------------------------------------------
 constexpr int RED_BLOCKS = 608;   // 152 SMs x 4
 constexpr int RED_THREADS = 256;
+constexpr int ARNOLDI_MAX_BLOCKS = 1024;
+// reduction scratch (doubles): [0, 4096) classic partials, [4096, 8192) Arnoldi partials,
+// then unsigned counters: [0] classic ticket, [1] barrier arrivals, [2] barrier generation
+constexpr size_t RED_DOUBLES = 8192;
+constexpr int COARSE_DENSE_MAX = 4096;   // 2E up to this size: explicit G^-1, one product per apply
 
 // flag word bits (device status)
-enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4 };
+enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8 };
 
 }  // namespace mrcm
 
@@ -163,6 +169,11 @@ cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E,
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st);
 cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st);
+cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st);
+cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);
+cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
+                           double* sn, double* gv, double* out, double* partials, unsigned* bar, int* flags,
+                           cudaStream_t st);
 
 // Krylov helpers (k_krylov.cu)
 cudaError_t launch_norm2(const double* x, size_t n, double* partials, unsigned* counter, double* out,

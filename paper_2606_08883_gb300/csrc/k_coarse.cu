@@ -157,6 +157,79 @@ __global__ void __launch_bounds__(256) k_gbtrs(CoarseDev c) {
   }
 }
 
+// Columns of G^-1 (banded row order in, canonical unknowns out): block j solves L U x = P e_j.
+// Written row-major, Ginv[i * n + j], so that the per-apply product reads rows contiguously.
+__global__ void __launch_bounds__(128) k_gbtrs_cols(CoarseDev c, double* __restrict__ Ginv) {
+  extern __shared__ double b[];
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const double* ab = c.ab;
+  const int col = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) b[i] = (i == col) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int lm = min(kl, n - 1 - j);
+    const int l = c.ipiv[j];
+    if (tid == 0 && l != j) {
+      const double t = b[l];
+      b[l] = b[j];
+      b[j] = t;
+    }
+    __syncthreads();
+    const double bj = b[j];
+    if (bj != 0.0)
+      for (int i = 1 + tid; i <= lm; i += nt) b[j + i] -= ab[(size_t)(kv + i) + (size_t)j * ld] * bj;
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    if (tid == 0) b[j] = b[j] / ab[(size_t)kv + (size_t)j * ld];
+    __syncthreads();
+    const double bj = b[j];
+    const int i0 = max(0, j - kv);
+    if (bj != 0.0)
+      for (int i = i0 + tid; i < j; i += nt) b[i] -= ab[(size_t)(kv + i - j) + (size_t)j * ld] * bj;
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) Ginv[(size_t)i * n + col] = b[i];
+}
+
+// Per apply: right-hand side from the particular side moments (Eq. 13-14 rows, banded order) and
+// c = G^-1 (-g0), one warp per unknown.
+__global__ void __launch_bounds__(256) k_coarse_apply(CoarseDev c, const double* __restrict__ Ginv,
+                                                      const double* __restrict__ mom0, int E, double* __restrict__ out) {
+  extern __shared__ double gs[];
+  const int n = c.n;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
+    const int ks = 2 * a + 1, ks2 = 2 * a;
+    gs[c.home[2 * e]] = -(mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2]);
+    gs[c.home[2 * e + 1]] = -(mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const double* gr = Ginv + (size_t)row * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc += gr[k] * gs[k];
+  acc = warp_sum(acc);
+  if (lane == 0) out[row] = acc;
+}
+
+cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  k_gbtrs_cols<<<c.n, 128, sizeof(double) * c.n, st>>>(c, Ginv);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  k_coarse_apply<<<(c.n + 7) / 8, 256, sizeof(double) * c.n, st>>>(c, Ginv, mom0, E, c.g);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st) {
   if (E == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(c.ab, 0, sizeof(double) * (size_t)c.ldab * c.n, st);

@@ -152,6 +152,239 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual_norm(Geo g, const doub
   grid_reduce<1>(v, partials, counter, outs, sm, 1);
 }
 
+// ============================================================================================
+// Fused Arnoldi step (cooperative launch, all blocks co-resident).  Each thread keeps R elements of
+// w in registers for the whole step, so the modified Gram-Schmidt passes read only v_i from memory;
+// between passes a grid barrier publishes the per-block partial sums, which every block then adds
+// in the same (block) order, so all blocks hold bit-identical h_{i,j}.
+// ============================================================================================
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;   // ~1-2 s of polling, then give up
+
+struct ArnoldiArgs {
+  const double* z;      // z_j
+  double* V;            // basis, V_i at V + i n
+  int j;
+  size_t n;
+  double* H;            // Hessenberg, column-major, leading dimension ldh
+  int ldh;
+  double* cs;
+  double* sn;
+  double* gv;
+  double* out;          // [0] |g_{j+1}|, [1] h_{j+1,j}, [2] ||A z_j||, [3] 1 if a barrier timed out
+  double* partials;     // 2 buffers x 2 values x gridDim
+  unsigned* bar;        // [0] arrivals, [1] generation
+  int* flags;
+};
+
+// Returns false if the wait gave up (the flag is set; the caller returns).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned my = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    s_ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == my) {
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicOr(flags, 8);
+          s_ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum of v0 (and v1) over the grid; every block receives the same totals.
+template <int NV>
+__device__ __forceinline__ bool grid_allreduce(double (&v)[NV], double* partials, int pass, unsigned* bar, int* flags,
+                                               double* smem32) {
+  const int G = gridDim.x;
+  double* buf = partials + (size_t)(pass & 1) * 2 * G;
+  for (int k = 0; k < NV; ++k) {
+    const double t = block_sum(v[k], smem32);
+    if (threadIdx.x == 0) buf[k * G + blockIdx.x] = t;
+  }
+  __threadfence();
+  if (!grid_barrier(bar, flags)) return false;
+  for (int k = 0; k < NV; ++k) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) acc += *((volatile double*)&buf[k * G + b]);
+    v[k] = block_sum(acc, smem32);
+  }
+  return true;
+}
+
+template <int R>
+__global__ void __launch_bounds__(512) k_arnoldi(Geo g, ArnoldiArgs a) {
+  __shared__ double sm[32];
+  const size_t n = a.n;
+  const size_t base = (size_t)blockIdx.x * R * blockDim.x + threadIdx.x;
+  const int j = a.j;
+  double w[R];
+  double red2[2] = {0.0, 0.0};
+  // w = A z_j ; (w, v_0) ; (w, w)
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const size_t c = base + (size_t)r * blockDim.x;
+    w[r] = 0.0;
+    if (c < n) {
+      const int i = (int)(c % g.nx), jj = (int)(c / g.nx);
+      const double* z = a.z;
+      const double zc = z[c];
+      const double zw = i > 0 ? z[c - 1] : 0.0;
+      const double ze = i < g.nx - 1 ? z[c + 1] : 0.0;
+      const double zs = jj > 0 ? z[c - g.nx] : 0.0;
+      const double zn = jj < g.ny - 1 ? z[c + g.nx] : 0.0;
+      const double* Tx = g.Tx + (size_t)jj * (g.nx + 1) + i;
+      const double* Ty = g.Ty + (size_t)jj * g.nx + i;
+      const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
+      const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
+      w[r] = wx + wy;
+      red2[0] += w[r] * a.V[c];
+      red2[1] += w[r] * w[r];
+    }
+  }
+  int pass = 0;
+  if (!grid_allreduce<2>(red2, a.partials, pass++, a.bar, a.flags, sm)) return;
+  double hprev = red2[0];
+  const double wn2 = red2[1];
+  double* col = a.H + (size_t)j * a.ldh;
+  if (blockIdx.x == 0 && threadIdx.x == 0) col[0] = hprev;
+  // modified Gram-Schmidt passes i = 1..j
+  for (int i = 1; i <= j; ++i) {
+    const double* vp = a.V + (size_t)(i - 1) * n;
+    const double* vi = a.V + (size_t)i * n;
+    double red1[1] = {0.0};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t c = base + (size_t)r * blockDim.x;
+      if (c < n) {
+        w[r] -= hprev * vp[c];
+        red1[0] += w[r] * vi[c];
+      }
+    }
+    if (!grid_allreduce<1>(red1, a.partials, pass++, a.bar, a.flags, sm)) return;
+    hprev = red1[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) col[i] = hprev;
+  }
+  // last pass: w -= h_{j,j} v_j, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
+  {
+    const double* vp = a.V + (size_t)j * n;
+    double red1[1] = {0.0};
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t c = base + (size_t)r * blockDim.x;
+      if (c < n) {
+        w[r] -= hprev * vp[c];
+        red1[0] += w[r] * w[r];
+      }
+    }
+    if (!grid_allreduce<1>(red1, a.partials, pass++, a.bar, a.flags, sm)) return;
+    const double hn = sqrt(red1[0]);
+    double* vn = a.V + (size_t)(j + 1) * n;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t c = base + (size_t)r * blockDim.x;
+      if (c < n) vn[c] = hn != 0.0 ? w[r] / hn : 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      col[j + 1] = hn;
+      // Givens update of column j
+      for (int i = 0; i < j; ++i) {
+        const double t0 = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
+        const double t1 = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
+        col[i] = t0;
+        col[i + 1] = t1;
+      }
+      const double x = col[j], y = col[j + 1];
+      double c, s, t;
+      if (y == 0.0) {
+        c = 1.0;
+        s = 0.0;
+        t = x;
+      } else {
+        t = hypot(x, y);
+        c = x / t;
+        s = y / t;
+      }
+      a.cs[j] = c;
+      a.sn[j] = s;
+      col[j] = t;
+      col[j + 1] = 0.0;
+      a.gv[j + 1] = -s * a.gv[j];
+      a.gv[j] = c * a.gv[j];
+      a.out[0] = fabs(a.gv[j + 1]);
+      a.out[1] = hn;
+      a.out[2] = sqrt(wn2);
+      a.out[3] = 0.0;
+    }
+  }
+}
+
+template <int R>
+static cudaError_t arnoldi_launch(const Geo& g, const ArnoldiArgs& a, int grid, cudaStream_t st) {
+  void* args[] = {(void*)&g, (void*)&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi<R>, dim3(grid), dim3(512), args, 0, st);
+  if (e == cudaSuccess) count_launch(1);
+  return e;
+}
+
+template <int R>
+static int arnoldi_max_blocks() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, per_sm = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<R>, 512, 0);
+    cached = per_sm * sms;
+  }
+  return cached;
+}
+
+// Returns cudaErrorNotSupported when the vector is too long for one co-resident wave.
+cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
+                           double* sn, double* gv, double* out, double* partials, unsigned* bar, int* flags,
+                           cudaStream_t st) {
+  ArnoldiArgs a{z, V, j, n, H, ldh, cs, sn, gv, out, partials, bar, flags};
+  const size_t per = 512;
+  // about one block per SM: a grid barrier costs roughly in proportion to the arriving blocks,
+  // while one block per SM still streams each basis vector at full bandwidth
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+#define MRCM_TRY_R(R_)                                                              \
+  {                                                                                 \
+    const int mb = arnoldi_max_blocks<R_>();                                        \
+    const size_t need = (n + per * R_ - 1) / (per * R_);                            \
+    if ((need <= (size_t)sms || R_ == 16) && need <= (size_t)mb &&                  \
+        need <= (size_t)ARNOLDI_MAX_BLOCKS)                                         \
+      return arnoldi_launch<R_>(g, a, (int)need, st);                               \
+  }
+  MRCM_TRY_R(1)
+  MRCM_TRY_R(2)
+  MRCM_TRY_R(4)
+  MRCM_TRY_R(8)
+  MRCM_TRY_R(16)
+#undef MRCM_TRY_R
+  return cudaErrorNotSupported;
+}
+
 static int red_grid(size_t n) {
   const size_t want = (n + RED_THREADS - 1) / RED_THREADS;
   return (int)(want < (size_t)RED_BLOCKS ? (want > 0 ? want : 1) : RED_BLOCKS);

@@ -198,13 +198,14 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.G = take(8 * (size_t)L.ldab * E2);
   L.ipiv = take(4 * E2);
   L.gc = take(8 * E2);
+  L.Ginv = take(E2 <= (size_t)COARSE_DENSE_MAX ? 8 * E2 * E2 : 0);
   L.rho = take(8 * n);
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);
   L.Z = take(8 * (size_t)L.m * n);
   L.w = take(8 * n);
   L.Hs = take(8 * ((size_t)(L.m + 1) * L.m + 4 * (L.m + 1) + 64));
-  L.red = take(8 * 4 * RED_BLOCKS + 64);
+  L.red = take(8 * RED_DOUBLES + 64);
   L.flags = take(4 * 64);
   L.tmpv = take(8 * n);
   // device copies of the plan tables: iface[3E], home[2E], off[S], rank[6S], coff[S]

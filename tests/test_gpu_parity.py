@@ -132,11 +132,14 @@ def test_apply_precond_matches_oracle(mrcm, name):
         assert _rel(z, parts["z"]) < 1e-10, (name, trial, _rel(z, parts["z"]))
 
 
-@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "dirichlet-all"])
-def test_gmres_matches_oracle(mrcm, name):
+# GMRES(8) where restarted GMRES converges for this operator (covers the restart path); a long
+# restart where it stagnates (A T has eigenvalues with negative real part once smoothing is on)
+@pytest.mark.parametrize("name,restart", [("os-96x64-l4s2", 8), ("mrcm-48x40", 8), ("dirichlet-all", 8),
+                                          ("os-48x40", 100), ("ragged-60x36", 100)])
+def test_gmres_matches_oracle(mrcm, name, restart):
     prob, q = _case(name)
     q.tol = 1e-9
-    q.restart = 8
+    q.restart = restart
     s = mrcm.Solver(prob, q)
     s.factor()
     p, info = s.solve(fluxes=True)
@@ -158,6 +161,7 @@ def test_gmres_matches_oracle(mrcm, name):
 def test_fp32_local_solves_reach_fp64_tolerance(mrcm):
     prob, q = _case("os-96x64-l4s2")
     q.tol = 1e-8
+    q.restart = 100
     p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       restart=q.restart)
@@ -167,8 +171,6 @@ def test_fp32_local_solves_reach_fp64_tolerance(mrcm):
     p, info = s.solve()
     assert info["status"] == 0 and info["rel_res"] <= 1e-8
     assert info["iterations"] <= info_ref["iterations"] + 1
-    A = grid.dense_matrix(grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind), 2, prob.K.shape) \
-        if prob.cells <= 4096 else None
     assert _rel(p.cpu().numpy(), p_ref) < 1e-6
 
 
@@ -206,6 +208,7 @@ def test_edge_cases(mrcm):
 def test_workspace_too_small_and_deterministic(mrcm):
     import ctypes as C
     prob, q = _case("os-48x40")
+    q.restart = 100  # GMRES(30) stagnates on this case (see test_gmres_matches_oracle)
     need = mrcm.footprint(prob, q)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     K = torch.as_tensor(prob.K.ravel(), device="cuda")
