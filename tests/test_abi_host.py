@@ -73,7 +73,7 @@ def test_pure_neumann_rejected_and_3d_unsupported(lib):
 def test_footprint_grows_with_restart_and_smoothing(lib):
     prob, params = W.channels(128, sub=32)
     a = lib.footprint(prob, params)
-    params.restart = 60
+    params.restart += 40
     b = lib.footprint(prob, params)
     assert b > a and a % 256 == 0 and b % 256 == 0
     params.smooth_steps = 0
