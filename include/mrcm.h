@@ -185,6 +185,21 @@ mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int3
 /* Total kernels this library has launched in the process (all handles), for launch accounting. */
 int64_t mrcm_launch_count(void);
 
+/* ||b - A p||_2 (the true residual that mrcm_gmres_solve reports in result->abs_res), for callers
+ * that cannot allocate device memory: code running inside a CUDA graph capture or a real-time loop
+ * that must not touch an allocator, or a component that is handed device pointers but owns no
+ * allocator.  The paper has no counterpart; it is a library service around the GMRES stopping test.
+ * Allocates nothing: its scratch (the residual vector and the reduction partial sums) is a fixed
+ * array of 8 MiB + 5 KiB compiled into the library, held on every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's device address and
+ * caches it; make that first call before any stream capture.  Grids of more than 1,048,576 cells
+ * are rejected with MRCM_ERR_INVALID_ARG.  b, p: device arrays of n cells; norm_out: device
+ * pointer to one double, written when `stream` reaches the launch.  All calls share the one
+ * array, so calls that overlap on the GPU (other streams, other threads) race: serialise them.
+ * Requires a factored handle (for the transmissibilities). */
+mrcm_status mrcm_residual_norm_noalloc(mrcm_handle h, const double* b, const double* p, double* norm_out,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ _SIGS = {
     "mrcm_profile_enable": ([_H, C.c_int32], C.c_int),
     "mrcm_profile_read": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "mrcm_launch_count": ([], C.c_int64),
+    "mrcm_residual_norm_noalloc": ([_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
           "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
