@@ -423,7 +423,6 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
   double* beta_d = wn2 + 1;
   double* bnorm_d = beta_d + 1;
   double* partials = at<double>(h, L.red);
-  double* apartials = partials + 4096;
   unsigned* counter = reinterpret_cast<unsigned*>(partials + RED_DOUBLES);
   unsigned* bar = counter + 1;
   int* flags = at<int>(h, L.flags);
@@ -480,7 +479,9 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
       {
         Phase ph(h, MRCM_PH_KRYLOV, st);
         cudaError_t ea = cudaErrorNotSupported;
-        if (fused) ea = launch_arnoldi(g, zj, V, j, n, H, ldh, cs, sn, gv, out, apartials, bar, flags, st);
+        if (fused)
+          ea = launch_arnoldi(g, zj, V, j, n, H, ldh, cs, sn, gv, out, w, at<double>(h, L.apart), at<double>(h, L.atot),
+                              at<double>(h, L.aT), bar, flags, st);
         if (ea == cudaErrorNotSupported) {
           fused = false;
           (void)cudaGetLastError();

@@ -53,6 +53,7 @@ struct Layout {
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
+  size_t apart, atot, aT;                 // Arnoldi partial sums, totals, (I + R)^-1
   size_t total;
   // sizes
   int wl, wo;             // line width of the Omega and hat-Omega boxes
@@ -172,8 +173,8 @@ cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st);
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st);
 cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
-                           double* sn, double* gv, double* out, double* partials, unsigned* bar, int* flags,
-                           cudaStream_t st);
+                           double* sn, double* gv, double* out, double* wbuf, double* part, double* tot, double* Tm,
+                           unsigned* bar, int* flags, cudaStream_t st);
 
 // Krylov helpers (k_krylov.cu)
 cudaError_t launch_norm2(const double* x, size_t n, double* partials, unsigned* counter, double* out,

@@ -1,10 +1,12 @@
 // Krylov kernels for Algorithm 1 (restarted right-preconditioned GMRES storing Z), FP64.
 //
-// Inner step j: w = A z_j fused with h_{0,j} = (w, v_0) and ||w||^2; modified Gram-Schmidt passes
-// i = 1..j fused as "w -= h_{i-1,j} v_{i-1}, then h_{i,j} = (w, v_i)"; a last pass subtracts
-// h_{j,j} v_j and returns h_{j+1,j} = ||w||.  The Givens rotation update of the Hessenberg column
-// runs in one thread.  Reductions are deterministic: fixed grid, per-block partials, last block
-// sums them in block order.
+// Inner step j runs as one cooperative kernel (k_arnoldi_ls below).  For vectors too long for one
+// co-resident wave the step falls back to separate launches in MGS pass order: w = A z_j fused with
+// h_{0,j} = (w, v_0) and ||w||^2, then "w -= h_{i-1,j} v_{i-1}, h_{i,j} = (w, v_i)" for i = 1..j, a
+// last pass for h_{j+1,j} = ||w||, and the Givens update in one thread.  Reductions are
+// deterministic: fixed grid, per-block partials, summed in block order.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mrcm {
@@ -153,28 +155,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual_norm(Geo g, const doub
 }
 
 // ============================================================================================
-// Fused Arnoldi step (cooperative launch, all blocks co-resident).  Each thread keeps R elements of
-// w in registers for the whole step, so the modified Gram-Schmidt passes read only v_i from memory;
-// between passes a grid barrier publishes the per-block partial sums, which every block then adds
-// in the same (block) order, so all blocks hold bit-identical h_{i,j}.
+// Cooperative Arnoldi step.  All blocks are co-resident (cooperative launch); grid barriers are
+// an arrival counter plus a generation word, polled with a bounded spin that sets FLAG_TIMEOUT and
+// returns instead of waiting forever.
 // ============================================================================================
 constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;   // ~1-2 s of polling, then give up
-
-struct ArnoldiArgs {
-  const double* z;      // z_j
-  double* V;            // basis, V_i at V + i n
-  int j;
-  size_t n;
-  double* H;            // Hessenberg, column-major, leading dimension ldh
-  int ldh;
-  double* cs;
-  double* sn;
-  double* gv;
-  double* out;          // [0] |g_{j+1}|, [1] h_{j+1,j}, [2] ||A z_j||, [3] 1 if a barrier timed out
-  double* partials;     // 2 buffers x 2 values x gridDim
-  unsigned* bar;        // [0] arrivals, [1] generation
-  int* flags;
-};
 
 // Returns false if the wait gave up (the flag is set; the caller returns).
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags) {
@@ -206,183 +191,204 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags) {
   return s_ok != 0;
 }
 
-// Sum of v0 (and v1) over the grid; every block receives the same totals.
-template <int NV>
-__device__ __forceinline__ bool grid_allreduce(double (&v)[NV], double* partials, int pass, unsigned* bar, int* flags,
-                                               double* smem32) {
-  const int G = gridDim.x;
-  double* buf = partials + (size_t)(pass & 1) * 2 * G;
-  for (int k = 0; k < NV; ++k) {
-    const double t = block_sum(v[k], smem32);
-    if (threadIdx.x == 0) buf[k * G + blockIdx.x] = t;
+// One Arnoldi step (inner step j) in a single cooperative launch, with the modified
+// Gram-Schmidt coefficients obtained from one global reduction.  MGS computes
+//   h_i = (w - sum_{k<i} h_k v_k, v_i) = a_i - sum_{k<i} (v_k, v_i) h_k,   a_i = (w, v_i),
+// i.e. (I + R) h = a with R the strictly lower Gram matrix of the basis.  T = (I + R)^-1 is kept in
+// its compact inverse form and grows by one row per step (t_j = -r^T T_{j-1}, r_k = (v_k, v_j)),
+// so h = T a is a product instead of a sequential solve.  Per step: one sweep over the basis for
+// the j+1 coefficients a, the j new Gram entries r and ||A z||^2; one sweep for w -= V h and
+// ||w||^2; three grid barriers.  Each block owns one contiguous slice of the vectors; dot products
+// are computed one warp per dot over the slice (lanes stride the elements), then reduced across
+// blocks in block order (deterministic).
+struct LsArgs {
+  const double* z;      // z_j
+  double* V;            // basis, V_i at V + i n
+  int j;
+  size_t n;
+  double* H;            // Hessenberg, column-major, leading dimension ldh
+  int ldh;
+  double* cs;
+  double* sn;
+  double* gv;
+  double* out;          // [0] |g_{j+1}|, [1] h_{j+1,j}, [2] ||A z_j||
+  double* wbuf;         // w (n)
+  double* part;         // (2 ldh + 2) x gridDim partial sums
+  double* tot;          // 2 ldh + 2 totals
+  double* Tm;           // (I + R)^-1, row-major lower, leading dimension ldh
+  unsigned* bar;
+  int* flags;
+};
+
+__global__ void __launch_bounds__(512) k_arnoldi_ls(Geo g, LsArgs a) {
+  extern __shared__ double sh[];      // a[j+1] | r[j] | tj[j] | h[j+1] | misc
+  __shared__ double sm[32];
+  __shared__ double s_hn;
+  const int j = a.j, G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const size_t n = a.n;
+  const size_t chunk = (n + G - 1) / G;
+  const size_t lo = (size_t)b * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double* w = a.wbuf;
+  const double* vj = a.V + (size_t)j * n;
+  // 1. w = A z_j on the slice
+  for (size_t c = lo + tid; c < hi; c += nt) {
+    const int i = (int)(c % g.nx), jj = (int)(c / g.nx);
+    const double* z = a.z;
+    const double zc = z[c];
+    const double zw = i > 0 ? z[c - 1] : 0.0;
+    const double ze = i < g.nx - 1 ? z[c + 1] : 0.0;
+    const double zs = jj > 0 ? z[c - g.nx] : 0.0;
+    const double zn = jj < g.ny - 1 ? z[c + g.nx] : 0.0;
+    const double* Tx = g.Tx + (size_t)jj * (g.nx + 1) + i;
+    const double* Ty = g.Ty + (size_t)jj * g.nx + i;
+    const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
+    const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
+    w[c] = wx + wy;
+  }
+  __syncthreads();
+  // 2. block partials of a_t = (w, v_t) (t <= j), r_k = (v_j, v_k) (k < j), ||w||^2 -- one warp per dot
+  const int nd = 2 * j + 2;
+  for (int t = warp; t < nd; t += nw) {
+    double acc = 0.0;
+    if (t <= j) {
+      const double* vt = a.V + (size_t)t * n;
+      for (size_t c = lo + lane; c < hi; c += 32) acc += w[c] * vt[c];
+    } else if (t <= 2 * j) {
+      const double* vk = a.V + (size_t)(t - j - 1) * n;
+      for (size_t c = lo + lane; c < hi; c += 32) acc += vj[c] * vk[c];
+    } else {
+      for (size_t c = lo + lane; c < hi; c += 32) acc += w[c] * w[c];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) a.part[(size_t)t * G + b] = acc;
   }
   __threadfence();
-  if (!grid_barrier(bar, flags)) return false;
-  for (int k = 0; k < NV; ++k) {
+  if (!grid_barrier(a.bar, a.flags)) return;
+  // 3. totals, one dot per block (in block order)
+  if (warp == 0)
+    for (int t = b; t < nd; t += G) {
+      double acc = 0.0;
+      for (int k = lane; k < G; k += 32) acc += *((volatile double*)&a.part[(size_t)t * G + k]);
+      acc = warp_sum(acc);
+      if (lane == 0) a.tot[t] = acc;
+    }
+  __threadfence();
+  if (!grid_barrier(a.bar, a.flags)) return;
+  // 4. MGS coefficients h = T_j a, with the new row t_j = -r^T T_{j-1}
+  double* sa = sh;               // a[0..j]
+  double* sr = sa + (j + 1);     // r[0..j-1]
+  double* st = sr + j;           // t_j[0..j-1]
+  double* shh = st + j;          // h[0..j]
+  for (int t = tid; t < nd - 1; t += nt) sh[t] = *((volatile double*)&a.tot[t]);
+  const double wn2 = *((volatile double*)&a.tot[nd - 1]);
+  __syncthreads();
+  const int ldt = a.ldh;
+  for (int k = tid; k < j; k += nt) {
     double acc = 0.0;
-    for (int b = threadIdx.x; b < G; b += blockDim.x) acc += *((volatile double*)&buf[k * G + b]);
-    v[k] = block_sum(acc, smem32);
+    for (int i = k; i < j; ++i) acc += sr[i] * a.Tm[(size_t)i * ldt + k];
+    st[k] = -acc;
   }
-  return true;
-}
-
-template <int R>
-__global__ void __launch_bounds__(512) k_arnoldi(Geo g, ArnoldiArgs a) {
-  __shared__ double sm[32];
-  const size_t n = a.n;
-  const size_t base = (size_t)blockIdx.x * R * blockDim.x + threadIdx.x;
-  const int j = a.j;
-  double w[R];
-  double red2[2] = {0.0, 0.0};
-  // w = A z_j ; (w, v_0) ; (w, w)
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const size_t c = base + (size_t)r * blockDim.x;
-    w[r] = 0.0;
-    if (c < n) {
-      const int i = (int)(c % g.nx), jj = (int)(c / g.nx);
-      const double* z = a.z;
-      const double zc = z[c];
-      const double zw = i > 0 ? z[c - 1] : 0.0;
-      const double ze = i < g.nx - 1 ? z[c + 1] : 0.0;
-      const double zs = jj > 0 ? z[c - g.nx] : 0.0;
-      const double zn = jj < g.ny - 1 ? z[c + g.nx] : 0.0;
-      const double* Tx = g.Tx + (size_t)jj * (g.nx + 1) + i;
-      const double* Ty = g.Ty + (size_t)jj * g.nx + i;
-      const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
-      const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
-      w[r] = wx + wy;
-      red2[0] += w[r] * a.V[c];
-      red2[1] += w[r] * w[r];
+  __syncthreads();
+  for (int i = tid; i <= j; i += nt) {
+    double acc = 0.0;
+    if (i < j) {
+      const double* row = a.Tm + (size_t)i * ldt;
+      for (int k = 0; k < i; ++k) acc += row[k] * sa[k];
+    } else {
+      for (int k = 0; k < j; ++k) acc += st[k] * sa[k];
     }
+    shh[i] = acc + sa[i];
   }
-  int pass = 0;
-  if (!grid_allreduce<2>(red2, a.partials, pass++, a.bar, a.flags, sm)) return;
-  double hprev = red2[0];
-  const double wn2 = red2[1];
-  double* col = a.H + (size_t)j * a.ldh;
-  if (blockIdx.x == 0 && threadIdx.x == 0) col[0] = hprev;
-  // modified Gram-Schmidt passes i = 1..j
-  for (int i = 1; i <= j; ++i) {
-    const double* vp = a.V + (size_t)(i - 1) * n;
-    const double* vi = a.V + (size_t)i * n;
-    double red1[1] = {0.0};
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const size_t c = base + (size_t)r * blockDim.x;
-      if (c < n) {
-        w[r] -= hprev * vp[c];
-        red1[0] += w[r] * vi[c];
-      }
-    }
-    if (!grid_allreduce<1>(red1, a.partials, pass++, a.bar, a.flags, sm)) return;
-    hprev = red1[0];
-    if (blockIdx.x == 0 && threadIdx.x == 0) col[i] = hprev;
+  __syncthreads();
+  if (b == 0) {
+    for (int k = tid; k < j; k += nt) a.Tm[(size_t)j * ldt + k] = st[k];
+    if (tid == 0) a.Tm[(size_t)j * ldt + j] = 1.0;
   }
-  // last pass: w -= h_{j,j} v_j, h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
-  {
-    const double* vp = a.V + (size_t)j * n;
-    double red1[1] = {0.0};
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const size_t c = base + (size_t)r * blockDim.x;
-      if (c < n) {
-        w[r] -= hprev * vp[c];
-        red1[0] += w[r] * w[r];
-      }
+  // 5. w -= V h on the slice, ||w||^2
+  double nrm = 0.0;
+  for (size_t c = lo + tid; c < hi; c += nt) {
+    double acc0 = w[c], acc1 = 0.0;
+    int i = 0;
+    for (; i + 1 <= j; i += 2) {
+      acc0 -= shh[i] * a.V[(size_t)i * n + c];
+      acc1 -= shh[i + 1] * a.V[(size_t)(i + 1) * n + c];
     }
-    if (!grid_allreduce<1>(red1, a.partials, pass++, a.bar, a.flags, sm)) return;
-    const double hn = sqrt(red1[0]);
-    double* vn = a.V + (size_t)(j + 1) * n;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const size_t c = base + (size_t)r * blockDim.x;
-      if (c < n) vn[c] = hn != 0.0 ? w[r] / hn : 0.0;
+    if (i <= j) acc0 -= shh[i] * a.V[(size_t)i * n + c];
+    const double wc = acc0 + acc1;
+    w[c] = wc;
+    nrm += wc * wc;
+  }
+  nrm = block_sum(nrm, sm);
+  if (tid == 0) a.part[(size_t)nd * G + b] = nrm;
+  __threadfence();
+  if (!grid_barrier(a.bar, a.flags)) return;
+  // 6. h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}; Hessenberg column and Givens update (block 0)
+  if (warp == 0) {
+    double acc = 0.0;
+    for (int k = lane; k < G; k += 32) acc += *((volatile double*)&a.part[(size_t)nd * G + k]);
+    acc = warp_sum(acc);
+    if (lane == 0) s_hn = sqrt(acc);
+  }
+  __syncthreads();
+  const double hn = s_hn;
+  double* vn = a.V + (size_t)(j + 1) * n;
+  for (size_t c = lo + tid; c < hi; c += nt) vn[c] = hn != 0.0 ? w[c] / hn : 0.0;
+  if (b == 0 && tid == 0) {
+    double* col = a.H + (size_t)j * a.ldh;
+    for (int i = 0; i <= j; ++i) col[i] = shh[i];
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double t0 = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
+      const double t1 = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
+      col[i] = t0;
+      col[i + 1] = t1;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      col[j + 1] = hn;
-      // Givens update of column j
-      for (int i = 0; i < j; ++i) {
-        const double t0 = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
-        const double t1 = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
-        col[i] = t0;
-        col[i + 1] = t1;
-      }
-      const double x = col[j], y = col[j + 1];
-      double c, s, t;
-      if (y == 0.0) {
-        c = 1.0;
-        s = 0.0;
-        t = x;
-      } else {
-        t = hypot(x, y);
-        c = x / t;
-        s = y / t;
-      }
-      a.cs[j] = c;
-      a.sn[j] = s;
-      col[j] = t;
-      col[j + 1] = 0.0;
-      a.gv[j + 1] = -s * a.gv[j];
-      a.gv[j] = c * a.gv[j];
-      a.out[0] = fabs(a.gv[j + 1]);
-      a.out[1] = hn;
-      a.out[2] = sqrt(wn2);
-      a.out[3] = 0.0;
+    const double x = col[j], y = col[j + 1];
+    double c, s, t;
+    if (y == 0.0) {
+      c = 1.0;
+      s = 0.0;
+      t = x;
+    } else {
+      t = hypot(x, y);
+      c = x / t;
+      s = y / t;
     }
+    a.cs[j] = c;
+    a.sn[j] = s;
+    col[j] = t;
+    col[j + 1] = 0.0;
+    a.gv[j + 1] = -s * a.gv[j];
+    a.gv[j] = c * a.gv[j];
+    a.out[0] = fabs(a.gv[j + 1]);
+    a.out[1] = hn;
+    a.out[2] = sqrt(wn2);
+    a.out[3] = 0.0;
   }
 }
 
-template <int R>
-static cudaError_t arnoldi_launch(const Geo& g, const ArnoldiArgs& a, int grid, cudaStream_t st) {
-  void* args[] = {(void*)&g, (void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi<R>, dim3(grid), dim3(512), args, 0, st);
-  if (e == cudaSuccess) count_launch(1);
-  return e;
-}
-
-template <int R>
-static int arnoldi_max_blocks() {
-  static int cached = -1;
-  if (cached < 0) {
-    int dev = 0, per_sm = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<R>, 512, 0);
-    cached = per_sm * sms;
-  }
-  return cached;
-}
-
-// Returns cudaErrorNotSupported when the vector is too long for one co-resident wave.
+// Returns cudaErrorNotSupported when one co-resident wave cannot cover the grid.
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
-                           double* sn, double* gv, double* out, double* partials, unsigned* bar, int* flags,
-                           cudaStream_t st) {
-  ArnoldiArgs a{z, V, j, n, H, ldh, cs, sn, gv, out, partials, bar, flags};
-  const size_t per = 512;
-  // about one block per SM: a grid barrier costs roughly in proportion to the arriving blocks,
-  // while one block per SM still streams each basis vector at full bandwidth
-  static int sms = 0;
+                           double* sn, double* gv, double* out, double* wbuf, double* part, double* tot, double* Tm,
+                           unsigned* bar, int* flags, cudaStream_t st) {
+  static int sms = 0, per_sm = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_arnoldi_ls, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * 260);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_ls, 512, 8 * 4 * 260);
   }
-#define MRCM_TRY_R(R_)                                                              \
-  {                                                                                 \
-    const int mb = arnoldi_max_blocks<R_>();                                        \
-    const size_t need = (n + per * R_ - 1) / (per * R_);                            \
-    if ((need <= (size_t)sms || R_ == 16) && need <= (size_t)mb &&                  \
-        need <= (size_t)ARNOLDI_MAX_BLOCKS)                                         \
-      return arnoldi_launch<R_>(g, a, (int)need, st);                               \
-  }
-  MRCM_TRY_R(1)
-  MRCM_TRY_R(2)
-  MRCM_TRY_R(4)
-  MRCM_TRY_R(8)
-  MRCM_TRY_R(16)
-#undef MRCM_TRY_R
-  return cudaErrorNotSupported;
+  int grid = (int)std::min<size_t>((size_t)sms, (n + 511) / 512);
+  if (grid < 1) grid = 1;
+  if (grid > ARNOLDI_MAX_BLOCKS || per_sm < 1 || ldh > 257) return cudaErrorNotSupported;
+  LsArgs a{z, V, j, n, H, ldh, cs, sn, gv, out, wbuf, part, tot, Tm, bar, flags};
+  void* args[] = {(void*)&g, (void*)&a};
+  const size_t smem = sizeof(double) * (4 * (size_t)(j + 1) + 8);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_arnoldi_ls, dim3(grid), dim3(512), args, smem, st);
+  if (e == cudaSuccess) count_launch(1);
+  return e;
 }
 
 static int red_grid(size_t n) {

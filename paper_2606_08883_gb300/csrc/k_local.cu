@@ -2,14 +2,16 @@
 // overlapping-Schwarz local solves.  One CTA per subdomain.
 //
 // A box of width w (x) and height h (lines along x, x fastest) has a block-tridiagonal operator:
-// tridiagonal line blocks D_J and diagonal couplings -E_J between lines J-1 and J.  Its Cholesky
-// factor is block bidiagonal with L_{J,J-1} = -E_J L_{J-1}^-T, so only the inverse diagonal
-// blocks Linv_J = L_JJ^-1 are stored (packed lower triangle, one line block per line):
-//   factor  S_0 = D_0, S_J = D_J - E_J (Linv_{J-1}^T Linv_{J-1}) E_J, L_JJ = chol(S_J)
-//   forward y_J = Linv_J (b_J + E_J Linv_{J-1}^T y_{J-1})
-//   back    x_J = Linv_J^T (y_J + Linv_J E_{J+1} x_{J+1})
-// Each solve streams every line block once forward and once backward (cp.async double buffer),
-// with four threads per row in the triangular matrix-vector products.
+// tridiagonal line blocks D_J and diagonal couplings -E_J between lines J-1 and J.  Its block
+// LDL^T factorisation has the Schur complements S_0 = D_0, S_J = D_J - E_J S_{J-1}^-1 E_J as the
+// block diagonal and -E_J S_{J-1}^-1 below it, so only the inverses S_J^-1 are stored (symmetric,
+// packed lower triangle, one line block per line):
+//   factor  S_J as above, S_J = L L^T (Cholesky), L^-1, S_J^-1 = L^-T L^-1
+//   forward u_0 = b_0, u_J = b_J + E_J S_{J-1}^-1 u_{J-1}
+//   back    x_last = S_last^-1 u_last, x_J = S_J^-1 (u_J + E_{J+1} x_{J+1})
+// Each solve streams every line block once forward and once backward (cp.async double buffer);
+// every step is one symmetric matrix-vector product with the same w products per row, four threads
+// per row.
 //
 // Oversampled boxes are padded to the full (sub + 2l)^2 size; cells outside the grid get identity
 // rows with zero couplings and zero data, which leaves the clipped region's solution unchanged.
@@ -96,9 +98,9 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   const int w = b.w;
   T* Sm = reinterpret_cast<T*>(smem_raw);  // Schur complement, then inverse work rows
   T* Lm = Sm + w * w;                      // Cholesky factor of the line block
-  T* Lc = Lm + w * w;                      // Linv of the current line
-  T* Lp = Lc + w * w;                      // Linv of the previous line
-  T* ev = Lp + w * w;                      // couplings to the previous line
+  T* Lc = Lm + w * w;                      // L_JJ^-1 of the current line
+  T* Sp = Lc + w * w;                      // S^-1 of the previous (then current) line, lower part
+  T* ev = Sp + w * w;                      // couplings to the previous line
   T* rinv = ev + w;                        // reciprocal diagonal of Lm
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   T* out = Linv + (size_t)s * b.h * LS;
   const int npk = w * (w + 1) / 2;
   for (int J = 0; J < b.h; ++J) {
-    // (1) S_J = D_J - E_J (Lp^T Lp) E_J, lower triangle
+    // (1) S_J = D_J - E_J S_{J-1}^-1 E_J, lower triangle
     for (int i = tid; i < w; i += nt) {
       double d, o, e;
       line_coeffs(g, b, robin, J, i, d, o, e);
@@ -118,11 +120,7 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
     for (int k = tid; k < npk; k += nt) {
       const int i = tri_row(k), j = k - i * (i + 1) / 2;
       T v = (i == j || i == j + 1) ? Sm[i * w + j] : (T)0;
-      if (J > 0) {
-        T acc = 0;
-        for (int r = i; r < w; ++r) acc += Lp[r * w + i] * Lp[r * w + j];
-        v -= ev[i] * ev[j] * acc;
-      }
+      if (J > 0) v -= ev[i] * ev[j] * Sp[i * w + j];
       Sm[i * w + j] = v;
     }
     __syncthreads();
@@ -166,13 +164,14 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
       }
       __syncthreads();
     }
-    // (4) store packed, keep as previous line
+    // (4) S_J^-1 = Lc^T Lc (lower part), store packed, keep for the next line's Schur complement
     for (int k = tid; k < npk; k += nt) {
       const int i = tri_row(k), j = k - i * (i + 1) / 2;
-      const T v = Lc[i * w + j];
-      out[(size_t)J * LS + k] = v;
+      T acc = 0;
+      for (int r = i; r < w; ++r) acc += Lc[r * w + i] * Lc[r * w + j];
+      Sp[i * w + j] = acc;
+      out[(size_t)J * LS + k] = acc;
     }
-    for (int k = tid; k < w * w; k += nt) Lp[k] = Lc[k];
     __syncthreads();
   }
   if (tid == 0 && bad) atomicOr(flags, FLAG_SINGULAR_LOCAL);
@@ -221,19 +220,23 @@ __device__ __forceinline__ void fetch_line(T* dst, const T* src, int LS) {
   cp_async_commit();
 }
 
-// out[i][r] = sum_{c <= i} L[i][c] in[c][r]  (lower) -- 4 threads per row, rows < w
+// out[i][r] = sum_c S[i][c] in[c][r] for a symmetric S stored as its packed lower triangle:
+// S[i][c] is P[i(i+1)/2 + c] for c <= i and P[c(c+1)/2 + i] for c > i.  Four threads per row,
+// each over the columns c = q (mod 4): every row costs exactly w products, so all lanes of a warp
+// stay busy; warps with no row skip the reduction.
 template <typename T, int NR>
-__device__ __forceinline__ void gemv_lower(const T* L, const T* in, T* out, int w, bool accumulate) {
+__device__ __forceinline__ void gemv_sym(const T* P, const T* in, T* out, int w) {
   const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  if ((threadIdx.x >> 5) * 8 >= w) return;  // whole warp beyond the last row (warp-uniform)
   T acc[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) acc[r] = 0;
   if (i < w) {
-    const T* row = L + i * (i + 1) / 2;
-    for (int c = q; c <= i; c += 4) {
-      const T lv = row[c];
+    const T* row = P + i * (i + 1) / 2;
+    for (int c = q; c < w; c += 4) {
+      const T sv = c <= i ? row[c] : P[c * (c + 1) / 2 + i];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r] += lv * in[c * NR + r];
+      for (int r = 0; r < NR; ++r) acc[r] += sv * in[c * NR + r];
     }
   }
 #pragma unroll
@@ -243,32 +246,7 @@ __device__ __forceinline__ void gemv_lower(const T* L, const T* in, T* out, int 
   }
   if (i < w && q == 0) {
 #pragma unroll
-    for (int r = 0; r < NR; ++r) out[i * NR + r] = accumulate ? out[i * NR + r] + acc[r] : acc[r];
-  }
-}
-
-// out[c][r] = sum_{i >= c} L[i][c] in[i][r]  (upper = transpose of the packed lower)
-template <typename T, int NR>
-__device__ __forceinline__ void gemv_upper(const T* L, const T* in, T* out, int w) {
-  const int c = threadIdx.x >> 2, q = threadIdx.x & 3;
-  T acc[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r] = 0;
-  if (c < w) {
-    for (int i = c + q; i < w; i += 4) {
-      const T lv = L[i * (i + 1) / 2 + c];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r] += lv * in[i * NR + r];
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
-  }
-  if (c < w && q == 0) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) out[c * NR + r] = acc[r];
+    for (int r = 0; r < NR; ++r) out[i * NR + r] = acc[r];
   }
 }
 
@@ -322,7 +300,7 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
   T* Y = Lb1 + LS;                 // [hgt][w][NR]
   T* tv = Y + (size_t)hgt * w * NR; // [w][NR]
   T* vv = tv + w * NR;              // [w][NR]
-  __shared__ double red[8][4][2];
+  T* Ec = vv + w * NR;              // [hgt][w] line couplings
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * hgt * LS;
   fetch_line(Lb0, Lg, LS);  // overlap the first line block with the right-hand side set-up
@@ -376,52 +354,43 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
   }
   __syncthreads();
 
-  // ---------------- forward sweep
+  // couplings between consecutive lines: Ec[J][x] joins line J-1 and line J (J >= 1)
+  for (int k = tid; k < hgt * w; k += nt) Ec[k] = (T)couple_up(g, b, k / w, k % w);
+  __syncthreads();
+
+  // ---------------- forward sweep: u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (kept in Y), vv = S_J^-1 u_J
   for (int J = 0; J < hgt; ++J) {
-    T* L = (J & 1) ? Lb1 : Lb0;
+    const T* L = (J & 1) ? Lb1 : Lb0;
     if (J + 1 < hgt) {
       fetch_line((J & 1) ? Lb0 : Lb1, Lg + (size_t)(J + 1) * LS, LS);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    for (int k = tid; k < w * NR; k += nt) {
-      const int x = k / NR;
-      T v = Y[(size_t)J * w * NR + k];
-      if (J > 0) v += (T)couple_up(g, b, J, x) * vv[k];
-      tv[k] = v;
-    }
+    T* uJ = Y + (size_t)J * w * NR;
+    if (J > 0)
+      for (int k = tid; k < w * NR; k += nt) uJ[k] += Ec[J * w + k / NR] * vv[k];
     __syncthreads();
-    gemv_lower<T, NR>(L, tv, Y + (size_t)J * w * NR, w, false);
-    __syncthreads();
-    if (J + 1 < hgt) gemv_upper<T, NR>(L, Y + (size_t)J * w * NR, vv, w);
+    gemv_sym<T, NR>(L, uJ, vv, w);
     __syncthreads();
   }
-  // ---------------- backward sweep
-  fetch_line(Lb0, Lg + (size_t)(hgt - 1) * LS, LS);
-  for (int J = hgt - 1, it = 0; J >= 0; --J, ++it) {
-    T* L = (it & 1) ? Lb1 : Lb0;
+  // ---------------- backward sweep: x_last = vv, x_J = S_J^-1 (u_J + E_{J+1} x_{J+1})
+  for (int k = tid; k < w * NR; k += nt) Y[(size_t)(hgt - 1) * w * NR + k] = vv[k];
+  __syncthreads();
+  if (hgt >= 2) fetch_line(Lb0, Lg + (size_t)(hgt - 2) * LS, LS);
+  for (int J = hgt - 2, it = 0; J >= 0; --J, ++it) {
+    const T* L = (it & 1) ? Lb1 : Lb0;
     if (J > 0) {
       fetch_line((it & 1) ? Lb0 : Lb1, Lg + (size_t)(J - 1) * LS, LS);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
-    __syncthreads();
     T* yJ = Y + (size_t)J * w * NR;
-    if (J + 1 < hgt) {
-      const T* xn = Y + (size_t)(J + 1) * w * NR;
-      for (int k = tid; k < w * NR; k += nt) {
-        const int x = k / NR;
-        tv[k] = (T)couple_up(g, b, J + 1, x) * xn[k];
-      }
-      __syncthreads();
-      gemv_lower<T, NR>(L, tv, yJ, w, true);  // y_J + Linv_J E x_{J+1}
-      __syncthreads();
-    }
-    gemv_upper<T, NR>(L, yJ, vv, w);
+    const T* xn = yJ + w * NR;
+    for (int k = tid; k < w * NR; k += nt) tv[k] = yJ[k] + Ec[(J + 1) * w + k / NR] * xn[k];
     __syncthreads();
-    for (int k = tid; k < w * NR; k += nt) yJ[k] = vv[k];
+    gemv_sym<T, NR>(L, tv, yJ, w);
     __syncthreads();
   }
 
@@ -513,18 +482,12 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
       }
     }
   }
-  (void)red;
-}
-
-template <typename T, int MODE, int NR>
-static cudaError_t run_solve(const Geo& g, const SolveArgs& a, bool ohat) {
-  return cudaSuccess;
 }
 
 template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
-  const size_t sm = sizeof(T) * (2 * (size_t)a.LS + (size_t)h * w * NR + 2 * (size_t)w * NR) + 16;
+  const size_t sm = sizeof(T) * (2 * (size_t)a.LS + (size_t)h * w * NR + 2 * (size_t)w * NR + (size_t)h * w) + 16;
   cudaError_t e = cudaFuncSetAttribute(k_solve<T, MODE, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_solve<T, MODE, NR><<<g.mx * g.my, 256, sm, st>>>(g, a);

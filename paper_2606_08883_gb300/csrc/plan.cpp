@@ -208,6 +208,10 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.red = take(8 * RED_DOUBLES + 64);
   L.flags = take(4 * 64);
   L.tmpv = take(8 * n);
+  const size_t ldh = (size_t)L.m + 1;
+  L.apart = take(8 * (2 * ldh + 3) * ARNOLDI_MAX_BLOCKS);
+  L.atot = take(8 * (2 * ldh + 3));
+  L.aT = take(8 * ldh * ldh);
   // device copies of the plan tables: iface[3E], home[2E], off[S], rank[6S], coff[S]
   L.tab = take(4 * (3 * P.E + E2 + S + 6 * S + S + 16));
   L.total = o;
