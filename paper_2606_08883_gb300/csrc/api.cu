@@ -360,20 +360,23 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
       CK(h, launch_coarse_solve(c, st));
     }
   }
-  // reconstruction
+  // reconstruction, into the buffer that makes the last smoothing sweep land in z: each sweep
+  // reads one buffer (its residual needs the neighbours' values) and writes the other
+  const int s = h->prm.smooth_steps;
+  double* zb[2] = {z, at<double>(h, L.zt)};
+  double* z_rec = zb[s & 1];
   {
     Phase ph(h, MRCM_PH_RECONSTRUCT, st);
-    CK(h, launch_reconstruct(g, at<double>(h, L.psi0), at<double>(h, L.psi), tables(h).cidx, at<double>(h, L.gc), z, st));
+    CK(h, launch_reconstruct(g, at<double>(h, L.psi0), at<double>(h, L.psi), tables(h).cidx, at<double>(h, L.gc),
+                             z_rec, st));
   }
-  if (h->keep_z0) CK(h, cudaMemcpyAsync(at<double>(h, L.z0), z, 8 * ncell(h), cudaMemcpyDeviceToDevice, st));
-  // smoothing sweeps (restricted additive Schwarz)
-  for (int it = 0; it < h->prm.smooth_steps; ++it) {
-    {
-      Phase ph(h, MRCM_PH_RESIDUAL, st);
-      CK(h, launch_residual(g, r, z, at<double>(h, L.rho), st));
-    }
+  if (h->keep_z0) CK(h, cudaMemcpyAsync(at<double>(h, L.z0), z_rec, 8 * ncell(h), cudaMemcpyDeviceToDevice, st));
+  // smoothing sweeps (restricted additive Schwarz; residual fused into the local solve)
+  for (int it = 0; it < s; ++it) {
     Phase ph(h, MRCM_PH_SCHWARZ, st);
-    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, at<double>(h, L.rho), z, st));
+    const double* zin = zb[(s - it) & 1];
+    double* zout = zb[(s - it - 1) & 1];
+    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, st));
   }
   return MRCM_OK;
 }

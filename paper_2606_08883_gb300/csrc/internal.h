@@ -148,8 +148,8 @@ cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, cons
                          double* mom, cudaStream_t st);
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, cudaStream_t st);
-cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* rho, double* z,
-                           cudaStream_t st);
+cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
+                           double* zout, cudaStream_t st);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
 size_t factor_smem_bytes(int w, bool fp32);

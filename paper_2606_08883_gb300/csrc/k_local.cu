@@ -212,44 +212,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T>
-__device__ __forceinline__ void fetch_line(T* dst, const T* src, int LS) {
-  const int nch = LS * (int)sizeof(T) / 16;
-  for (int c = threadIdx.x; c < nch; c += blockDim.x)
-    cp_async16(reinterpret_cast<unsigned char*>(dst) + 16 * c, reinterpret_cast<const unsigned char*>(src) + 16 * c);
-  cp_async_commit();
-}
-
-// out[i][r] = sum_c S[i][c] in[c][r] for a symmetric S stored as its packed lower triangle:
-// S[i][c] is P[i(i+1)/2 + c] for c <= i and P[c(c+1)/2 + i] for c > i.  Four threads per row,
-// each over the columns c = q (mod 4): every row costs exactly w products, so all lanes of a warp
-// stay busy; warps with no row skip the reduction.
-template <typename T, int NR>
-__device__ __forceinline__ void gemv_sym(const T* P, const T* in, T* out, int w) {
-  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
-  if ((threadIdx.x >> 5) * 8 >= w) return;  // whole warp beyond the last row (warp-uniform)
-  T acc[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) acc[r] = 0;
-  if (i < w) {
-    const T* row = P + i * (i + 1) / 2;
-    for (int c = q; c < w; c += 4) {
-      const T sv = c <= i ? row[c] : P[c * (c + 1) / 2 + i];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r] += sv * in[c * NR + r];
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
-  }
-  if (i < w && q == 0) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) out[i * NR + r] = acc[r];
-  }
-}
-
 // coupling value (T > 0) between local lines J-1 and J at x, 0 if absent
 __device__ __forceinline__ double couple_up(const Geo& g, const Box& b, int J, int x) {
   const int gx = b.ox + x, gy = b.oy + J;
@@ -260,9 +222,10 @@ __device__ __forceinline__ double couple_up(const Geo& g, const Box& b, int J, i
 struct SolveArgs {
   const void* Linv;
   int LS;
-  const double* in;    // particular: r; schwarz: rho; basis: phi
-  double* out;         // particular: psi0; schwarz: z; basis: psi; informed: phi
+  const double* in;    // particular, schwarz: r; basis: phi
+  double* out;         // particular: psi0; schwarz: z after the sweep; basis: psi; informed: phi
   double* mom;         // particular: mom0 [S][4][2]; basis: mom [S][4][4][2]
+  const double* zin;   // schwarz: z before the sweep (read only)
 };
 
 // Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.
@@ -288,31 +251,91 @@ __device__ __forceinline__ bool robin_side(const Geo& g, int s, int k) {
   }
 }
 
-template <typename T, int MODE, int NR>
+
+// S x for symmetric S in packed storage (see gemv_sym); epi(i, r, value) is called once per
+// output by the q == 0 thread of row i, so a step can produce the next step's input directly.
+template <typename T, int NR, class Epi>
+__device__ __forceinline__ void gemv_sym_epi(const T* P, const T* in, int w, Epi epi) {
+  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+  if ((threadIdx.x >> 5) * 8 >= w) return;
+  T acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = 0;
+  if (i < w) {
+    const T* row = P + i * (i + 1) / 2;
+    for (int c = q; c < w; c += 4) {
+      const T sv = c <= i ? row[c] : P[c * (c + 1) / 2 + i];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] += sv * in[c * NR + r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
+    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
+  }
+  if (i < w && q == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) epi(i, r, acc[r]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void issue_line(T* buf, const T* src, int LS, bool valid) {
+  if (valid) {
+    const int nch = LS * (int)sizeof(T) / 16;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x)
+      cp_async16(reinterpret_cast<unsigned char*>(buf) + 16 * c, reinterpret_cast<const unsigned char*>(src) + 16 * c);
+  }
+  cp_async_commit();  // one group per step, empty past the last line, so the wait count stays uniform
+}
+
+// NBUF line blocks in flight (prefetch distance NBUF - 1).
+template <typename T, int MODE, int NR, int NBUF>
 __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
-  T* Lb0 = reinterpret_cast<T*>(smem_raw);
-  T* Lb1 = Lb0 + LS;
-  T* Y = Lb1 + LS;                 // [hgt][w][NR]
-  T* tv = Y + (size_t)hgt * w * NR; // [w][NR]
-  T* vv = tv + w * NR;              // [w][NR]
-  T* Ec = vv + w * NR;              // [hgt][w] line couplings
+  T* Lb = reinterpret_cast<T*>(smem_raw);   // [NBUF][LS] line blocks
+  T* Y = Lb + NBUF * LS;                     // [hgt][w][NR]: b, then u (forward), then x (backward)
+  T* tvA = Y + (size_t)hgt * w * NR;         // [w][NR] ping-pong inputs of the backward steps
+  T* tvB = tvA + w * NR;
+  T* xl = tvB + w * NR;                      // [w][NR] x of the last line
+  T* Ec = xl + w * NR;                       // [hgt][w] line couplings
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * hgt * LS;
-  fetch_line(Lb0, Lg, LS);  // overlap the first line block with the right-hand side set-up
+  // forward prologue: lines 0 .. NBUF-2 in flight while the right-hand sides are set up
+  for (int p = 0; p < NBUF - 1; ++p) issue_line(Lb + (p % NBUF) * LS, Lg + (size_t)p * LS, LS, p < hgt);
 
   // ---------------- right-hand sides into Y
   for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
   __syncthreads();
-  if (MODE == MODE_PARTICULAR || MODE == MODE_SCHWARZ) {
+  if (MODE == MODE_PARTICULAR) {
     for (int k = tid; k < hgt * w; k += nt) {
       const int J = k / w, x = k % w;
       const int gx = b.ox + x, gy = b.oy + J;
       if (active(g, gx, gy)) Y[k * NR] = (T)a.in[(size_t)gy * g.nx + gx];
+    }
+  } else if (MODE == MODE_SCHWARZ) {
+    // rho = r - A z on the box, from the sweep's input z (read only; the output goes elsewhere)
+    const double* z = a.zin;
+    for (int k = tid; k < hgt * w; k += nt) {
+      const int J = k / w, x = k % w;
+      const int gx = b.ox + x, gy = b.oy + J;
+      if (!active(g, gx, gy)) continue;
+      const size_t c = (size_t)gy * g.nx + gx;
+      const double zc = z[c];
+      const double zw = gx > 0 ? z[c - 1] : 0.0;
+      const double ze = gx < g.nx - 1 ? z[c + 1] : 0.0;
+      const double zs = gy > 0 ? z[c - g.nx] : 0.0;
+      const double zn = gy < g.ny - 1 ? z[c + g.nx] : 0.0;
+      const double* Tx = g.Tx + (size_t)gy * (g.nx + 1) + gx;
+      const double* Ty = g.Ty + (size_t)gy * g.nx + gx;
+      const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
+      const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
+      Y[k * NR] = (T)(a.in[c] - (wx + wy));
     }
   } else if (MODE == MODE_INFORMED) {
     // lambda^r = 1 on the faces of Robin side r of the oversampled box
@@ -352,47 +375,62 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
       __syncthreads();
     }
   }
-  __syncthreads();
-
   // couplings between consecutive lines: Ec[J][x] joins line J-1 and line J (J >= 1)
   for (int k = tid; k < hgt * w; k += nt) Ec[k] = (T)couple_up(g, b, k / w, k % w);
-  __syncthreads();
 
-  // ---------------- forward sweep: u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (kept in Y), vv = S_J^-1 u_J
+  // ---------------- forward sweep: u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (in Y); one barrier per line
   for (int J = 0; J < hgt; ++J) {
-    const T* L = (J & 1) ? Lb1 : Lb0;
-    if (J + 1 < hgt) {
-      fetch_line((J & 1) ? Lb0 : Lb1, Lg + (size_t)(J + 1) * LS, LS);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    cp_async_wait<NBUF - 2>();
+    __syncthreads();
+    {
+      const int nxt = J + NBUF - 1;
+      issue_line(Lb + (nxt % NBUF) * LS, Lg + (size_t)nxt * LS, LS, nxt < hgt);
     }
+    const T* L = Lb + (J % NBUF) * LS;
     T* uJ = Y + (size_t)J * w * NR;
-    if (J > 0)
-      for (int k = tid; k < w * NR; k += nt) uJ[k] += Ec[J * w + k / NR] * vv[k];
-    __syncthreads();
-    gemv_sym<T, NR>(L, uJ, vv, w);
-    __syncthreads();
-  }
-  // ---------------- backward sweep: x_last = vv, x_J = S_J^-1 (u_J + E_{J+1} x_{J+1})
-  for (int k = tid; k < w * NR; k += nt) Y[(size_t)(hgt - 1) * w * NR + k] = vv[k];
-  __syncthreads();
-  if (hgt >= 2) fetch_line(Lb0, Lg + (size_t)(hgt - 2) * LS, LS);
-  for (int J = hgt - 2, it = 0; J >= 0; --J, ++it) {
-    const T* L = (it & 1) ? Lb1 : Lb0;
-    if (J > 0) {
-      fetch_line((it & 1) ? Lb0 : Lb1, Lg + (size_t)(J - 1) * LS, LS);
-      cp_async_wait<1>();
+    if (J + 1 < hgt) {
+      T* un = uJ + w * NR;
+      const T* en = Ec + (J + 1) * w;
+      gemv_sym_epi<T, NR>(L, uJ, w, [&](int i, int r, T v) { un[i * NR + r] += en[i] * v; });
     } else {
-      cp_async_wait<0>();
+      const T* um = uJ - w * NR;   // u of the line before (first backward input), if any
+      const T* el = Ec + J * w;
+      const bool more = hgt >= 2;
+      gemv_sym_epi<T, NR>(L, uJ, w, [&](int i, int r, T v) {
+        xl[i * NR + r] = v;
+        if (more) tvA[i * NR + r] = um[i * NR + r] + el[i] * v;
+      });
     }
-    T* yJ = Y + (size_t)J * w * NR;
-    const T* xn = yJ + w * NR;
-    for (int k = tid; k < w * NR; k += nt) tv[k] = yJ[k] + Ec[(J + 1) * w + k / NR] * xn[k];
-    __syncthreads();
-    gemv_sym<T, NR>(L, tv, yJ, w);
-    __syncthreads();
   }
+  // ---------------- backward sweep: x_J = S_J^-1 (u_J + E_{J+1} x_{J+1}), lines hgt-2 .. 0
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int p = 0; p < NBUF - 1; ++p) {
+    const int line = hgt - 2 - p;
+    issue_line(Lb + (p % NBUF) * LS, Lg + (size_t)(line > 0 ? line : 0) * LS, LS, line >= 0);
+  }
+  for (int t = 0, J = hgt - 2; J >= 0; ++t, --J) {
+    cp_async_wait<NBUF - 2>();
+    __syncthreads();
+    {
+      const int nt2 = t + NBUF - 1, line = hgt - 2 - nt2;
+      issue_line(Lb + (nt2 % NBUF) * LS, Lg + (size_t)(line > 0 ? line : 0) * LS, LS, line >= 0);
+    }
+    const T* L = Lb + (t % NBUF) * LS;
+    const T* in = (t & 1) ? tvB : tvA;
+    T* nxt = (t & 1) ? tvA : tvB;
+    T* xJ = Y + (size_t)J * w * NR;
+    const T* um = xJ - w * NR;
+    const T* eJ = Ec + J * w;
+    gemv_sym_epi<T, NR>(L, in, w, [&](int i, int r, T v) {
+      xJ[i * NR + r] = v;
+      if (J > 0) nxt[i * NR + r] = um[i * NR + r] + eJ[i] * v;
+    });
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int k = tid; k < w * NR; k += nt) Y[(size_t)(hgt - 1) * w * NR + k] = xl[k];
+  __syncthreads();
 
   // ---------------- outputs
   const int lane = tid & 31, wid = tid >> 5;
@@ -427,7 +465,8 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
     for (int k = tid; k < g.sx * g.sy; k += nt) {
       const int y = k / g.sx, x = k % g.sx;
       const int gx = b.ox + g.l + x, gy = b.oy + g.l + y;
-      a.out[(size_t)gy * g.nx + gx] += (double)Y[(g.l + y) * w + g.l + x];
+      const size_t c = (size_t)gy * g.nx + gx;
+      a.out[c] = a.zin[c] + (double)Y[(g.l + y) * w + g.l + x];
     }
   } else if (MODE == MODE_BASIS) {
     for (int k = tid; k < hgt * w * NR; k += nt) {
@@ -484,15 +523,28 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
   }
 }
 
-template <typename T, int MODE, int NR>
-static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
+template <typename T, int MODE, int NR, int NBUF>
+static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
-  const size_t sm = sizeof(T) * (2 * (size_t)a.LS + (size_t)h * w * NR + 2 * (size_t)w * NR + (size_t)h * w) + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_solve<T, MODE, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return sizeof(T) * (NBUF * (size_t)a.LS + (size_t)h * w * NR + 3 * (size_t)w * NR + (size_t)h * w) + 16;
+}
+
+template <typename T, int MODE, int NR, int NBUF>
+static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_solve<T, MODE, NR, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_solve<T, MODE, NR><<<g.mx * g.my, 256, sm, st>>>(g, a);
+  k_solve<T, MODE, NR, NBUF><<<g.mx * g.my, 256, sm, st>>>(g, a);
   count_launch(1);
   return cudaGetLastError();
+}
+
+// Four line blocks in flight when they fit in shared memory next to the right-hand sides, else two.
+template <typename T, int MODE, int NR>
+static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
+  constexpr size_t kMaxSmem = 227 * 1024;
+  const size_t sm4 = solve_smem<T, MODE, NR, 4>(g, a, ohat);
+  if (sm4 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 4>(g, a, sm4, st);
+  return launch_solve_nb<T, MODE, NR, 2>(g, a, solve_smem<T, MODE, NR, 2>(g, a, ohat), st);
 }
 
 template <int MODE, int NR>
@@ -517,25 +569,25 @@ cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, d
     count_launch(1);
     return cudaGetLastError();
   }
-  SolveArgs a{Linv, LS, nullptr, phi, nullptr};
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr};
   return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
 }
 
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
                          double* mom, cudaStream_t st) {
-  SolveArgs a{Linv, LS, phi, psi, mom};
+  SolveArgs a{Linv, LS, phi, psi, mom, nullptr};
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, cudaStream_t st) {
-  SolveArgs a{Linv, LS, r, psi0, mom0};
+  SolveArgs a{Linv, LS, r, psi0, mom0, nullptr};
   return launch_solve<MODE_PARTICULAR, 1>(g, a, false, fp32, st);
 }
 
-cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* rho, double* z,
-                           cudaStream_t st) {
-  SolveArgs a{Linv, LS, rho, z, nullptr};
+cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
+                           double* zout, cudaStream_t st) {
+  SolveArgs a{Linv, LS, r, zout, nullptr, zin};
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 
