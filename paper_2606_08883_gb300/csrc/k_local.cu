@@ -9,9 +9,10 @@
 //   factor  S_J as above, S_J = L L^T (Cholesky), L^-1, S_J^-1 = L^-T L^-1
 //   forward u_0 = b_0, u_J = b_J + E_J S_{J-1}^-1 u_{J-1}
 //   back    x_last = S_last^-1 u_last, x_J = S_J^-1 (u_J + E_{J+1} x_{J+1})
-// Each solve streams every line block once forward and once backward (cp.async double buffer);
-// every step is one symmetric matrix-vector product with the same w products per row, four threads
-// per row.
+// Each solve streams every line block once forward and once backward through a cp.async pipeline
+// of 2-8 line blocks; every step is one symmetric matrix-vector product with the same w products
+// per row (four threads per row) whose epilogue forms the next step's input, so a step costs one
+// barrier.
 //
 // Oversampled boxes are padded to the full (sub + 2l)^2 size; cells outside the grid get identity
 // rows with zero couplings and zero data, which leaves the clipped region's solution unchanged.
@@ -319,23 +320,24 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
       if (active(g, gx, gy)) Y[k * NR] = (T)a.in[(size_t)gy * g.nx + gx];
     }
   } else if (MODE == MODE_SCHWARZ) {
-    // rho = r - A z on the box, from the sweep's input z (read only; the output goes elsewhere)
+    // rho = r - A z on the box, from the sweep's input z (read only; the output goes elsewhere),
+    // in the precision of the local solve
     const double* z = a.zin;
     for (int k = tid; k < hgt * w; k += nt) {
       const int J = k / w, x = k % w;
       const int gx = b.ox + x, gy = b.oy + J;
       if (!active(g, gx, gy)) continue;
       const size_t c = (size_t)gy * g.nx + gx;
-      const double zc = z[c];
-      const double zw = gx > 0 ? z[c - 1] : 0.0;
-      const double ze = gx < g.nx - 1 ? z[c + 1] : 0.0;
-      const double zs = gy > 0 ? z[c - g.nx] : 0.0;
-      const double zn = gy < g.ny - 1 ? z[c + g.nx] : 0.0;
+      const T zc = (T)z[c];
+      const T zw = gx > 0 ? (T)z[c - 1] : (T)0;
+      const T ze = gx < g.nx - 1 ? (T)z[c + 1] : (T)0;
+      const T zs = gy > 0 ? (T)z[c - g.nx] : (T)0;
+      const T zn = gy < g.ny - 1 ? (T)z[c + g.nx] : (T)0;
       const double* Tx = g.Tx + (size_t)gy * (g.nx + 1) + gx;
       const double* Ty = g.Ty + (size_t)gy * g.nx + gx;
-      const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
-      const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
-      Y[k * NR] = (T)(a.in[c] - (wx + wy));
+      const T wx = (T)Tx[1] * (zc - ze) - (T)Tx[0] * (zw - zc);
+      const T wy = (T)Ty[g.nx] * (zc - zn) - (T)Ty[0] * (zs - zc);
+      Y[k * NR] = (T)a.in[c] - (wx + wy);
     }
   } else if (MODE == MODE_INFORMED) {
     // lambda^r = 1 on the faces of Robin side r of the oversampled box
@@ -538,10 +540,16 @@ static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, 
   return cudaGetLastError();
 }
 
-// Four line blocks in flight when they fit in shared memory next to the right-hand sides, else two.
+// Line blocks in flight: eight for FP32 solves (short steps, so the prefetch must run further ahead
+// to cover memory latency), four for FP64; fewer when they would not fit next to the right-hand sides.
 template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   constexpr size_t kMaxSmem = 227 * 1024;
+  constexpr size_t kBudget = 100 * 1024;  // keep two CTAs per SM when possible
+  if (sizeof(T) == 4) {
+    const size_t sm8 = solve_smem<T, MODE, NR, 8>(g, a, ohat);
+    if (sm8 <= kBudget) return launch_solve_nb<T, MODE, NR, 8>(g, a, sm8, st);
+  }
   const size_t sm4 = solve_smem<T, MODE, NR, 4>(g, a, ohat);
   if (sm4 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 4>(g, a, sm4, st);
   return launch_solve_nb<T, MODE, NR, 2>(g, a, solve_smem<T, MODE, NR, 2>(g, a, ohat), st);
