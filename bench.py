@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=8, help="GMRES iterations per reference-arm sample")
+    ap.add_argument("--serve", action="store_true", help="serving stream instead of the single-solve benchmark")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--inflight", type=int, default=8)
+    ap.add_argument("--arena-gb", type=float, default=48.0)
     return ap.parse_args()
 
 
@@ -364,10 +368,76 @@ def mrcm_arm(args):
         dist.destroy_process_group()
 
 
+def serve_arm(args):
+    """Serving stream: requests with grids drawn from 128^2..1024^2, log-normal fields (variance
+    U[1, 5], correlation length 0.1, seed = 1000 + id), 32 x 32 subdomains, oversampling 2, two
+    sweeps (one sweep leaves the preconditioned operator indefinite on these fields and GMRES
+    stagnates from 256^2 up), FP32 local solves, FP64 GMRES.  First the mix back to back (capacity), then Poisson
+    arrivals at 0.8 x capacity (seed 7) for latency percentiles."""
+    import numpy as np
+    import torch
+    from paper_2606_08883_gb300 import mrcm, workloads as W
+    rng = np.random.default_rng(7)
+    sizes = rng.choice([128, 256, 512, 1024], size=args.requests)
+    reqs = []
+    for i, N in enumerate(sizes):
+        var = float(np.random.default_rng(1000 + i).uniform(1.0, 5.0))
+        prob, q = W.lognormal(int(N), seed=1000 + i, variance=var, corr=0.1, sub=32, oversample=2, smooth_steps=2,
+                              prec=W.PREC_FP32)
+        q.restart = args.restart
+        q.max_iter = 3 * args.restart
+        reqs.append((prob, q))
+    torch.cuda.set_device(0)
+    srv = mrcm.Server(int(args.arena_gb * (1 << 30)), max_inflight=args.inflight)
+
+    def run(arrivals):
+        t0 = time.perf_counter()
+        pending, done, k = {}, {}, 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(reqs) and arrivals[k] <= now:
+                pending[srv.submit(*reqs[k])] = k
+                k += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    done[pending.pop(t)] = r
+            time.sleep(0.0005)
+        return time.perf_counter() - t0, done
+
+    # warm-up: one request of each size through the server (module loading, first-touch costs)
+    for N in sorted(set(int(v) for v in sizes)):
+        i = int(np.nonzero(sizes == N)[0][0])
+        t = srv.submit(*reqs[i])
+        while srv.poll(t) is None:
+            time.sleep(0.001)
+    makespan, done = run([0.0] * len(reqs))
+    capacity = len(reqs) / makespan
+    gaps = rng.exponential(1.0 / (0.8 * capacity), size=len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    wall, done2 = run(list(arrivals))
+    lat = sorted(r[2]["latency_ms"] for r in done2.values())
+    ok = sum(1 for r in done2.values() if r[0] == mrcm.MRCM_OK)
+    cells = sum(p.cells for p, _ in reqs)
+    line = {"metric": "serving solves/s and latency (Poisson arrivals at 0.8 x capacity)",
+            "value": len(reqs) / wall, "unit": "solves/s", "n_gpus": 1, "requests": len(reqs),
+            "capacity_solves_per_s": capacity, "mcells_per_s": cells / wall / 1e6,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "converged": ok, "iterations_median": float(np.median([r[2]["iterations"] for r in done2.values()])),
+            "max_inflight": args.inflight, "arena_gb": args.arena_gb, "arena_peak_gb": srv.stats()["arena_peak"] / 2 ** 30,
+            "dtype": "f32 local / f64 Krylov", "data": "synthetic",
+            "config": {"workload": "serving-lognormal-128..1024", "subdomain": "32x32", "oversample": 2,
+                       "smooth_steps": 2, "restart": args.restart}}
+    srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.serve:
+        serve_arm(args)
     else:
         mrcm_arm(args)
 

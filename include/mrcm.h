@@ -50,7 +50,8 @@ typedef enum {
   MRCM_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
   MRCM_ERR_CUDA = 6,          /* a CUDA runtime call failed (message in mrcm_last_error) */
   MRCM_ERR_BUSY = 7,
-  MRCM_ERR_UNSUPPORTED = 8    /* valid input outside what the GPU path implements */
+  MRCM_ERR_UNSUPPORTED = 8,   /* valid input outside what the GPU path implements */
+  MRCM_ERR_CANCELLED = 9      /* the request was cancelled before it finished */
 } mrcm_status;
 
 enum { MRCM_BC_DIRICHLET = 0, MRCM_BC_NEUMANN = 1 };
@@ -93,6 +94,8 @@ typedef struct mrcm_result {
   double* history;          /* host, optional: initial residual, |g_{j+1}| per step, true residual
                                after each cycle; NULL to skip */
   int32_t history_cap;      /* capacity of history */
+  double latency_ms;        /* server requests: submit to completion (0 for direct solves) */
+  double queue_ms;          /* server requests: submit to admission */
 } mrcm_result;
 
 typedef struct mrcm_ctx* mrcm_handle;
@@ -184,6 +187,49 @@ mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int3
 
 /* Total kernels this library has launched in the process (all handles), for launch accounting. */
 int64_t mrcm_launch_count(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Request server with continuous batching (not in the paper: a serving layer around Algorithm 1).
+ *
+ * The caller gives the server one device arena (arena_bytes at a 256-byte-aligned device address,
+ * e.g. from PyTorch's allocator); the library still allocates no device memory.  Each submitted
+ * request (a whole problem: grid, K, boundary data, source, parameters) is admitted when its
+ * device footprint (mrcm_footprint() plus its input and solution arrays) fits in the free part of
+ * the arena and fewer than max_inflight requests run; admission takes the oldest queued request
+ * that fits (a request skipped more than 8 times blocks later ones until it is admitted).  Every
+ * admitted request runs set-up, mrcm_factor_local and mrcm_gmres_solve (p0 = 0) on its own CUDA
+ * stream and host worker thread, so the work of concurrent requests overlaps on the GPU, and its
+ * arena block is released on completion.  Results do not depend on what else is running.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct mrcm_server* mrcm_server_handle;
+
+/* max_inflight in 1..64.  The current device at creation is the server's device. */
+mrcm_status mrcm_server_create(void* arena, size_t arena_bytes, int32_t max_inflight, mrcm_server_handle* out);
+
+/* Queue a solve.  problem->K, bc_val[] and f are HOST pointers here; they are copied before the
+ * call returns.  Returns MRCM_ERR_OOM if the request could never fit in the arena, and the
+ * validation errors of mrcm_footprint().  *ticket identifies the request. */
+mrcm_status mrcm_submit(mrcm_server_handle s, const mrcm_problem* problem, const mrcm_params* params, uint64_t* ticket);
+
+/* Non-blocking.  *done = 0 while queued or running.  Once finished, *done = 1, the solution (n
+ * doubles) is copied to the host array p_out (if not NULL), result is filled (history up to its
+ * capacity, latency_ms and queue_ms), the request is forgotten, and the request's own status is
+ * returned (MRCM_OK, MRCM_ERR_NOT_CONVERGED, MRCM_ERR_CANCELLED, or the error that stopped it).
+ * Unknown tickets give MRCM_ERR_INVALID_ARG. */
+mrcm_status mrcm_poll(mrcm_server_handle s, uint64_t ticket, double* p_out, mrcm_result* result, int32_t* done);
+
+/* Cancel a queued request (it finishes at once as MRCM_ERR_CANCELLED) or ask a running one to stop
+ * at its next GMRES step. */
+mrcm_status mrcm_cancel(mrcm_server_handle s, uint64_t ticket);
+
+/* counts[5]: submitted, queued, running, completed, failed (including cancelled).  The latencies
+ * (ms, submit to completion) of completed requests, in completion order, are copied to latency_ms
+ * (up to cap; *len receives the total).  *arena_peak receives the largest arena use so far. */
+mrcm_status mrcm_server_stats(mrcm_server_handle s, int64_t* counts, double* latency_ms, size_t cap, size_t* len,
+                              size_t* arena_peak);
+
+/* Waits for running requests to finish, drops queued ones, releases host resources. */
+void mrcm_server_destroy(mrcm_server_handle s);
 
 /* ||b - A p||_2 (the true residual that mrcm_gmres_solve reports in result->abs_res), for callers
  * that cannot allocate device memory: code running inside a CUDA graph capture or a real-time loop

@@ -14,7 +14,7 @@ OBJDIR = os.path.join(ROOT, "_build", "libmrcm")
 LIB = os.path.join(LIBDIR, "libmrcm.so")
 
 CUDA_SOURCES = ["api.cu", "k_grid.cu", "k_local.cu", "k_coarse.cu", "k_krylov.cu", "noalloc.cu"]
-CXX_SOURCES = ["plan.cpp"]
+CXX_SOURCES = ["plan.cpp", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -59,7 +59,7 @@ def build(force=False, verbose=False):
                      os.path.join(CSRC, src), "-o", obj])
     for src in CXX_SOURCES:
         obj = os.path.join(OBJDIR, src.replace(".cpp", ".o"))
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I" + os.path.join(cuda, "include"), "-c",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I" + os.path.join(cuda, "include"), "-c",
                      os.path.join(CSRC, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))

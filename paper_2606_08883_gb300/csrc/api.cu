@@ -182,6 +182,7 @@ const char* mrcm_status_string(mrcm_status s) {
     case MRCM_ERR_CUDA: return "CUDA error";
     case MRCM_ERR_BUSY: return "busy";
     case MRCM_ERR_UNSUPPORTED: return "unsupported on the GPU path";
+    case MRCM_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }
@@ -434,6 +435,8 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
   result->iterations = 0;
   result->restarts = 0;
   result->status = MRCM_OK;
+  result->latency_ms = 0.0;
+  result->queue_ms = 0.0;
   double hb[2] = {0, 0};
   CK(h, launch_norm2(bb, n, partials, counter, bnorm_d, st));
   CK(h, cudaMemcpyAsync(hb, bnorm_d, 8, cudaMemcpyDeviceToHost, st));
@@ -506,6 +509,10 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
       CK(h, cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
       if (hflag & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "grid barrier in the Arnoldi step timed out");
+      if (h->cancel && *h->cancel) {
+        result->iterations = it;
+        return fail(h, MRCM_ERR_CANCELLED, "cancelled");
+      }
       hist.push_back(ho[0]);
       k = j + 1;
       const bool breakdown = ho[1] <= 1e-14 * ho[2];

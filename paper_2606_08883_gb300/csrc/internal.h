@@ -117,6 +117,7 @@ struct mrcm_ctx {
   int coarse_n;       // 2E
   std::vector<int> tab_host;  // plan tables uploaded to the device
   bool keep_z0 = false;       // keep the last multiscale solution for debug reads
+  const volatile int* cancel = nullptr;  // set by the request server; checked once per GMRES step
   // phase profiler
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;

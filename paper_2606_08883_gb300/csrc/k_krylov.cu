@@ -372,14 +372,19 @@ __global__ void __launch_bounds__(512) k_arnoldi_ls(Geo g, LsArgs a) {
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
                            double* sn, double* gv, double* out, double* wbuf, double* part, double* tot, double* Tm,
                            unsigned* bar, int* flags, cudaStream_t st) {
-  static int sms = 0, per_sm = 0;
-  if (sms == 0) {
+  struct Occ {
+    int sms = 0, per_sm = 0;
+  };
+  static const Occ occ = [] {  // thread-safe one-time initialisation (request workers call this)
+    Occ o;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_arnoldi_ls, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 4 * 260);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi_ls, 512, 8 * 4 * 260);
-  }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, k_arnoldi_ls, 512, 8 * 4 * 260);
+    return o;
+  }();
+  const int sms = occ.sms, per_sm = occ.per_sm;
   int grid = (int)std::min<size_t>((size_t)sms, (n + 511) / 512);
   if (grid < 1) grid = 1;
   if (grid > ARNOLDI_MAX_BLOCKS || per_sm < 1 || ldh > 257) return cudaErrorNotSupported;

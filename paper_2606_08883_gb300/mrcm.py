@@ -21,7 +21,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = C.CDLL(_LIB_PATH)
 
 MRCM_OK, MRCM_ERR_INVALID_ARG, MRCM_ERR_OOM, MRCM_ERR_SINGULAR, MRCM_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
-MRCM_ERR_TIMEOUT, MRCM_ERR_CUDA, MRCM_ERR_BUSY, MRCM_ERR_UNSUPPORTED = 5, 6, 7, 8
+MRCM_ERR_TIMEOUT, MRCM_ERR_CUDA, MRCM_ERR_BUSY, MRCM_ERR_UNSUPPORTED, MRCM_ERR_CANCELLED = 5, 6, 7, 8, 9
 MRCM_BC_DIRICHLET, MRCM_BC_NEUMANN = 0, 1
 MRCM_PREC_FP64, MRCM_PREC_FP32 = 0, 1
 MRCM_DBG_TRANS, MRCM_DBG_PHI, MRCM_DBG_PSI, MRCM_DBG_MOMENTS, MRCM_DBG_G, MRCM_DBG_COARSE, MRCM_DBG_ZMRCM = range(7)
@@ -41,7 +41,8 @@ class mrcm_params(C.Structure):
 class mrcm_result(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("status", C.c_int32),
                 ("history_len", C.c_int32), ("abs_res", C.c_double), ("rel_res", C.c_double),
-                ("bnorm", C.c_double), ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int32)]
+                ("bnorm", C.c_double), ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int32),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double)]
 
 
 _P, _Q, _R = C.POINTER(mrcm_problem), C.POINTER(mrcm_params), C.POINTER(mrcm_result)
@@ -65,6 +66,13 @@ _SIGS = {
     "mrcm_profile_read": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "mrcm_launch_count": ([], C.c_int64),
     "mrcm_residual_norm_noalloc": ([_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "mrcm_server_create": ([C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "mrcm_submit": ([C.c_void_p, _P, _Q, C.POINTER(C.c_uint64)], C.c_int),
+    "mrcm_poll": ([C.c_void_p, C.c_uint64, C.c_void_p, _R, C.POINTER(C.c_int32)], C.c_int),
+    "mrcm_cancel": ([C.c_void_p, C.c_uint64], C.c_int),
+    "mrcm_server_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_size_t,
+                           C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
+    "mrcm_server_destroy": ([C.c_void_p], None),
 }
 PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
           "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
@@ -254,6 +262,78 @@ class Solver:
     def close(self):
         if getattr(self, "handle", None):
             mrcm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server over a caller-owned device arena (a torch tensor)."""
+
+    def __init__(self, arena_bytes, max_inflight=4, device="cuda"):
+        import torch
+        self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8, device=device)
+        base = (self.arena.data_ptr() + 255) // 256 * 256
+        self.handle = C.c_void_p()
+        _check(mrcm_server_create(C.c_void_p(base), arena_bytes, max_inflight, C.byref(self.handle)))
+        self._keep = {}
+
+    def submit(self, problem, params):
+        """Queue a solve of a ``workloads.Problem`` (host numpy data); returns the ticket."""
+        K = np.ascontiguousarray(problem.K, dtype=np.float64).ravel()
+        bcs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64).ravel() for v in problem.bc_val]
+        f = None if problem.f is None else np.ascontiguousarray(problem.f, dtype=np.float64).ravel()
+        p = make_problem(problem, K.ctypes.data, [0 if v is None else v.ctypes.data for v in bcs],
+                         0 if f is None else f.ctypes.data)
+        q = make_params(params)
+        t = C.c_uint64()
+        _check(mrcm_submit(self.handle, C.byref(p), C.byref(q), C.byref(t)))
+        self._keep[t.value] = int(np.prod(problem.n))
+        return t.value
+
+    def poll(self, ticket, history_cap=0):
+        """None while running; else (status, p (numpy), info)."""
+        n = self._keep[ticket]
+        p = np.empty(n)
+        hist = (C.c_double * max(history_cap, 1))()
+        res = mrcm_result()
+        res.history = C.cast(hist, C.POINTER(C.c_double)) if history_cap else None
+        res.history_cap = history_cap
+        done = C.c_int32(0)
+        rc = mrcm_poll(self.handle, ticket, C.c_void_p(p.ctypes.data), C.byref(res), C.byref(done))
+        if not done.value:
+            if rc != MRCM_OK:
+                _check(rc)
+            return None
+        del self._keep[ticket]
+        info = {"iterations": res.iterations, "restarts": res.restarts, "abs_res": res.abs_res,
+                "rel_res": res.rel_res, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms,
+                "history": [hist[i] for i in range(res.history_len)]}
+        return rc, p, info
+
+    def cancel(self, ticket):
+        _check(mrcm_cancel(self.handle, ticket))
+
+    def stats(self):
+        counts = (C.c_int64 * 5)()
+        n = C.c_size_t(0)
+        peak = C.c_size_t(0)
+        _check(mrcm_server_stats(self.handle, counts, None, 0, C.byref(n), C.byref(peak)))
+        lat = (C.c_double * max(n.value, 1))()
+        _check(mrcm_server_stats(self.handle, counts, lat, n.value, C.byref(n), C.byref(peak)))
+        keys = ("submitted", "queued", "running", "completed", "failed")
+        out = {k: counts[i] for i, k in enumerate(keys)}
+        out["latency_ms"] = [lat[i] for i in range(n.value)]
+        out["arena_peak"] = peak.value
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mrcm_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
