@@ -53,9 +53,25 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(rank):
+    """Each rank solves its own independent problem (weak scaling): seed 1 + rank."""
+    return 1 + int(rank)
+
+
+def aggregate(total_ms, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput: the slowest rank's timed region (MAX over ranks) bounds the job, and
+    every rank solved `steps` problems.  Returns (solves/s over all ranks, max total ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def workload(args, rank=0):
     from paper_2606_08883_gb300 import workloads as W
-    prob, q = W.channels(args.N, seed=1 + rank, prec=W.PREC_FP32 if args.prec == "fp32" else W.PREC_FP64)
+    prob, q = W.channels(args.N, seed=rank_seed(rank), prec=W.PREC_FP32 if args.prec == "fp32" else W.PREC_FP64)
     q.restart = args.restart
     q.max_iter = 3 * args.restart
     return prob, q
@@ -302,12 +318,7 @@ def mrcm_arm(args):
     clk = clocks.stop()
     prof = solver.profile_read(reset=True)
     solver.profile(False)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = aggregate(sum(times), args.steps, world, dist, dev)
     # set-up / solve split from one profiled-free step
     torch.cuda.synchronize(dev)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -331,12 +342,8 @@ def mrcm_arm(args):
             solver.solve_host(K_host, p_host)
         torch.cuda.synchronize(dev)
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.cells,
+        e2e_value, _ = aggregate(1e3 * (time.perf_counter() - t0), args.steps, world, dist, dev)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.cells,
                "d2h_bytes_per_step": 8 * prob.cells}
     if rank != 0:
         if world > 1:
