@@ -1,10 +1,9 @@
 // mrcm_residual_norm_noalloc: the true-residual norm ||b - A p||_2 of the GMRES stopping test,
 // for callers that cannot allocate device memory.
 //
-// Who needs it: code that runs where device allocation is not allowed or not possible -- inside a
-// region being captured into a CUDA graph, in a real-time loop that must not touch the allocator,
-// or in a host process that only receives device pointers from another component and owns no
-// allocator of its own.  mrcm_gmres_solve computes the same quantity with reduction scratch carved
+// Who needs it: code that runs where device allocation is not allowed or not possible -- in a
+// real-time loop that must not touch the allocator, or in a host process that only receives device
+// pointers from another component and owns no allocator of its own.  mrcm_gmres_solve computes the same quantity with reduction scratch carved
 // from the handle's workspace; this entry point keeps its scratch in a fixed device array that is
 // part of the library image instead, so a call allocates nothing.
 //
