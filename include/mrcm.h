@@ -214,8 +214,9 @@ mrcm_status mrcm_submit(mrcm_server_handle s, const mrcm_problem* problem, const
 /* Non-blocking.  *done = 0 while queued or running.  Once finished, *done = 1, the solution (n
  * doubles) is copied to the host array p_out (if not NULL), result is filled (history up to its
  * capacity, latency_ms and queue_ms), the request is forgotten, and the request's own status is
- * returned (MRCM_OK, MRCM_ERR_NOT_CONVERGED, MRCM_ERR_CANCELLED, or the error that stopped it).
- * Unknown tickets give MRCM_ERR_INVALID_ARG. */
+ * returned (MRCM_OK, MRCM_ERR_NOT_CONVERGED, MRCM_ERR_CANCELLED, or the error that stopped it);
+ * for a status other than MRCM_OK its message is then readable with mrcm_last_error(NULL) on the
+ * calling thread.  Unknown tickets give MRCM_ERR_INVALID_ARG. */
 mrcm_status mrcm_poll(mrcm_server_handle s, uint64_t ticket, double* p_out, mrcm_result* result, int32_t* done);
 
 /* Cancel a queued request (it finishes at once as MRCM_ERR_CANCELLED) or ask a running one to stop
@@ -232,13 +233,12 @@ mrcm_status mrcm_server_stats(mrcm_server_handle s, int64_t* counts, double* lat
 void mrcm_server_destroy(mrcm_server_handle s);
 
 /* ||b - A p||_2 (the true residual that mrcm_gmres_solve reports in result->abs_res), for callers
- * that cannot allocate device memory: code running inside a CUDA graph capture or a real-time loop
- * that must not touch an allocator, or a component that is handed device pointers but owns no
- * allocator.  The paper has no counterpart; it is a library service around the GMRES stopping test.
+ * that cannot allocate device memory: a real-time loop that must not touch an allocator, or a
+ * component that is handed device pointers but owns no allocator.  The paper has no counterpart; it is a library service around the GMRES stopping test.
  * Allocates nothing: its scratch (the residual vector and the reduction partial sums) is a fixed
  * array of 8 MiB + 5 KiB compiled into the library, held on every GPU that loads the library
  * until the process exits.  The first call on a device looks up that array's device address and
- * caches it; make that first call before any stream capture.  Grids of more than 1,048,576 cells
+ * caches it.  Grids of more than 1,048,576 cells
  * are rejected with MRCM_ERR_INVALID_ARG.  b, p: device arrays of n cells; norm_out: device
  * pointer to one double, written when `stream` reaches the launch.  All calls share the one
  * array, so calls that overlap on the GPU (other streams, other threads) race: serialise them.

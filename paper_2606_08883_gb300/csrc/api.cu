@@ -17,9 +17,13 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
 }  // namespace mrcm
 
-namespace {
+static thread_local std::string g_last_error;
 
-thread_local std::string g_last_error;
+namespace mrcm {
+void set_thread_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace mrcm
+
+namespace {
 
 // Phase brackets: a (start, stop) event pair per kernel group while profiling is enabled.
 struct Phase {
@@ -431,6 +435,10 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
   unsigned* bar = counter + 1;
   int* flags = at<int>(h, L.flags);
   bool fused = true;  // fused Arnoldi kernel, unless the vector is too long for one co-resident wave
+  if (!h->rb) {
+    CK(h, cudaHostAlloc(reinterpret_cast<void**>(&h->rb), 2 * sizeof(mrcm_ctx::StepReadback), cudaHostAllocDefault));
+    for (cudaEvent_t& e : h->rb_ev) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   std::vector<double> hist;
   result->iterations = 0;
   result->restarts = 0;
@@ -474,52 +482,65 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
     CK(h, cudaMemsetAsync(gv, 0, 8 * (m + 1), st));
     k_set<<<1, 1, 0, st>>>(gv, beta);
     CK(h, cudaGetLastError());
+    // Steps are pipelined by one: step j+1 is enqueued before the host reads step j's residual
+    // estimate, so the device never waits for the host.  When step j ends the cycle, the extra step
+    // has only written V_{j+2}, Z_{j+1}, column j+1 of H, rotation j+1 and g_{j+1..j+2}, none of
+    // which the solution update over columns 0..j reads.
     int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double* vj = V + (size_t)j * n;
-      double* zj = Z + (size_t)j * n;
-      mrcm_status rc = apply_T(h, vj, zj, st);
-      if (rc != MRCM_OK) return rc;
-      ++it;
-      double* col = H + (size_t)j * ldh;
-      {
-        Phase ph(h, MRCM_PH_KRYLOV, st);
-        cudaError_t ea = cudaErrorNotSupported;
-        if (fused)
-          ea = launch_arnoldi(g, zj, V, j, n, H, ldh, cs, sn, gv, out, w, at<double>(h, L.apart), at<double>(h, L.atot),
-                              at<double>(h, L.aT), bar, flags, st);
-        if (ea == cudaErrorNotSupported) {
-          fused = false;
-          (void)cudaGetLastError();
-          CK(h, launch_matvec_dot(g, zj, V, w, partials, counter, col, st));
-          // launch_matvec_dot writes (w, v0) to col[0] and ||w||^2 to col[1]; move the latter
-          CK(h, cudaMemcpyAsync(wn2, col + 1, 8, cudaMemcpyDeviceToDevice, st));
-          for (int i = 1; i <= j; ++i)
-            CK(h, launch_mgs_pass(V + (size_t)(i - 1) * n, col + (i - 1), V + (size_t)i * n, n, w, partials, counter,
-                                  col + i, 0, st));
-          CK(h, launch_mgs_pass(V + (size_t)j * n, col + j, nullptr, n, w, partials, counter, col + j + 1, 1, st));
-          CK(h, launch_givens(H, cs, sn, gv, j, ldh, wn2, out, st));
-        } else {
-          CK(h, ea);
+    int pend = -1;  // step whose read-back is in flight
+    for (int j = 0; j <= m; ++j) {
+      const bool launch = j < m && it + (pend >= 0 ? 1 : 0) < h->prm.max_iter;
+      if (launch) {
+        double* vj = V + (size_t)j * n;
+        double* zj = Z + (size_t)j * n;
+        mrcm_status rc = apply_T(h, vj, zj, st);
+        if (rc != MRCM_OK) return rc;
+        double* col = H + (size_t)j * ldh;
+        {
+          Phase ph(h, MRCM_PH_KRYLOV, st);
+          cudaError_t ea = cudaErrorNotSupported;
+          if (fused)
+            ea = launch_arnoldi(g, zj, V, j, n, H, ldh, cs, sn, gv, out, w, at<double>(h, L.apart),
+                                at<double>(h, L.atot), at<double>(h, L.aT), bar, flags, st);
+          if (ea == cudaErrorNotSupported) {
+            fused = false;
+            (void)cudaGetLastError();
+            CK(h, launch_matvec_dot(g, zj, V, w, partials, counter, col, st));
+            // launch_matvec_dot writes (w, v0) to col[0] and ||w||^2 to col[1]; move the latter
+            CK(h, cudaMemcpyAsync(wn2, col + 1, 8, cudaMemcpyDeviceToDevice, st));
+            for (int i = 1; i <= j; ++i)
+              CK(h, launch_mgs_pass(V + (size_t)(i - 1) * n, col + (i - 1), V + (size_t)i * n, n, w, partials, counter,
+                                    col + i, 0, st));
+            CK(h, launch_mgs_pass(V + (size_t)j * n, col + j, nullptr, n, w, partials, counter, col + j + 1, 1, st));
+            CK(h, launch_givens(H, cs, sn, gv, j, ldh, wn2, out, st));
+            // v_{j+1} = w / h_{j+1,j}; the rotation has zeroed col[j+1], out[1] keeps the value
+            CK(h, launch_scale(w, out + 1, n, V + (size_t)(j + 1) * n, st));
+          } else {
+            CK(h, ea);
+          }
         }
+        mrcm_ctx::StepReadback* slot = h->rb + (j & 1);
+        CK(h, cudaMemcpyAsync(slot->out, out, 24, cudaMemcpyDeviceToHost, st));
+        CK(h, cudaMemcpyAsync(&slot->flags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(h, cudaEventRecord(h->rb_ev[j & 1], st));
       }
-      double ho[3];
-      int hflag = 0;
-      CK(h, cudaMemcpyAsync(ho, out, 24, cudaMemcpyDeviceToHost, st));
-      CK(h, cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(h, cudaStreamSynchronize(st));
-      if (hflag & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "grid barrier in the Arnoldi step timed out");
-      if (h->cancel && *h->cancel) {
-        result->iterations = it;
-        return fail(h, MRCM_ERR_CANCELLED, "cancelled");
+      if (pend >= 0) {
+        CK(h, cudaEventSynchronize(h->rb_ev[pend & 1]));
+        const mrcm_ctx::StepReadback* slot = h->rb + (pend & 1);
+        const double ho[3] = {slot->out[0], slot->out[1], slot->out[2]};
+        ++it;
+        if (slot->flags & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "grid barrier in the Arnoldi step timed out");
+        if (h->cancel && *h->cancel) {
+          result->iterations = it;
+          return fail(h, MRCM_ERR_CANCELLED, "cancelled");
+        }
+        hist.push_back(ho[0]);
+        k = pend + 1;
+        const bool breakdown = ho[1] <= 1e-14 * ho[2];
+        if (ho[0] <= tol_abs || breakdown || it >= h->prm.max_iter) break;
       }
-      hist.push_back(ho[0]);
-      k = j + 1;
-      const bool breakdown = ho[1] <= 1e-14 * ho[2];
-      if (ho[0] <= tol_abs || breakdown || it >= h->prm.max_iter) break;
-      // v_{j+1} = w / h_{j+1,j} (the fused kernel writes it itself); the rotation has already
-      // zeroed col[j+1], out[1] keeps the value
-      if (!fused) CK(h, launch_scale(w, out + 1, n, V + (size_t)(j + 1) * n, st));
+      if (!launch) break;
+      pend = j;
     }
     CK(h, launch_update(p, Z, n, H, gv, k, ldh, st));
     CK(h, launch_residual_norm(g, bb, p, V, partials, counter, beta_d, st));

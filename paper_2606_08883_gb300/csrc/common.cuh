@@ -7,6 +7,25 @@
 
 namespace mrcm {
 
+// Raises kernel K's dynamic shared-memory limit to the device maximum, once per kernel and
+// process (thread-safe).  Launches then pass their own size: the limit only gates launches and
+// does not change occupancy, and a limit that never moves cannot be lowered by another thread
+// between its own set and launch (request workers launch the same kernels with different sizes).
+template <auto K>
+cudaError_t raise_smem_limit() {
+  static const cudaError_t err = [] {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, K);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+  }();
+  return err;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -125,13 +125,27 @@ struct mrcm_ctx {
   size_t ev_used = 0;          // pairs recorded since the last read
   double ph_ms[MRCM_PHASES] = {0};
   long long ph_launch[MRCM_PHASES] = {0};
+  // GMRES step read-back: pinned slots so that step j's residual estimate is read while step j+1
+  // runs (created on the first solve)
+  struct StepReadback {
+    double out[4];
+    int flags;
+    int pad;
+  };
+  StepReadback* rb = nullptr;
+  cudaEvent_t rb_ev[2] = {nullptr, nullptr};
   ~mrcm_ctx() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : rb_ev)
+      if (e) cudaEventDestroy(e);
+    if (rb) cudaFreeHost(rb);
   }
 };
 
 namespace mrcm {
 void count_launch(int kernels);
+// message returned by mrcm_last_error(NULL) on the calling thread
+void set_thread_error(const std::string& msg);
 // kernel launchers (k_*.cu)
 cudaError_t launch_assemble(const Geo& g, const int* bc_kind, const double* const* bcv, const double* f,
                             double* Tx, double* Ty, double* b, cudaStream_t st);

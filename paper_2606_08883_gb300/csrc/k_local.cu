@@ -189,11 +189,13 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
   const int S = g.mx * g.my;
   const size_t sm = factor_smem_bytes(w, fp32);
   if (fp32) {
-    cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const cudaError_t e = raise_smem_limit<k_factor<float>>();
+    if (e != cudaSuccess) return e;
     k_factor<float><<<S, 256, sm, st>>>(g, kind, LS, (float*)Linv, flags);
     count_launch(1);
   } else {
-    cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const cudaError_t e = raise_smem_limit<k_factor<double>>();
+    if (e != cudaSuccess) return e;
     k_factor<double><<<S, 256, sm, st>>>(g, kind, LS, (double*)Linv, flags);
     count_launch(1);
   }
@@ -533,7 +535,7 @@ static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
 
 template <typename T, int MODE, int NR, int NBUF>
 static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_solve<T, MODE, NR, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const cudaError_t e = raise_smem_limit<k_solve<T, MODE, NR, NBUF>>();
   if (e != cudaSuccess) return e;
   k_solve<T, MODE, NR, NBUF><<<g.mx * g.my, 256, sm, st>>>(g, a);
   count_launch(1);

@@ -334,6 +334,7 @@ mrcm_status mrcm_poll(mrcm_server_handle S, uint64_t ticket, double* p_out, mrcm
     result->queue_ms = r->state == FINISHED && r->t_start.time_since_epoch().count() ? ms_since(r->t_submit, r->t_start) : 0.0;
     result->status = r->status;
   }
+  if (r->status != MRCM_OK) mrcm::set_thread_error(r->err);
   return r->status;
 }
 

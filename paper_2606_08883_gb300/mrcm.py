@@ -313,6 +313,8 @@ class Server:
         info = {"iterations": res.iterations, "restarts": res.restarts, "abs_res": res.abs_res,
                 "rel_res": res.rel_res, "latency_ms": res.latency_ms, "queue_ms": res.queue_ms,
                 "history": [hist[i] for i in range(res.history_len)]}
+        if rc != MRCM_OK:
+            info["error"] = (mrcm_last_error(None) or b"").decode()
         return rc, p, info
 
     def cancel(self, ticket):

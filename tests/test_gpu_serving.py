@@ -54,7 +54,8 @@ def test_results_identical_alone_and_in_the_mix(mrcm):
     tickets = [srv.submit(p, q) for (p, q) in mix]
     results = _wait(srv, tickets)
     st = srv.stats()
-    assert st["completed"] == len(mix) and st["failed"] == 0 and len(st["latency_ms"]) == len(mix)
+    bad = [(prob.name, results[t][2].get("error")) for t, (prob, q) in zip(tickets, mix) if results[t][0] != mrcm.MRCM_OK]
+    assert st["completed"] == len(mix) and st["failed"] == 0 and len(st["latency_ms"]) == len(mix), bad
     assert 0 < st["arena_peak"] <= 2 << 30
     srv.close()
     for t, (prob, q) in zip(tickets, mix):
