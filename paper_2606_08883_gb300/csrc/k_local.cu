@@ -2,17 +2,22 @@
 // overlapping-Schwarz local solves.  One CTA per subdomain.
 //
 // A box of width w (x) and height h (lines along x, x fastest) has a block-tridiagonal operator:
-// tridiagonal line blocks D_J and diagonal couplings -E_J between lines J-1 and J.  Its block
-// LDL^T factorisation has the Schur complements S_0 = D_0, S_J = D_J - E_J S_{J-1}^-1 E_J as the
-// block diagonal and -E_J S_{J-1}^-1 below it, so only the inverses S_J^-1 are stored (symmetric,
-// packed lower triangle, one line block per line):
-//   factor  S_J as above, S_J = L L^T (Cholesky), L^-1, S_J^-1 = L^-T L^-1
-//   forward u_0 = b_0, u_J = b_J + E_J S_{J-1}^-1 u_{J-1}
-//   back    x_last = S_last^-1 u_last, x_J = S_J^-1 (u_J + E_{J+1} x_{J+1})
-// Each solve streams every line block once forward and once backward through a cp.async pipeline
-// of 2-8 line blocks; every step is one symmetric matrix-vector product with the same w products
-// per row (four threads per row) whose epilogue forms the next step's input, so a step costs one
-// barrier.
+// tridiagonal line blocks D_J and diagonal couplings -E_J between lines J-1 and J.  It is
+// factored from both ends towards the middle line m = h/2 (a twisted block LDL^T):
+//   top     S_0 = D_0,          S_J = D_J - E_J S_{J-1}^-1 E_J            J = 1 .. m-1
+//   bottom  S_{h-1} = D_{h-1},  S_J = D_J - E_{J+1} S_{J+1}^-1 E_{J+1}    J = h-2 .. m+1
+//   middle  S_m = D_m - E_m S_{m-1}^-1 E_m - E_{m+1} S_{m+1}^-1 E_{m+1}
+// and only the inverses S_J^-1 are stored (symmetric, packed lower triangle, one line block per
+// line; each by Cholesky S_J = L L^T, L^-1, S_J^-1 = L^-T L^-1).  A solve eliminates from both ends
+//   u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (top),  u_J = b_J + E_{J+1} S_{J+1}^-1 u_{J+1} (bottom),
+//   x_m = S_m^-1 u_m with u_m = b_m + E_m S_{m-1}^-1 u_{m-1} + E_{m+1} S_{m+1}^-1 u_{m+1},
+// and substitutes back outwards: x_J = S_J^-1 (u_J + E_{J+1} x_{J+1}) above the middle,
+// x_J = S_J^-1 (u_J + E_J x_{J-1}) below it.  The two ends run in the same step, so a solve is
+// about h/2 + 1 + h/2 steps deep instead of 2h - 1, and a restricted Schwarz solve stops its back
+// substitution at the first and last lines it keeps (the oversampling lines are never formed).
+// Every step streams its (up to two) line blocks through a cp.async pipeline and is one or two
+// symmetric matrix-vector products whose epilogue forms the next step's input, so a step costs
+// one barrier.
 //
 // Oversampled boxes are padded to the full (sub + 2l)^2 size; cells outside the grid get identity
 // rows with zero couplings and zero data, which leaves the clipped region's solution unchanged.
@@ -108,20 +113,44 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   if (tid == 0) bad = 0;
   T* out = Linv + (size_t)s * b.h * LS;
   const int npk = w * (w + 1) / 2;
-  for (int J = 0; J < b.h; ++J) {
-    // (1) S_J = D_J - E_J S_{J-1}^-1 E_J, lower triangle
+  const int h = b.h, m = h / 2;
+  T* ev2 = rinv + w;                       // second coupling vector (middle line)
+  // processing order: top lines 0..m-1, bottom lines h-1..m+1, then the middle line m
+  for (int step = 0; step < h; ++step) {
+    const bool top = step < m, bottom = !top && step < h - 1;
+    const int J = top ? step : (bottom ? h - 1 - (step - m) : m);
+    // previous line of the same recursion and its coupling vector: top uses E_J = eup(J),
+    // bottom uses E_{J+1} = eup(J+1)
+    const bool has_prev = top ? J > 0 : (bottom ? J < h - 1 : false);
+    // (1) S_J = D_J - E S_prev^-1 E (middle: minus both sides), lower triangle
     for (int i = tid; i < w; i += nt) {
       double d, o, e;
       line_coeffs(g, b, robin, J, i, d, o, e);
-      ev[i] = (T)e;
       Sm[i * w + i] = (T)d;
       if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
+      if (top) {
+        ev[i] = (T)e;
+      } else if (bottom) {
+        double d2, o2, e2;
+        line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+        ev[i] = (T)e2;
+      } else {
+        ev[i] = (T)e;                      // E_m (towards line m-1)
+        double d2, o2, e2 = 0.0;
+        if (J + 1 < h) line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+        ev2[i] = (T)e2;                    // E_{m+1} (towards line m+1)
+      }
     }
     __syncthreads();
+    const bool mid_up = !top && !bottom && m > 0;          // S_{m-1}^-1 from the stored top line
+    const bool mid_dn = !top && !bottom && m + 1 < h;      // S_{m+1}^-1 still in Sp
+    const T* Sup = out + (size_t)(m > 0 ? m - 1 : 0) * LS;
     for (int k = tid; k < npk; k += nt) {
       const int i = tri_row(k), j = k - i * (i + 1) / 2;
       T v = (i == j || i == j + 1) ? Sm[i * w + j] : (T)0;
-      if (J > 0) v -= ev[i] * ev[j] * Sp[i * w + j];
+      if (has_prev) v -= ev[i] * ev[j] * Sp[i * w + j];
+      if (mid_up) v -= ev[i] * ev[j] * Sup[k];
+      if (mid_dn) v -= ev2[i] * ev2[j] * Sp[i * w + j];
       Sm[i * w + j] = v;
     }
     __syncthreads();
@@ -180,7 +209,7 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
 
 size_t factor_smem_bytes(int w, bool fp32) {
   const size_t e = fp32 ? 4 : 8;
-  return e * (4 * (size_t)w * w + 2 * (size_t)w) + 16;
+  return e * (4 * (size_t)w * w + 3 * (size_t)w) + 16;
 }
 
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
@@ -255,31 +284,46 @@ __device__ __forceinline__ bool robin_side(const Geo& g, int s, int k) {
 }
 
 
-// S x for symmetric S in packed storage (see gemv_sym); epi(i, r, value) is called once per
-// output by the q == 0 thread of row i, so a step can produce the next step's input directly.
+// Threads per row of a line product: FP64 runs against the DFMA pipe, so two threads per row keep
+// the shuffle adds to one per output; FP32 runs against latency, so four threads shorten the chain.
+template <typename T>
+struct LineTPR {
+  static constexpr int value = sizeof(T) == 8 ? 2 : 4;
+};
+
+// Up to two symmetric products per step, S_A x_A (threads [0, w TPR)) and S_B x_B (threads
+// [w TPR, 2 w TPR)), S in packed lower storage.  Every thread of the block reaches the shuffles (a
+// product that is off this step, or a thread past the rows, contributes zeros); epi(half, i, r, v)
+// is called once per output by the first thread of row i, so a step can produce the next step's
+// input directly.
 template <typename T, int NR, class Epi>
-__device__ __forceinline__ void gemv_sym_epi(const T* P, const T* in, int w, Epi epi) {
-  const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
-  if ((threadIdx.x >> 5) * 8 >= w) return;
+__device__ __forceinline__ void gemv_pair(const T* PA, const T* inA, bool onA, const T* PB, const T* inB, bool onB,
+                                          int w, Epi epi) {
+  constexpr int TPR = LineTPR<T>::value;
+  const int r0 = threadIdx.x / TPR, q = threadIdx.x % TPR;
+  const int half = r0 >= w ? 1 : 0;
+  const int i = r0 - half * w;
+  const bool on = (half == 0 ? onA : onB) && r0 < 2 * w;
+  const T* P = half == 0 ? PA : PB;
+  const T* in = half == 0 ? inA : inB;
   T acc[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) acc[r] = 0;
-  if (i < w) {
+  if (on) {
     const T* row = P + i * (i + 1) / 2;
-    for (int c = q; c < w; c += 4) {
+    for (int c = q; c < w; c += TPR) {
       const T sv = c <= i ? row[c] : P[c * (c + 1) / 2 + i];
 #pragma unroll
       for (int r = 0; r < NR; ++r) acc[r] += sv * in[c * NR + r];
     }
   }
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 1);
-    acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], 2);
-  }
-  if (i < w && q == 0) {
+  for (int r = 0; r < NR; ++r)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) epi(i, r, acc[r]);
+    for (int o = TPR / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (on && q == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) epi(half, i, r, acc[r]);
   }
 }
 
@@ -290,30 +334,72 @@ __device__ __forceinline__ void issue_line(T* buf, const T* src, int LS, bool va
     for (int c = threadIdx.x; c < nch; c += blockDim.x)
       cp_async16(reinterpret_cast<unsigned char*>(buf) + 16 * c, reinterpret_cast<const unsigned char*>(src) + 16 * c);
   }
-  cp_async_commit();  // one group per step, empty past the last line, so the wait count stays uniform
 }
 
-// NBUF line blocks in flight (prefetch distance NBUF - 1).
+// Line blocks used by step st of a twisted solve (-1: none).  Steps 0..nf-1 eliminate (top line t,
+// bottom line h-1-t), step nf is the middle line, the rest substitute back (m-1-t, m+1+t) down to
+// line lo_keep and up to line hi_keep.
+struct Twist {
+  int h, m, nf, nb, lo_keep, hi_keep;
+  __device__ __forceinline__ void lines(int st, int& A, int& B) const {
+    if (st < nf) {
+      A = st < m ? st : -1;
+      B = h - 1 - st >= m + 1 ? h - 1 - st : -1;
+    } else if (st == nf) {
+      A = m;
+      B = -1;
+    } else {
+      const int t = st - nf - 1;
+      A = m - 1 - t >= lo_keep ? m - 1 - t : -1;
+      B = m + 1 + t <= hi_keep ? m + 1 + t : -1;
+    }
+  }
+};
+
+// NBUF steps of line blocks in flight (two blocks per step; prefetch distance NBUF - 1).
 template <typename T, int MODE, int NR, int NBUF>
-__global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
+__global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
-  T* Lb = reinterpret_cast<T*>(smem_raw);   // [NBUF][LS] line blocks
-  T* Y = Lb + NBUF * LS;                     // [hgt][w][NR]: b, then u (forward), then x (backward)
-  T* tvA = Y + (size_t)hgt * w * NR;         // [w][NR] ping-pong inputs of the backward steps
-  T* tvB = tvA + w * NR;
-  T* xl = tvB + w * NR;                      // [w][NR] x of the last line
-  T* Ec = xl + w * NR;                       // [hgt][w] line couplings
+  T* Lb = reinterpret_cast<T*>(smem_raw);    // [NBUF][2][LS] line blocks
+  T* Y = Lb + 2 * NBUF * LS;                 // [hgt][w][NR]: b, then u (elimination), then x (back)
+  T* tv = Y + (size_t)hgt * w * NR;          // [4][w][NR] ping-pong inputs of the back steps (top, bottom)
+  T* xm = tv + 4 * w * NR;                   // [w][NR] x of the middle line
+  T* cb = xm + w * NR;                       // [w][NR] bottom contribution to the middle (odd h)
+  T* Ec = cb + w * NR;                       // [hgt][w] line couplings
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * hgt * LS;
-  // forward prologue: lines 0 .. NBUF-2 in flight while the right-hand sides are set up
-  for (int p = 0; p < NBUF - 1; ++p) issue_line(Lb + (p % NBUF) * LS, Lg + (size_t)p * LS, LS, p < hgt);
+  Twist tw;
+  tw.h = hgt;
+  tw.m = hgt / 2;
+  tw.nf = tw.m > hgt - 1 - tw.m ? tw.m : hgt - 1 - tw.m;
+  // a restricted Schwarz solve keeps only the lines of its subdomain
+  tw.lo_keep = MODE == MODE_SCHWARZ ? g.l : 0;
+  tw.hi_keep = MODE == MODE_SCHWARZ ? hgt - 1 - g.l : hgt - 1;
+  {
+    const int nt_ = tw.m - tw.lo_keep, nb_ = tw.hi_keep - tw.m;
+    tw.nb = nt_ > nb_ ? nt_ : nb_;
+    if (tw.nb < 0) tw.nb = 0;
+  }
+  const int nsteps = tw.nf + 1 + tw.nb;
+  auto issue_step = [&](int st) {
+    if (st < nsteps) {
+      int A, B;
+      tw.lines(st, A, B);
+      T* slot = Lb + (size_t)(st % NBUF) * 2 * LS;
+      issue_line(slot, Lg + (size_t)(A > 0 ? A : 0) * LS, LS, A >= 0);
+      issue_line(slot + LS, Lg + (size_t)(B > 0 ? B : 0) * LS, LS, B >= 0);
+    }
+    cp_async_commit();  // one group per step, empty past the last, so the wait count stays uniform
+  };
+  for (int p = 0; p < NBUF - 1; ++p) issue_step(p);  // NBUF = 1: no prefetch, each step loads its own lines
 
   // ---------------- right-hand sides into Y
   for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
+  for (int k = tid; k < w * NR; k += nt) cb[k] = (T)0;
   __syncthreads();
   if (MODE == MODE_PARTICULAR) {
     for (int k = tid; k < hgt * w; k += nt) {
@@ -382,69 +468,84 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
   // couplings between consecutive lines: Ec[J][x] joins line J-1 and line J (J >= 1)
   for (int k = tid; k < hgt * w; k += nt) Ec[k] = (T)couple_up(g, b, k / w, k % w);
 
-  // ---------------- forward sweep: u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (in Y); one barrier per line
-  for (int J = 0; J < hgt; ++J) {
-    cp_async_wait<NBUF - 2>();
-    __syncthreads();
-    {
-      const int nxt = J + NBUF - 1;
-      issue_line(Lb + (nxt % NBUF) * LS, Lg + (size_t)nxt * LS, LS, nxt < hgt);
-    }
-    const T* L = Lb + (J % NBUF) * LS;
-    T* uJ = Y + (size_t)J * w * NR;
-    if (J + 1 < hgt) {
-      T* un = uJ + w * NR;
-      const T* en = Ec + (J + 1) * w;
-      gemv_sym_epi<T, NR>(L, uJ, w, [&](int i, int r, T v) { un[i * NR + r] += en[i] * v; });
+  const int m = tw.m;
+  T* tA0 = tv;                   // top back inputs (ping-pong)
+  T* tA1 = tv + w * NR;
+  T* tB0 = tv + 2 * w * NR;      // bottom back inputs (ping-pong)
+  T* tB1 = tv + 3 * w * NR;
+  for (int st = 0; st < nsteps; ++st) {
+    if constexpr (NBUF == 1) {
+      __syncthreads();  // the previous step is done with the single slot
+      issue_step(st);
+      cp_async_wait<0>();
+      __syncthreads();
     } else {
-      const T* um = uJ - w * NR;   // u of the line before (first backward input), if any
-      const T* el = Ec + J * w;
-      const bool more = hgt >= 2;
-      gemv_sym_epi<T, NR>(L, uJ, w, [&](int i, int r, T v) {
-        xl[i * NR + r] = v;
-        if (more) tvA[i * NR + r] = um[i * NR + r] + el[i] * v;
+      cp_async_wait<NBUF - 2>();
+      __syncthreads();
+      issue_step(st + NBUF - 1);
+    }
+    int A, B;
+    tw.lines(st, A, B);
+    const T* LA = Lb + (size_t)(st % NBUF) * 2 * LS;
+    const T* LBk = LA + LS;
+    if (st < tw.nf) {
+      // ---- elimination: top line A (u_{A+1} += E_{A+1} S_A^-1 u_A), bottom line B
+      //      (u_{B-1} += E_B S_B^-1 u_B); the bottom's last contribution to the middle goes to cb
+      //      when the two ends reach the middle in the same step (odd h)
+      const bool to_cb = B == m + 1 && A == m - 1;
+      gemv_pair<T, NR>(LA, Y + (size_t)(A > 0 ? A : 0) * w * NR, A >= 0, LBk, Y + (size_t)(B > 0 ? B : 0) * w * NR,
+                       B >= 0, w, [&](int half, int i, int r, T v) {
+                         if (half == 0) {
+                           Y[((size_t)(A + 1) * w + i) * NR + r] += Ec[(A + 1) * w + i] * v;
+                         } else {
+                           T* dst = to_cb ? cb : Y + (size_t)(B - 1) * w * NR;
+                           dst[i * NR + r] += Ec[B * w + i] * v;
+                         }
+                       });
+    } else if (st == tw.nf) {
+      // ---- middle line: x_m = S_m^-1 u_m; first back inputs u_{m-1} + E_m x_m, u_{m+1} + E_{m+1} x_m
+      if (hgt & 1) {
+        for (int k = tid; k < w * NR; k += nt) Y[(size_t)m * w * NR + k] += cb[k];
+        __syncthreads();
+      }
+      const bool up = m - 1 >= tw.lo_keep, dn = m + 1 <= tw.hi_keep;
+      gemv_pair<T, NR>(LA, Y + (size_t)m * w * NR, true, LA, Y, false, w, [&](int, int i, int r, T v) {
+        xm[i * NR + r] = v;
+        if (up) tA0[i * NR + r] = Y[((size_t)(m - 1) * w + i) * NR + r] + Ec[m * w + i] * v;
+        if (dn) tB0[i * NR + r] = Y[((size_t)(m + 1) * w + i) * NR + r] + Ec[(m + 1) * w + i] * v;
+      });
+    } else {
+      // ---- back substitution: x_A = S_A^-1 (u_A + E_{A+1} x_{A+1}), x_B = S_B^-1 (u_B + E_B x_{B-1})
+      const int t = st - tw.nf - 1;
+      const T* inA = (t & 1) ? tA1 : tA0;
+      T* nxA = (t & 1) ? tA0 : tA1;
+      const T* inB = (t & 1) ? tB1 : tB0;
+      T* nxB = (t & 1) ? tB0 : tB1;
+      const bool moreA = A - 1 >= tw.lo_keep, moreB = B + 1 <= tw.hi_keep;
+      gemv_pair<T, NR>(LA, inA, A >= 0, LBk, inB, B >= 0, w, [&](int half, int i, int r, T v) {
+        if (half == 0) {
+          Y[((size_t)A * w + i) * NR + r] = v;
+          if (moreA) nxA[i * NR + r] = Y[((size_t)(A - 1) * w + i) * NR + r] + Ec[A * w + i] * v;
+        } else {
+          Y[((size_t)B * w + i) * NR + r] = v;
+          if (moreB) nxB[i * NR + r] = Y[((size_t)(B + 1) * w + i) * NR + r] + Ec[(B + 1) * w + i] * v;
+        }
       });
     }
   }
-  // ---------------- backward sweep: x_J = S_J^-1 (u_J + E_{J+1} x_{J+1}), lines hgt-2 .. 0
   cp_async_wait<0>();
   __syncthreads();
-  for (int p = 0; p < NBUF - 1; ++p) {
-    const int line = hgt - 2 - p;
-    issue_line(Lb + (p % NBUF) * LS, Lg + (size_t)(line > 0 ? line : 0) * LS, LS, line >= 0);
-  }
-  for (int t = 0, J = hgt - 2; J >= 0; ++t, --J) {
-    cp_async_wait<NBUF - 2>();
-    __syncthreads();
-    {
-      const int nt2 = t + NBUF - 1, line = hgt - 2 - nt2;
-      issue_line(Lb + (nt2 % NBUF) * LS, Lg + (size_t)(line > 0 ? line : 0) * LS, LS, line >= 0);
-    }
-    const T* L = Lb + (t % NBUF) * LS;
-    const T* in = (t & 1) ? tvB : tvA;
-    T* nxt = (t & 1) ? tvA : tvB;
-    T* xJ = Y + (size_t)J * w * NR;
-    const T* um = xJ - w * NR;
-    const T* eJ = Ec + J * w;
-    gemv_sym_epi<T, NR>(L, in, w, [&](int i, int r, T v) {
-      xJ[i * NR + r] = v;
-      if (J > 0) nxt[i * NR + r] = um[i * NR + r] + eJ[i] * v;
-    });
-  }
-  cp_async_wait<0>();
-  __syncthreads();
-  for (int k = tid; k < w * NR; k += nt) Y[(size_t)(hgt - 1) * w * NR + k] = xl[k];
+  for (int k = tid; k < w * NR; k += nt) Y[(size_t)m * w * NR + k] = xm[k];
   __syncthreads();
 
   // ---------------- outputs
-  const int lane = tid & 31, wid = tid >> 5;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (MODE == MODE_PARTICULAR) {
     for (int k = tid; k < hgt * w; k += nt) {
       const int J = k / w, x = k % w;
       a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
-    if (wid < 4) {
-      const int kside = wid;
+    for (int kside = wid; kside < 4; kside += nw) {
       double F = 0.0, Pw = 0.0;
       if (robin_side(g, s, kside)) {
         const int len = (kside < 2) ? g.sy : g.sx;
@@ -477,8 +578,8 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
       const int r = k % NR, c = k / NR, J = c / w, x = c % w;
       a.out[(size_t)r * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
-    // moments: 16 (side, function) pairs over 8 warps
-    for (int pr = wid; pr < 16; pr += 8) {
+    // moments: 16 (side, function) pairs, one warp each
+    for (int pr = wid; pr < 16; pr += nw) {
       const int kside = pr / 4, r = pr % 4;
       double F = 0.0, Pw = 0.0;
       if (robin_side(g, s, kside)) {
@@ -530,31 +631,38 @@ __global__ void __launch_bounds__(256) k_solve(Geo g, SolveArgs a) {
 template <typename T, int MODE, int NR, int NBUF>
 static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
-  return sizeof(T) * (NBUF * (size_t)a.LS + (size_t)h * w * NR + 3 * (size_t)w * NR + (size_t)h * w) + 16;
+  return sizeof(T) * (2 * NBUF * (size_t)a.LS + (size_t)h * w * NR + 6 * (size_t)w * NR + (size_t)h * w) + 16;
 }
 
 template <typename T, int MODE, int NR, int NBUF>
-static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, cudaStream_t st) {
+static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, bool ohat, cudaStream_t st) {
   const cudaError_t e = raise_smem_limit<k_solve<T, MODE, NR, NBUF>>();
   if (e != cudaSuccess) return e;
-  k_solve<T, MODE, NR, NBUF><<<g.mx * g.my, 256, sm, st>>>(g, a);
+  // two line products per step, LineTPR threads per row; at least four warps for the moment sums
+  const int w = g.sx + (ohat ? 2 * g.l : 0);
+  int threads = (2 * w * LineTPR<T>::value + 31) / 32 * 32;
+  if (threads < 128) threads = 128;
+  k_solve<T, MODE, NR, NBUF><<<g.mx * g.my, threads, sm, st>>>(g, a);
   count_launch(1);
   return cudaGetLastError();
 }
 
-// Line blocks in flight: eight for FP32 solves (short steps, so the prefetch must run further ahead
-// to cover memory latency), four for FP64; fewer when they would not fit next to the right-hand sides.
+// Steps of line blocks in flight: eight for FP32 solves (short steps, so the prefetch must run
+// further ahead to cover memory latency), four for FP64; fewer when they would not fit next to the
+// right-hand sides, down to one (no prefetch) for the widest boxes with four right-hand sides.
 template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   constexpr size_t kMaxSmem = 227 * 1024;
   constexpr size_t kBudget = 100 * 1024;  // keep two CTAs per SM when possible
   if (sizeof(T) == 4) {
     const size_t sm8 = solve_smem<T, MODE, NR, 8>(g, a, ohat);
-    if (sm8 <= kBudget) return launch_solve_nb<T, MODE, NR, 8>(g, a, sm8, st);
+    if (sm8 <= kBudget) return launch_solve_nb<T, MODE, NR, 8>(g, a, sm8, ohat, st);
   }
   const size_t sm4 = solve_smem<T, MODE, NR, 4>(g, a, ohat);
-  if (sm4 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 4>(g, a, sm4, st);
-  return launch_solve_nb<T, MODE, NR, 2>(g, a, solve_smem<T, MODE, NR, 2>(g, a, ohat), st);
+  if (sm4 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 4>(g, a, sm4, ohat, st);
+  const size_t sm2 = solve_smem<T, MODE, NR, 2>(g, a, ohat);
+  if (sm2 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 2>(g, a, sm2, ohat, st);
+  return launch_solve_nb<T, MODE, NR, 1>(g, a, solve_smem<T, MODE, NR, 1>(g, a, ohat), ohat, st);
 }
 
 template <int MODE, int NR>
