@@ -119,11 +119,14 @@ mrcm_status mrcm_update_problem(mrcm_handle h, const mrcm_problem* problem, void
 /* Set-up of T (MRCM-OS steps 1-3 and the smoothing factors): face transmissibilities and b
  * (Sec. 3), oversampled Robin solves and informed spaces (Eq. 15), local Robin factors and
  * multiscale basis functions, coupling system (Eq. 13-14) and its LU factors, Dirichlet factors of
- * the oversampled regions.  Synchronises `stream` to report MRCM_ERR_SINGULAR. */
+ * the oversampled regions.  Synchronises `stream` to report MRCM_ERR_SINGULAR (or
+ * MRCM_ERR_TIMEOUT if a bounded device wait gave up). */
 mrcm_status mrcm_factor_local(mrcm_handle h, void* stream);
 
 /* z = T r (Sec. 3: the modified MRCM-O with homogeneous conditions and source r, followed by the
- * smoothing sweeps).  r and z are device arrays of n0*n1*n2 doubles; they may not overlap. */
+ * smoothing sweeps).  r and z are device arrays of n0*n1*n2 doubles; they may not overlap.  Only
+ * enqueues work: a bounded device wait that gives up sets the handle's device status word, which
+ * the next mrcm_gmres_solve() step reports as MRCM_ERR_TIMEOUT. */
 mrcm_status mrcm_apply_precond(mrcm_handle h, const double* r, double* z, void* stream);
 
 /* w = A v, the matrix-free fine operator (Sec. 3) with homogeneous boundary data; device arrays. */

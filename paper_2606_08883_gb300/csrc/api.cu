@@ -309,7 +309,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   }
   {
     Phase ph(h, MRCM_PH_INFORMED, st);
-    CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), st));
+    CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), at<int>(h, L.flags), st));
   }
   // MRCM-OS step 3: local Robin factors and multiscale basis functions
   {
@@ -319,7 +319,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   {
     Phase ph(h, MRCM_PH_BASIS, st);
     CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), at<double>(h, L.psi),
-                       at<double>(h, L.mom), st));
+                       at<double>(h, L.mom), at<int>(h, L.flags), st));
   }
   // coupling system (Eq. 13-14)
   CoarseDev c = coarse(h);
@@ -340,6 +340,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   if (hf & FLAG_NONFINITE) return fail(h, MRCM_ERR_INVALID_ARG, "K must be positive and finite");
   if (hf & FLAG_SINGULAR_LOCAL) return fail(h, MRCM_ERR_SINGULAR, "non-positive pivot in a local factorisation");
   if (hf & FLAG_SINGULAR_COARSE) return fail(h, MRCM_ERR_SINGULAR, "zero pivot in the coupling system");
+  if (hf & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "a bounded device wait gave up (local solve line copy)");
   h->factored = true;
   return MRCM_OK;
 }
@@ -352,7 +353,8 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   // particular solutions and their side moments
   {
     Phase ph(h, MRCM_PH_PARTICULAR, st);
-    CK(h, launch_particular(g, at<void>(h, L.Linv_loc), L.LSl, fp32, r, at<double>(h, L.psi0), at<double>(h, L.mom0), st));
+    CK(h, launch_particular(g, at<void>(h, L.Linv_loc), L.LSl, fp32, r, at<double>(h, L.psi0), at<double>(h, L.mom0),
+                              at<int>(h, L.flags), st));
   }
   // coupling system
   CoarseDev c = coarse(h);
@@ -381,7 +383,7 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
     Phase ph(h, MRCM_PH_SCHWARZ, st);
     const double* zin = zb[(s - it) & 1];
     double* zout = zb[(s - it - 1) & 1];
-    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, st));
+    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), st));
   }
   return MRCM_OK;
 }
@@ -529,7 +531,8 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
         const mrcm_ctx::StepReadback* slot = h->rb + (pend & 1);
         const double ho[3] = {slot->out[0], slot->out[1], slot->out[2]};
         ++it;
-        if (slot->flags & FLAG_TIMEOUT) return fail(h, MRCM_ERR_TIMEOUT, "grid barrier in the Arnoldi step timed out");
+        if (slot->flags & FLAG_TIMEOUT)
+          return fail(h, MRCM_ERR_TIMEOUT, "a bounded device wait gave up (Arnoldi grid barrier or local-solve line copy)");
         if (h->cancel && *h->cancel) {
           result->iterations = it;
           return fail(h, MRCM_ERR_CANCELLED, "cancelled");

@@ -70,6 +70,17 @@ Layout make_layout(const Plan& plan, const mrcm_params& q);
 // ------------------------------------------------------------------------------------------
 // Device-side geometry passed by value to kernels (2-D).
 // ------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+#define MRCM_HD __host__ __device__
+#else
+#define MRCM_HD
+#endif
+// Elements per box of a line-block factor array: h packed line blocks of LS elements, then the
+// h x w line couplings (coupling of each cell to the line below), padded to a 16-byte multiple.
+MRCM_HD inline size_t box_stride(int w, int h, int LS) {
+  return (size_t)h * LS + (((size_t)h * w + 3) & ~(size_t)3);
+}
+
 struct Geo {
   int nx, ny;
   int sx, sy;              // subdomain size
@@ -158,13 +169,13 @@ cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const*
 enum BoxKind : int { BOX_OMEGA_ROBIN = 0, BOX_OHAT_ROBIN = 1, BOX_OHAT_DIRICHLET = 2 };
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
                           cudaStream_t st);
-cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, cudaStream_t st);
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int* flags, cudaStream_t st);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
-                         double* mom, cudaStream_t st);
+                         double* mom, int* flags, cudaStream_t st);
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, cudaStream_t st);
+                              double* mom0, int* flags, cudaStream_t st);
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, cudaStream_t st);
+                           double* zout, int* flags, cudaStream_t st);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
 size_t factor_smem_bytes(int w, bool fp32);

@@ -8,7 +8,7 @@
 //   bottom  S_{h-1} = D_{h-1},  S_J = D_J - E_{J+1} S_{J+1}^-1 E_{J+1}    J = h-2 .. m+1
 //   middle  S_m = D_m - E_m S_{m-1}^-1 E_m - E_{m+1} S_{m+1}^-1 E_{m+1}
 // and only the inverses S_J^-1 are stored (symmetric, packed lower triangle, one line block per
-// line; each by Cholesky S_J = L L^T, L^-1, S_J^-1 = L^-T L^-1).  A solve eliminates from both ends
+// line; each by Cholesky S_J = L L^T, L^-1, S_J^-1 = L^-T L^-1), followed by the couplings E_J.  A solve eliminates from both ends
 //   u_J = b_J + E_J S_{J-1}^-1 u_{J-1} (top),  u_J = b_J + E_{J+1} S_{J+1}^-1 u_{J+1} (bottom),
 //   x_m = S_m^-1 u_m with u_m = b_m + E_m S_{m-1}^-1 u_{m-1} + E_{m+1} S_{m+1}^-1 u_{m+1},
 // and substitutes back outwards: x_J = S_J^-1 (u_J + E_{J+1} x_{J+1}) above the middle,
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   __shared__ int bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) bad = 0;
-  T* out = Linv + (size_t)s * b.h * LS;
+  T* out = Linv + (size_t)s * box_stride(w, b.h, LS);
+  T* ec_out = out + (size_t)b.h * LS;      // line couplings E_J[x], read by every solve
   const int npk = w * (w + 1) / 2;
   const int h = b.h, m = h / 2;
   T* ev2 = rinv + w;                       // second coupling vector (middle line)
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
     for (int i = tid; i < w; i += nt) {
       double d, o, e;
       line_coeffs(g, b, robin, J, i, d, o, e);
+      ec_out[(size_t)J * w + i] = (T)e;
       Sm[i * w + i] = (T)d;
       if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
       if (top) {
@@ -244,11 +246,31 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// coupling value (T > 0) between local lines J-1 and J at x, 0 if absent
-__device__ __forceinline__ double couple_up(const Geo& g, const Box& b, int J, int x) {
-  const int gx = b.ox + x, gy = b.oy + J;
-  if (J <= 0 || J >= b.h || !active(g, gx, gy) || !active(g, gx, gy - 1)) return 0.0;
-  return g.Ty[(size_t)gy * g.nx + gx];
+// mbarrier-completed bulk copies (one per line block) for box-resident solves
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Waits for phase 0 of bar to complete; gives up (returns false) after a bounded number of polls.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar))
+        : "memory");
+    if (done) return true;
+  }
+  return false;
 }
 
 struct SolveArgs {
@@ -258,6 +280,7 @@ struct SolveArgs {
   double* out;         // particular: psi0; schwarz: z after the sweep; basis: psi; informed: phi
   double* mom;         // particular: mom0 [S][4][2]; basis: mom [S][4][4][2]
   const double* zin;   // schwarz: z before the sweep (read only)
+  int* flags;          // device status word (FLAG_TIMEOUT if a bounded wait gives up)
 };
 
 // Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.
@@ -356,22 +379,34 @@ struct Twist {
   }
 };
 
-// NBUF steps of line blocks in flight (two blocks per step; prefetch distance NBUF - 1).
+// NBUF steps of line blocks in flight (two blocks per step; prefetch distance NBUF - 1), or, for
+// NBUF = 0, the whole box resident: every line block is copied once at the start (one bulk copy and
+// one mbarrier per line, issued in the order the elimination uses them) and serves both the
+// elimination and the back substitution.
 template <typename T, int MODE, int NR, int NBUF>
-__global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
+__global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool RES = NBUF == 0;
   const int s = blockIdx.x;
   const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
-  T* Lb = reinterpret_cast<T*>(smem_raw);    // [NBUF][2][LS] line blocks
-  T* Y = Lb + 2 * NBUF * LS;                 // [hgt][w][NR]: b, then u (elimination), then x (back)
+  T* Lb = reinterpret_cast<T*>(smem_raw);    // [NBUF][2][LS] line blocks, or [hgt][LS] (resident)
+  T* Y = Lb + (RES ? (size_t)hgt * LS : (size_t)2 * NBUF * LS);  // [hgt][w][NR]: b, u, then x
   T* tv = Y + (size_t)hgt * w * NR;          // [4][w][NR] ping-pong inputs of the back steps (top, bottom)
   T* xm = tv + 4 * w * NR;                   // [w][NR] x of the middle line
   T* cb = xm + w * NR;                       // [w][NR] bottom contribution to the middle (odd h)
-  T* Ec = cb + w * NR;                       // [hgt][w] line couplings
+  T* Ec = reinterpret_cast<T*>(              // [hgt][w] line couplings (16-byte aligned, padded copy)
+      smem_raw + ((reinterpret_cast<unsigned char*>(cb + w * NR) - smem_raw + 15) & ~(size_t)15));
+  const int ecn = (hgt * w + 3) & ~3;
+  unsigned long long* bars =                 // [hgt] line-block barriers (resident)
+      reinterpret_cast<unsigned long long*>(smem_raw + ((reinterpret_cast<unsigned char*>(Ec + ecn) - smem_raw + 7) & ~(size_t)7));
   const int tid = threadIdx.x, nt = blockDim.x;
-  const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * hgt * LS;
+  const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * box_stride(w, hgt, LS);
+  // the couplings join the first copy group (ring) or their own group (resident)
+  for (int c = tid; c < ecn * (int)sizeof(T) / 16; c += nt)
+    cp_async16(reinterpret_cast<unsigned char*>(Ec) + 16 * c, reinterpret_cast<const unsigned char*>(Lg + (size_t)hgt * LS) + 16 * c);
+  if (RES) cp_async_commit();
   Twist tw;
   tw.h = hgt;
   tw.m = hgt / 2;
@@ -386,46 +421,93 @@ __global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
   }
   const int nsteps = tw.nf + 1 + tw.nb;
   auto issue_step = [&](int st) {
+    if (RES) return;
     if (st < nsteps) {
       int A, B;
       tw.lines(st, A, B);
-      T* slot = Lb + (size_t)(st % NBUF) * 2 * LS;
+      T* slot = Lb + (size_t)(st % (NBUF > 0 ? NBUF : 1)) * 2 * LS;
       issue_line(slot, Lg + (size_t)(A > 0 ? A : 0) * LS, LS, A >= 0);
       issue_line(slot + LS, Lg + (size_t)(B > 0 ? B : 0) * LS, LS, B >= 0);
     }
     cp_async_commit();  // one group per step, empty past the last, so the wait count stays uniform
   };
-  for (int p = 0; p < NBUF - 1; ++p) issue_step(p);  // NBUF = 1: no prefetch, each step loads its own lines
+  if constexpr (RES) {
+    if (tid == 0) {
+      for (int L = 0; L < hgt; ++L) mbar_init(&bars[L], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned bytes = (unsigned)(LS * sizeof(T));
+      for (int t = 0; t < tw.nf; ++t) {
+        if (t < tw.m) bulk_load(Lb + (size_t)t * LS, Lg + (size_t)t * LS, bytes, &bars[t]);
+        const int B = hgt - 1 - t;
+        if (B >= tw.m + 1) bulk_load(Lb + (size_t)B * LS, Lg + (size_t)B * LS, bytes, &bars[B]);
+      }
+      bulk_load(Lb + (size_t)tw.m * LS, Lg + (size_t)tw.m * LS, bytes, &bars[tw.m]);
+    }
+  } else {
+    for (int p = 0; p < NBUF - 1; ++p) issue_step(p);  // NBUF = 1: no prefetch, each step loads its own lines
+  }
 
   // ---------------- right-hand sides into Y
   for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
   for (int k = tid; k < w * NR; k += nt) cb[k] = (T)0;
   __syncthreads();
   if (MODE == MODE_PARTICULAR) {
-    for (int k = tid; k < hgt * w; k += nt) {
-      const int J = k / w, x = k % w;
-      const int gx = b.ox + x, gy = b.oy + J;
-      if (active(g, gx, gy)) Y[k * NR] = (T)a.in[(size_t)gy * g.nx + gx];
+    // four cells per thread per pass, all loads before the stores
+    const double* __restrict__ rin = a.in;
+    for (int k0 = tid; k0 < hgt * w; k0 += 4 * nt) {
+      double v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = k0 + e * nt, J = k / w, x = k % w;
+        const int gx = b.ox + x, gy = b.oy + J;
+        v[e] = (k < hgt * w && active(g, gx, gy)) ? rin[(size_t)gy * g.nx + gx] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (k0 + e * nt < hgt * w) Y[(k0 + e * nt) * NR] = (T)v[e];
     }
   } else if (MODE == MODE_SCHWARZ) {
     // rho = r - A z on the box, from the sweep's input z (read only; the output goes elsewhere),
-    // in the precision of the local solve
-    const double* z = a.zin;
-    for (int k = tid; k < hgt * w; k += nt) {
-      const int J = k / w, x = k % w;
-      const int gx = b.ox + x, gy = b.oy + J;
-      if (!active(g, gx, gy)) continue;
-      const size_t c = (size_t)gy * g.nx + gx;
-      const T zc = (T)z[c];
-      const T zw = gx > 0 ? (T)z[c - 1] : (T)0;
-      const T ze = gx < g.nx - 1 ? (T)z[c + 1] : (T)0;
-      const T zs = gy > 0 ? (T)z[c - g.nx] : (T)0;
-      const T zn = gy < g.ny - 1 ? (T)z[c + g.nx] : (T)0;
-      const double* Tx = g.Tx + (size_t)gy * (g.nx + 1) + gx;
-      const double* Ty = g.Ty + (size_t)gy * g.nx + gx;
-      const T wx = (T)Tx[1] * (zc - ze) - (T)Tx[0] * (zw - zc);
-      const T wy = (T)Ty[g.nx] * (zc - zn) - (T)Ty[0] * (zs - zc);
-      Y[k * NR] = (T)a.in[c] - (wx + wy);
+    // in the precision of the local solve; four cells per thread per pass, all loads first
+    const double* __restrict__ z = a.zin;
+    const double* __restrict__ rin = a.in;
+    const double* __restrict__ Txg = g.Tx;
+    const double* __restrict__ Tyg = g.Ty;
+    for (int k0 = tid; k0 < hgt * w; k0 += 4 * nt) {
+      double zc[4], zw[4], ze[4], zs[4], zn[4], t0[4], t1[4], t2[4], t3[4], rv[4];
+      bool on[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = k0 + e * nt, J = k / w, x = k % w;
+        const int gx = b.ox + x, gy = b.oy + J;
+        on[e] = k < hgt * w && active(g, gx, gy);
+        zc[e] = zw[e] = ze[e] = zs[e] = zn[e] = t0[e] = t1[e] = t2[e] = t3[e] = rv[e] = 0.0;
+        if (on[e]) {
+          const size_t c = (size_t)gy * g.nx + gx;
+          zc[e] = z[c];
+          if (gx > 0) zw[e] = z[c - 1];
+          if (gx < g.nx - 1) ze[e] = z[c + 1];
+          if (gy > 0) zs[e] = z[c - g.nx];
+          if (gy < g.ny - 1) zn[e] = z[c + g.nx];
+          const size_t cx = (size_t)gy * (g.nx + 1) + gx;
+          t0[e] = Txg[cx];
+          t1[e] = Txg[cx + 1];
+          t2[e] = Tyg[c];
+          t3[e] = Tyg[c + g.nx];
+          rv[e] = rin[c];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (!on[e]) continue;
+        const T c0 = (T)zc[e];
+        const T wx = (T)t1[e] * (c0 - (T)ze[e]) - (T)t0[e] * ((T)zw[e] - c0);
+        const T wy = (T)t3[e] * (c0 - (T)zn[e]) - (T)t2[e] * ((T)zs[e] - c0);
+        Y[(k0 + e * nt) * NR] = (T)rv[e] - (wx + wy);
+      }
     }
   } else if (MODE == MODE_INFORMED) {
     // lambda^r = 1 on the faces of Robin side r of the oversampled box
@@ -465,8 +547,7 @@ __global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
       __syncthreads();
     }
   }
-  // couplings between consecutive lines: Ec[J][x] joins line J-1 and line J (J >= 1)
-  for (int k = tid; k < hgt * w; k += nt) Ec[k] = (T)couple_up(g, b, k / w, k % w);
+  if constexpr (RES) cp_async_wait<0>();  // couplings (each thread waits for its own copies)
 
   const int m = tw.m;
   T* tA0 = tv;                   // top back inputs (ping-pong)
@@ -474,20 +555,39 @@ __global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
   T* tB0 = tv + 2 * w * NR;      // bottom back inputs (ping-pong)
   T* tB1 = tv + 3 * w * NR;
   for (int st = 0; st < nsteps; ++st) {
-    if constexpr (NBUF == 1) {
-      __syncthreads();  // the previous step is done with the single slot
-      issue_step(st);
-      cp_async_wait<0>();
-      __syncthreads();
-    } else {
-      cp_async_wait<NBUF - 2>();
-      __syncthreads();
-      issue_step(st + NBUF - 1);
-    }
     int A, B;
     tw.lines(st, A, B);
-    const T* LA = Lb + (size_t)(st % NBUF) * 2 * LS;
-    const T* LBk = LA + LS;
+    const T* LA;
+    const T* LBk;
+    if constexpr (RES) {
+      bool ok = true;
+      if (A >= 0) ok = mbar_wait0(&bars[A]);
+      if (B >= 0) ok = mbar_wait0(&bars[B]) && ok;
+      if (__syncthreads_or(!ok)) {
+        // a line block never arrived: report, let every copy of this CTA land (bounded), stop
+        if (tid == 0) {
+          atomicOr(a.flags, FLAG_TIMEOUT);
+          for (int L = 0; L < hgt; ++L) (void)mbar_wait0(&bars[L]);
+        }
+        __syncthreads();
+        return;
+      }
+      LA = Lb + (size_t)(A > 0 ? A : 0) * LS;
+      LBk = Lb + (size_t)(B > 0 ? B : 0) * LS;
+    } else {
+      if constexpr (NBUF == 1) {
+        __syncthreads();  // the previous step is done with the single slot
+        issue_step(st);
+        cp_async_wait<0>();
+        __syncthreads();
+      } else {
+        cp_async_wait<NBUF - 2>();
+        __syncthreads();
+        issue_step(st + NBUF - 1);
+      }
+      LA = Lb + (size_t)(st % (NBUF > 0 ? NBUF : 1)) * 2 * LS;
+      LBk = LA + LS;
+    }
     if (st < tw.nf) {
       // ---- elimination: top line A (u_{A+1} += E_{A+1} S_A^-1 u_A), bottom line B
       //      (u_{B-1} += E_B S_B^-1 u_B); the bottom's last contribution to the middle goes to cb
@@ -533,7 +633,7 @@ __global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
       });
     }
   }
-  cp_async_wait<0>();
+  if constexpr (!RES) cp_async_wait<0>();
   __syncthreads();
   for (int k = tid; k < w * NR; k += nt) Y[(size_t)m * w * NR + k] = xm[k];
   __syncthreads();
@@ -631,7 +731,9 @@ __global__ void __launch_bounds__(1024) k_solve(Geo g, SolveArgs a) {
 template <typename T, int MODE, int NR, int NBUF>
 static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
-  return sizeof(T) * (2 * NBUF * (size_t)a.LS + (size_t)h * w * NR + 6 * (size_t)w * NR + (size_t)h * w) + 16;
+  const size_t lines = NBUF == 0 ? (size_t)h * a.LS : 2 * NBUF * (size_t)a.LS;
+  const size_t ecn = ((size_t)h * w + 3) & ~(size_t)3;
+  return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32;
 }
 
 template <typename T, int MODE, int NR, int NBUF>
@@ -647,14 +749,19 @@ static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, 
   return cudaGetLastError();
 }
 
-// Steps of line blocks in flight: eight for FP32 solves (short steps, so the prefetch must run
-// further ahead to cover memory latency), four for FP64; fewer when they would not fit next to the
-// right-hand sides, down to one (no prefetch) for the widest boxes with four right-hand sides.
+// Line blocks: FP32 solves keep the whole box resident when two CTAs still fit on an SM (their
+// steps are short, so a prefetch ring cannot run far enough ahead of memory latency), else eight
+// steps in flight; FP64
+// solves keep four steps in flight; fewer when they would not fit next to the right-hand sides, down
+// to one (no prefetch) for the widest boxes with four right-hand sides.
 template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   constexpr size_t kMaxSmem = 227 * 1024;
   constexpr size_t kBudget = 100 * 1024;  // keep two CTAs per SM when possible
   if (sizeof(T) == 4) {
+    // FP32 solves wait on memory, not on arithmetic: keep the whole box on chip when it fits
+    const size_t sm0 = solve_smem<T, MODE, NR, 0>(g, a, ohat);
+    if (sm0 <= kBudget + 14 * 1024) return launch_solve_nb<T, MODE, NR, 0>(g, a, sm0, ohat, st);
     const size_t sm8 = solve_smem<T, MODE, NR, 8>(g, a, ohat);
     if (sm8 <= kBudget) return launch_solve_nb<T, MODE, NR, 8>(g, a, sm8, ohat, st);
   }
@@ -681,31 +788,31 @@ __global__ void k_phi_indicator(Geo g, double* phi) {
   }
 }
 
-cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, cudaStream_t st) {
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int* flags, cudaStream_t st) {
   if (g.l == 0) {
     k_phi_indicator<<<g.mx * g.my, 128, 0, st>>>(g, phi);
     count_launch(1);
     return cudaGetLastError();
   }
-  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr};
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags};
   return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
 }
 
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
-                         double* mom, cudaStream_t st) {
-  SolveArgs a{Linv, LS, phi, psi, mom, nullptr};
+                         double* mom, int* flags, cudaStream_t st) {
+  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags};
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, cudaStream_t st) {
-  SolveArgs a{Linv, LS, r, psi0, mom0, nullptr};
+                              double* mom0, int* flags, cudaStream_t st) {
+  SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags};
   return launch_solve<MODE_PARTICULAR, 1>(g, a, false, fp32, st);
 }
 
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, cudaStream_t st) {
-  SolveArgs a{Linv, LS, r, zout, nullptr, zin};
+                           double* zout, int* flags, cudaStream_t st) {
+  SolveArgs a{Linv, LS, r, zout, nullptr, zin, flags};
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 

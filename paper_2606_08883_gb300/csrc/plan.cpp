@@ -186,9 +186,9 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.b = take(8 * n);
   L.f = take(8 * n);
   L.bcv = take(8 * 4 * std::max(nx, ny));
-  L.Linv_loc = take(L.elt * S * L.hl * L.LSl);
-  L.Linv_ohat_r = take(P.l > 0 ? L.elt * S * L.ho * L.LSo : 0);
-  L.Linv_ohat_d = take(q.smooth_steps > 0 ? L.elt * S * L.ho * L.LSo : 0);
+  L.Linv_loc = take(L.elt * S * box_stride(L.wl, L.hl, L.LSl));
+  L.Linv_ohat_r = take(P.l > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
+  L.Linv_ohat_d = take(q.smooth_steps > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
   L.phi = take(8 * S * 16 * L.smax);
   L.psi = take(8 * 4 * n);
   L.mom = take(8 * S * 32);
