@@ -216,9 +216,217 @@ __global__ void __launch_bounds__(256) k_coarse_apply(CoarseDev c, const double*
   if (lane == 0) out[row] = acc;
 }
 
+// ---- Band LU in a sliding shared-memory window ------------------------------------------------
+// Step j touches columns j .. ju <= j + kl + ku, so W = kl + ku + 1 columns of the band hold all of
+// a step's data.  The window has W + 3 column slots (column c in slot c mod (W + 3)): the W active
+// ones, the column written back to global memory this step, and two being prefetched (column
+// j + W + 1 is requested at step j and first needed at step j + 2).  Per step, warp 0 finds the
+// pivot (first index of the largest magnitude, as above) and the multipliers l_i = A(j+i, j) / piv
+// (as a product with 1/piv); then each warp takes whole columns j .. ju and applies the row
+// interchange and the rank-one update from the values before the interchange, so a step costs two
+// block barriers and all arithmetic stays on chip.
+constexpr int GBW_THREADS = 1024;
+constexpr int GBW_MAX_KL = 512;
+
+__device__ __forceinline__ void gb_cp_async8(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void gb_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void gb_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* flags) {
+  extern __shared__ __align__(16) double win[];
+  __shared__ double sl[GBW_MAX_KL + 1];  // multipliers of the current column
+  __shared__ int s_jp, s_ju, s_ok;
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const int W = kl + ku + 1, NS = W + 3;
+  double* ab = c.ab;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nw = GBW_THREADS / 32;
+  auto slot = [&](int col) { return win + (size_t)(col % NS) * ld; };
+  auto load_col = [&](int col) {
+    double* dst = slot(col);
+    const double* src = ab + (size_t)col * ld;
+    for (int r = tid; r < ld; r += GBW_THREADS) gb_cp_async8(dst + r, src + r);
+  };
+  for (int col = 0; col < n && col <= W; ++col) load_col(col);
+  gb_commit();
+  gb_wait<0>();
+  __syncthreads();
+  int ju = 0;
+  for (int j = 0; j < n; ++j) {
+    gb_wait<1>();  // columns up to j + W - 1 (requested two steps ago) have landed
+    __syncthreads();
+    if (j >= 1) {  // column j - 1 is final: back to global memory
+      const double* src = slot(j - 1);
+      double* dst = ab + (size_t)(j - 1) * ld;
+      for (int r = tid; r < ld; r += GBW_THREADS) dst[r] = src[r];
+    }
+    if (j + W + 1 < n) load_col(j + W + 1);
+    gb_commit();
+    const int km = min(kl, n - 1 - j);
+    const double* cj = slot(j) + kv;  // cj[i] = A(j + i, j)
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = lane; i <= km; i += 32) {
+        const double v = fabs(cj[i]);
+        if (v > best || (v == best && i < bi)) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      const double piv = cj[bi];
+      const bool ok = piv != 0.0 && isfinite(piv);
+      if (ok) {
+        const double rp = 1.0 / piv;
+        const double old0 = cj[0];
+        for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi ? old0 : cj[i]) * rp;
+      }
+      if (lane == 0) {
+        s_ok = ok ? 1 : 0;
+        if (!ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
+        s_jp = bi;
+        c.ipiv[j] = j + bi;
+        s_ju = max(ju, min(j + ku + bi, n - 1));
+      }
+    }
+    __syncthreads();
+    if (!s_ok) continue;
+    ju = s_ju;
+    const int jp = s_jp;
+    for (int col = j + warp; col <= ju; col += nw) {
+      double* cc = slot(col) + kv + j - col;  // cc[i] = A(j + i, col)
+      const double up = cc[jp], old0 = cc[0];
+      __syncwarp();
+      if (col == j) {
+        if (lane == 0) cc[0] = up;
+        for (int i = 1 + lane; i <= km; i += 32) cc[i] = sl[i];
+      } else {
+        if (lane == 0) cc[0] = up;
+        for (int i = 1 + lane; i <= km; i += 32) cc[i] = (i == jp ? old0 : cc[i]) - sl[i] * up;
+      }
+    }
+  }
+  gb_wait<0>();
+  __syncthreads();
+  if (n >= 1) {
+    const double* src = slot(n - 1);
+    double* dst = ab + (size_t)(n - 1) * ld;
+    for (int r = tid; r < ld; r += GBW_THREADS) dst[r] = src[r];
+  }
+}
+
+// Columns of G^-1, one warp per column and no block barriers: the band entries of the next step
+// are loaded while the current step runs (at most four rows per lane, i.e. kl + ku <= 128).
+constexpr int GBC_ROWS = 4;
+__global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __restrict__ Ginv) {
+  extern __shared__ double sbuf[];
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const double* __restrict__ ab = c.ab;
+  const int* __restrict__ ipiv = c.ipiv;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = blockIdx.x * 4 + warp;
+  if (col >= n) return;  // whole warps
+  double* b = sbuf + (size_t)warp * n;
+  for (int i = lane; i < n; i += 32) b[i] = (i == col) ? 1.0 : 0.0;
+  __syncwarp();
+  // forward: b[j + i] -= L(j + i, j) b[j], after the interchange of step j
+  double cur[GBC_ROWS], nxt[GBC_ROWS];
+  auto loadL = [&](int j, double (&v)[GBC_ROWS]) {
+    const int lm = min(kl, n - 1 - j);
+#pragma unroll
+    for (int q = 0; q < GBC_ROWS; ++q) {
+      const int i = 1 + lane + 32 * q;
+      v[q] = i <= lm ? ab[(size_t)(kv + i) + (size_t)j * ld] : 0.0;
+    }
+  };
+  loadL(0, cur);
+  int lcur = ipiv[0];
+  for (int j = 0; j < n; ++j) {
+    int lnxt = 0;
+    if (j + 1 < n) {
+      loadL(j + 1, nxt);
+      lnxt = ipiv[j + 1];
+    }
+    if (lcur != j) {
+      if (lane == 0) {
+        const double t = b[lcur];
+        b[lcur] = b[j];
+        b[j] = t;
+      }
+      __syncwarp();
+    }
+    const double bj = b[j];
+    const int lm = min(kl, n - 1 - j);
+    if (bj != 0.0) {
+#pragma unroll
+      for (int q = 0; q < GBC_ROWS; ++q) {
+        const int i = 1 + lane + 32 * q;
+        if (i <= lm) b[j + i] -= cur[q] * bj;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < GBC_ROWS; ++q) cur[q] = nxt[q];
+    lcur = lnxt;
+  }
+  // backward: b[j] /= U(j, j), then b[i] -= U(i, j) b[j] for i = j - kv .. j - 1
+  double dcur, dnxt = 0.0;
+  auto loadU = [&](int j, double (&v)[GBC_ROWS]) {
+    const int i0 = max(0, j - kv);
+#pragma unroll
+    for (int q = 0; q < GBC_ROWS; ++q) {
+      const int i = i0 + lane + 32 * q;
+      v[q] = i < j ? ab[(size_t)(kv + i - j) + (size_t)j * ld] : 0.0;
+    }
+  };
+  loadU(n - 1, cur);
+  dcur = ab[(size_t)kv + (size_t)(n - 1) * ld];
+  for (int j = n - 1; j >= 0; --j) {
+    if (j > 0) {
+      loadU(j - 1, nxt);
+      dnxt = ab[(size_t)kv + (size_t)(j - 1) * ld];
+    }
+    if (lane == 0) b[j] = b[j] / dcur;
+    __syncwarp();
+    const double bj = b[j];
+    const int i0 = max(0, j - kv);
+    if (bj != 0.0) {
+#pragma unroll
+      for (int q = 0; q < GBC_ROWS; ++q) {
+        const int i = i0 + lane + 32 * q;
+        if (i < j) b[i] -= cur[q] * bj;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < GBC_ROWS; ++q) cur[q] = nxt[q];
+    dcur = dnxt;
+  }
+  for (int i = lane; i < n; i += 32) Ginv[(size_t)i * n + col] = b[i];
+}
+
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
-  k_gbtrs_cols<<<c.n, 128, sizeof(double) * c.n, st>>>(c, Ginv);
+  const size_t sm4 = sizeof(double) * 4 * (size_t)c.n;
+  if (c.kl <= 32 * GBC_ROWS && c.kl + c.ku <= 32 * GBC_ROWS && sm4 <= 96 * 1024) {
+    k_gbtrs_cols_warp<<<(c.n + 3) / 4, 128, sm4, st>>>(c, Ginv);
+  } else {
+    k_gbtrs_cols<<<c.n, 128, sizeof(double) * c.n, st>>>(c, Ginv);
+  }
   count_launch(1);
   return cudaGetLastError();
 }
@@ -241,7 +449,18 @@ cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E,
 
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
-  k_gbtf2<<<1, 512, 0, st>>>(c, flags);
+  const size_t win = sizeof(double) * (size_t)(c.kl + c.ku + 4) * c.ldab;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t static_smem = sizeof(double) * (GBW_MAX_KL + 1) + 64;
+  if (c.kl <= GBW_MAX_KL && win + static_smem <= (size_t)optin) {
+    const cudaError_t e = raise_smem_limit<k_gbtf2_win>();
+    if (e != cudaSuccess) return e;
+    k_gbtf2_win<<<1, GBW_THREADS, win, st>>>(c, flags);
+  } else {
+    k_gbtf2<<<1, 512, 0, st>>>(c, flags);
+  }
   count_launch(1);
   return cudaGetLastError();
 }
