@@ -545,7 +545,7 @@ mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* 
       if (!launch) break;
       pend = j;
     }
-    CK(h, launch_update(p, Z, n, H, gv, k, ldh, st));
+    CK(h, launch_update(p, Z, n, H, gv, k, ldh, at<double>(h, L.atot), st));
     CK(h, launch_residual_norm(g, bb, p, V, partials, counter, beta_d, st));
     CK(h, cudaMemcpyAsync(&beta, beta_d, 8, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));

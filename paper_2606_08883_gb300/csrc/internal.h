@@ -213,7 +213,7 @@ cudaError_t launch_mgs_pass(const double* vprev, const double* hprev, const doub
 cudaError_t launch_givens(double* H, double* cs, double* sn, double* gv, int j, int ldh, double* hnorm0,
                           double* out, cudaStream_t st);
 cudaError_t launch_update(double* p, const double* Z, size_t n, const double* H, const double* gv, int k, int ldh,
-                          cudaStream_t st);
+                          double* ybuf, cudaStream_t st);
 cudaError_t launch_residual_norm(const Geo& g, const double* b, const double* p, double* r, double* partials,
                                  unsigned* counter, double* out, cudaStream_t st);
 }  // namespace mrcm

@@ -238,10 +238,48 @@ __device__ __forceinline__ void gb_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Pivot choice and multipliers of step j (one warp): first index of the largest magnitude in
+// column j below the diagonal, l_i = A(j+i, j) / piv as a product with 1/piv, read before the
+// interchange; writes ipiv[j] and the step's column reach.
+__device__ __forceinline__ void gb_pivot(const double* cj, int j, int km, int n, int ku, int ju_prev, int lane,
+                                         double* sl, int* s_jp, int* s_ju, int* s_ok, int* ipiv, int* flags) {
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = lane; i <= km; i += 32) {
+    const double v = fabs(cj[i]);
+    if (v > best || (v == best && i < bi)) {
+      best = v;
+      bi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  const double piv = cj[bi];
+  const bool ok = piv != 0.0 && isfinite(piv);
+  if (ok) {
+    const double rp = 1.0 / piv;
+    const double old0 = cj[0];
+    for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi ? old0 : cj[i]) * rp;
+  }
+  if (lane == 0) {
+    *s_ok = ok ? 1 : 0;
+    if (!ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
+    *s_jp = bi;
+    ipiv[j] = j + bi;
+    *s_ju = ok ? max(ju_prev, min(j + ku + bi, n - 1)) : ju_prev;
+  }
+}
+
 __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* flags) {
   extern __shared__ __align__(16) double win[];
-  __shared__ double sl[GBW_MAX_KL + 1];  // multipliers of the current column
-  __shared__ int s_jp, s_ju, s_ok;
+  __shared__ double sl[2][GBW_MAX_KL + 1];  // multipliers of the current and the next column
+  __shared__ int s_jp[2], s_ju[2], s_ok[2];
   const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
   const int W = kl + ku + 1, NS = W + 3;
   double* ab = c.ab;
@@ -257,11 +295,13 @@ __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* 
   gb_commit();
   gb_wait<0>();
   __syncthreads();
-  int ju = 0;
+  if (warp == 0 && n > 0)
+    gb_pivot(slot(0) + kv, 0, min(kl, n - 1), n, ku, 0, lane, sl[0], &s_jp[0], &s_ju[0], &s_ok[0], c.ipiv, flags);
   for (int j = 0; j < n; ++j) {
+    const int pj = j & 1, pn = pj ^ 1;
     gb_wait<1>();  // columns up to j + W - 1 (requested two steps ago) have landed
-    __syncthreads();
-    if (j >= 1) {  // column j - 1 is final: back to global memory
+    __syncthreads();  // also publishes step j's pivot and multipliers
+    if (j >= 1) {     // column j - 1 is final: back to global memory
       const double* src = slot(j - 1);
       double* dst = ab + (size_t)(j - 1) * ld;
       for (int r = tid; r < ld; r += GBW_THREADS) dst[r] = src[r];
@@ -269,55 +309,28 @@ __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* 
     if (j + W + 1 < n) load_col(j + W + 1);
     gb_commit();
     const int km = min(kl, n - 1 - j);
-    const double* cj = slot(j) + kv;  // cj[i] = A(j + i, j)
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = 0x7fffffff;
-      for (int i = lane; i <= km; i += 32) {
-        const double v = fabs(cj[i]);
-        if (v > best || (v == best && i < bi)) {
-          best = v;
-          bi = i;
+    const bool ok = s_ok[pj] != 0;
+    const int ju = s_ju[pj], jp = s_jp[pj];
+    const double* l = sl[pj];
+    // warp w takes columns j + w, j + w + 32, ...; warp 1 starts with column j + 1 and, once it is
+    // final for this step, chooses the pivot of step j + 1
+    for (int col = j + warp; col <= ju || (warp == 1 && col == j + 1 && j + 1 < n); col += nw) {
+      if (ok && col <= ju) {
+        double* cc = slot(col) + kv + j - col;  // cc[i] = A(j + i, col)
+        const double up = cc[jp], old0 = cc[0];
+        __syncwarp();
+        if (col == j) {
+          if (lane == 0) cc[0] = up;
+          for (int i = 1 + lane; i <= km; i += 32) cc[i] = l[i];
+        } else {
+          if (lane == 0) cc[0] = up;
+          for (int i = 1 + lane; i <= km; i += 32) cc[i] = (i == jp ? old0 : cc[i]) - l[i] * up;
         }
+        __syncwarp();
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-          best = ov;
-          bi = oi;
-        }
-      }
-      const double piv = cj[bi];
-      const bool ok = piv != 0.0 && isfinite(piv);
-      if (ok) {
-        const double rp = 1.0 / piv;
-        const double old0 = cj[0];
-        for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi ? old0 : cj[i]) * rp;
-      }
-      if (lane == 0) {
-        s_ok = ok ? 1 : 0;
-        if (!ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
-        s_jp = bi;
-        c.ipiv[j] = j + bi;
-        s_ju = max(ju, min(j + ku + bi, n - 1));
-      }
-    }
-    __syncthreads();
-    if (!s_ok) continue;
-    ju = s_ju;
-    const int jp = s_jp;
-    for (int col = j + warp; col <= ju; col += nw) {
-      double* cc = slot(col) + kv + j - col;  // cc[i] = A(j + i, col)
-      const double up = cc[jp], old0 = cc[0];
-      __syncwarp();
-      if (col == j) {
-        if (lane == 0) cc[0] = up;
-        for (int i = 1 + lane; i <= km; i += 32) cc[i] = sl[i];
-      } else {
-        if (lane == 0) cc[0] = up;
-        for (int i = 1 + lane; i <= km; i += 32) cc[i] = (i == jp ? old0 : cc[i]) - sl[i] * up;
-      }
+      if (warp == 1 && col == j + 1 && j + 1 < n)
+        gb_pivot(slot(j + 1) + kv, j + 1, min(kl, n - 2 - j), n, ku, ju, lane, sl[pn], &s_jp[pn], &s_ju[pn], &s_ok[pn],
+                 c.ipiv, flags);
     }
   }
   gb_wait<0>();
@@ -383,7 +396,7 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __
     for (int q = 0; q < GBC_ROWS; ++q) cur[q] = nxt[q];
     lcur = lnxt;
   }
-  // backward: b[j] /= U(j, j), then b[i] -= U(i, j) b[j] for i = j - kv .. j - 1
+  // backward: b[j] *= 1 / U(j, j), then b[i] -= U(i, j) b[j] for i = j - kv .. j - 1
   double dcur, dnxt = 0.0;
   auto loadU = [&](int j, double (&v)[GBC_ROWS]) {
     const int i0 = max(0, j - kv);
@@ -394,13 +407,13 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __
     }
   };
   loadU(n - 1, cur);
-  dcur = ab[(size_t)kv + (size_t)(n - 1) * ld];
+  dcur = 1.0 / ab[(size_t)kv + (size_t)(n - 1) * ld];
   for (int j = n - 1; j >= 0; --j) {
     if (j > 0) {
       loadU(j - 1, nxt);
-      dnxt = ab[(size_t)kv + (size_t)(j - 1) * ld];
+      dnxt = 1.0 / ab[(size_t)kv + (size_t)(j - 1) * ld];  // reciprocal of the next diagonal, off the critical path
     }
-    if (lane == 0) b[j] = b[j] / dcur;
+    if (lane == 0) b[j] = b[j] * dcur;
     __syncwarp();
     const double bj = b[j];
     const int i0 = max(0, j - kv);
@@ -453,7 +466,7 @@ cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t static_smem = sizeof(double) * (GBW_MAX_KL + 1) + 64;
+  const size_t static_smem = sizeof(double) * 2 * (GBW_MAX_KL + 1) + 64;
   if (c.kl <= GBW_MAX_KL && win + static_smem <= (size_t)optin) {
     const cudaError_t e = raise_smem_limit<k_gbtf2_win>();
     if (e != cudaSuccess) return e;

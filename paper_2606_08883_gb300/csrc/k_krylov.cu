@@ -658,10 +658,71 @@ cudaError_t launch_givens(double* H, double* cs, double* sn, double* gv, int j, 
   return cudaGetLastError();
 }
 
+// y = R^-1 g (R = leading k x k of the rotated H, column-major) by column-oriented back
+// substitution in one CTA: y_i = g_i / R_ii, then g_t -= R_ti y_i for t < i.  Stores -y, the form
+// the update sweep below subtracts.
+__global__ void __launch_bounds__(256) k_backsub(const double* __restrict__ H, const double* __restrict__ gv, int k,
+                                                 int ldh, double* __restrict__ yneg) {
+  __shared__ double g[260];
+  __shared__ double s_y;
+  for (int t = threadIdx.x; t < k; t += blockDim.x) g[t] = gv[t];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      s_y = g[i] / H[(size_t)i * ldh + i];
+      yneg[i] = -s_y;
+    }
+    __syncthreads();
+    const double yi = s_y;
+    for (int t = threadIdx.x; t < i; t += blockDim.x) g[t] -= H[(size_t)i * ldh + t] * yi;
+    __syncthreads();
+  }
+}
+
+// p += Z y over the k stored preconditioned vectors: the Arnoldi update sweep (cp.async ring,
+// each element summed in order t = 0 .. k-1) with h = -y.
+__global__ void __launch_bounds__(ARN_THREADS, 1) k_update_p(double* __restrict__ p, const double* __restrict__ Z,
+                                                            size_t n, const double* __restrict__ yneg, int k) {
+  extern __shared__ double sh[];   // -y | ring
+  constexpr int nt = ARN_THREADS;
+  for (int t = threadIdx.x; t < k; t += nt) sh[t] = yneg[t];
+  __syncthreads();
+  double* ring = sh + ARN_SMALL;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const size_t chunk = (n + G - 1) / G;
+  const size_t lo = (size_t)b * chunk < n ? (size_t)b * chunk : n;
+  const size_t hi = lo + chunk < n ? lo + chunk : n;
+  double nrm = 0.0;
+  double keep[UPD_EL];
+  for (size_t base = lo + tid; base < hi; base += (size_t)UPD_EL * nt) {
+    const size_t left = (hi - base + nt - 1) / nt;
+    if (left >= (size_t)UPD_EL)
+      update_ring<UPD_EL>(Z, n, k - 1, sh, base, tid, ring, p, nrm, keep);
+    else
+      update_ring<1>(Z, n, k - 1, sh, base, tid, ring, p, nrm, keep);
+  }
+}
+
 cudaError_t launch_update(double* p, const double* Z, size_t n, const double* H, const double* gv, int k, int ldh,
-                          cudaStream_t st) {
+                          double* ybuf, cudaStream_t st) {
   if (k == 0) return cudaSuccess;
-  k_update<<<red_grid(n), RED_THREADS, sizeof(double) * k, st>>>(p, Z, n, H, gv, k, ldh);
+  if (k > ARN_SMALL || k > 256) {
+    k_update<<<red_grid(n), RED_THREADS, sizeof(double) * k, st>>>(p, Z, n, H, gv, k, ldh);
+    count_launch(1);
+    return cudaGetLastError();
+  }
+  k_backsub<<<1, 256, 0, st>>>(H, gv, k, ldh, ybuf);
+  count_launch(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = raise_smem_limit<k_update_p>();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (int)std::min<size_t>((size_t)sms, (n + ARN_THREADS - 1) / ARN_THREADS);
+  if (grid < 1) grid = 1;
+  k_update_p<<<grid, ARN_THREADS, sizeof(double) * (ARN_SMALL + ARN_RING), st>>>(p, Z, n, ybuf, k);
   count_launch(1);
   return cudaGetLastError();
 }
