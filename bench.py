@@ -16,6 +16,7 @@ workload (rank 0 only).
 """
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -210,6 +211,28 @@ def phase_model(prob, q, prec):
     }
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
+# capture of the kernel behind a phase, valid only while the kernel's source file is unchanged (its
+# SHA-256 at capture time); see profiles/ for the capture commands.
+NCU_TRAFFIC = {
+    ("schwarz", "fp64"): (78.918656e6 + 2.441472e6, "paper_2606_08883_gb300/csrc/k_local.cu",
+                          "9f4d7b173a7045a58e0e28d7e4938d6a4cbf6aecd59b85502077c5b8a56e2a01"),
+}
+
+
+def ncu_traffic(name, prec):
+    entry = NCU_TRAFFIC.get((name, prec))
+    if entry is None:
+        return None
+    nbytes, src, sha = entry
+    try:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            cur = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return nbytes if cur == sha else None
+
+
 def roofline(prof, prob, q, prec, peaks, iterations):
     """Roofline of the phase with the largest event-timed share (the dominant kernel)."""
     model = phase_model(prob, q, prec)
@@ -237,7 +260,7 @@ def roofline(prof, prob, q, prec, peaks, iterations):
     peak = NOMINAL_FP32_TFLOPS if prec == "fp32" else NOMINAL_FP64_TFLOPS
     achieved = flops / per_launch_s / 1e12
     return name, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                  "traffic": None, "kernel": name, "launch_ms": per_launch_s * 1e3,
+                  "traffic": ncu_traffic(name, prec), "kernel": name, "launch_ms": per_launch_s * 1e3,
                   "algorithmic_flops_per_launch": flops,
                   "peak_source": ("FP32 FMA lanes x 2 x 2070 MHz x 152 SMs" if prec == "fp32" else
                                   "nominal GB300 dense FP64 1.25 TFLOP/s at 2070 MHz")}
