@@ -178,7 +178,7 @@ cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, co
                            double* zout, int* flags, cudaStream_t st);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
-size_t factor_smem_bytes(int w, bool fp32);
+size_t factor_smem_bytes(int w, bool fp32, int nch);
 
 // coupling system (k_coarse.cu)
 struct CoarseDev {

@@ -94,140 +94,224 @@ __device__ __forceinline__ int tri_row(int k) {
 // ============================================================================================
 // Factor: one CTA per subdomain box; dense w x w working arrays in shared memory.
 // ============================================================================================
+// packed-triangle position t -> (row i, column j <= i), and advancing it by `step` positions
+__device__ __forceinline__ void tri_at(int t, int& i, int& j) {
+  i = tri_row(t);
+  j = t - i * (i + 1) / 2;
+}
+__device__ __forceinline__ void tri_advance(int& i, int& j, int step) {
+  j += step;
+  while (j > i) {
+    j -= i + 1;
+    ++i;
+  }
+}
+
+// nch = 2: the top and the bottom recursion of the twisted order advance together, one line each
+// per iteration on one half of the CTA (each half with its own working arrays), and the middle line
+// follows; nch = 1: the lines one after the other (boxes too wide for two sets of working arrays).
+// Each line: Schur complement, right-looking Cholesky (the next diagonal's square root is taken by
+// the thread that updates it, so a column costs one barrier), L^-1 by elimination on the identity,
+// and S^-1 = L^-T L^-1.
 template <typename T>
-__global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __restrict__ Linv, int* flags) {
+__global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __restrict__ Linv, int* flags, int nch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const bool ohat = kind != BOX_OMEGA_ROBIN;
   const bool robin = kind != BOX_OHAT_DIRICHLET;
   const Box b = box_of(g, s, ohat);
-  const int w = b.w;
-  T* Sm = reinterpret_cast<T*>(smem_raw);  // Schur complement, then inverse work rows
+  const int w = b.w, h = b.h, m = h / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nth = nt / nch, half = tid / nth, tidh = tid - half * nth;
+  const size_t per = 4 * (size_t)w * w + 4 * (size_t)w;   // one recursion's working arrays
+  T* Sm = reinterpret_cast<T*>(smem_raw) + half * per;   // Schur complement, then inverse work rows
   T* Lm = Sm + w * w;                      // Cholesky factor of the line block
   T* Lc = Lm + w * w;                      // L_JJ^-1 of the current line
   T* Sp = Lc + w * w;                      // S^-1 of the previous (then current) line, lower part
   T* ev = Sp + w * w;                      // couplings to the previous line
   T* rinv = ev + w;                        // reciprocal diagonal of Lm
-  __shared__ int bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) bad = 0;
-  T* out = Linv + (size_t)s * box_stride(w, b.h, LS);
-  T* ec_out = out + (size_t)b.h * LS;      // line couplings E_J[x], read by every solve
-  const int npk = w * (w + 1) / 2;
-  const int h = b.h, m = h / 2;
   T* ev2 = rinv + w;                       // second coupling vector (middle line)
-  // processing order: top lines 0..m-1, bottom lines h-1..m+1, then the middle line m
-  for (int step = 0; step < h; ++step) {
-    const bool top = step < m, bottom = !top && step < h - 1;
-    const int J = top ? step : (bottom ? h - 1 - (step - m) : m);
+  // the bottom recursion's last S^-1, read by the middle line when nch = 2
+  const T* Sp_bot = reinterpret_cast<T*>(smem_raw) + (nch == 2 ? per : 0) + 3 * (size_t)w * w;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  T* out = Linv + (size_t)s * box_stride(w, h, LS);
+  T* ec_out = out + (size_t)h * LS;        // line couplings E_J[x], read by every solve
+  const int npk = w * (w + 1) / 2;
+  const int iters = nch == 2 ? (m > h - 1 - m ? m : h - 1 - m) + 1 : h;
+  for (int it = 0; it < iters; ++it) {
+    // this half's line: top lines 0..m-1, bottom lines h-1..m+1, then the middle line m
+    bool top, bottom, mid, active;
+    int J;
+    if (nch == 2) {
+      const bool last = it == iters - 1;
+      top = !last && half == 0 && it < m;
+      bottom = !last && half == 1 && h - 1 - it >= m + 1;
+      mid = last && half == 0;
+      J = last ? m : (half == 0 ? it : h - 1 - it);
+      active = top || bottom || mid;
+    } else {
+      top = it < m;
+      bottom = !top && it < h - 1;
+      mid = !top && !bottom;
+      J = top ? it : (bottom ? h - 1 - (it - m) : m);
+      active = true;
+    }
     // previous line of the same recursion and its coupling vector: top uses E_J = eup(J),
     // bottom uses E_{J+1} = eup(J+1)
     const bool has_prev = top ? J > 0 : (bottom ? J < h - 1 : false);
     // (1) S_J = D_J - E S_prev^-1 E (middle: minus both sides), lower triangle
-    for (int i = tid; i < w; i += nt) {
-      double d, o, e;
-      line_coeffs(g, b, robin, J, i, d, o, e);
-      ec_out[(size_t)J * w + i] = (T)e;
-      Sm[i * w + i] = (T)d;
-      if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
-      if (top) {
-        ev[i] = (T)e;
-      } else if (bottom) {
-        double d2, o2, e2;
-        line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
-        ev[i] = (T)e2;
-      } else {
-        ev[i] = (T)e;                      // E_m (towards line m-1)
-        double d2, o2, e2 = 0.0;
-        if (J + 1 < h) line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
-        ev2[i] = (T)e2;                    // E_{m+1} (towards line m+1)
+    if (active)
+      for (int i = tidh; i < w; i += nth) {
+        double d, o, e;
+        line_coeffs(g, b, robin, J, i, d, o, e);
+        ec_out[(size_t)J * w + i] = (T)e;
+        Sm[i * w + i] = (T)d;
+        if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
+        if (top) {
+          ev[i] = (T)e;
+        } else if (bottom) {
+          double d2, o2, e2;
+          line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+          ev[i] = (T)e2;
+        } else {
+          ev[i] = (T)e;                      // E_m (towards line m-1)
+          double d2, o2, e2 = 0.0;
+          if (J + 1 < h) line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+          ev2[i] = (T)e2;                    // E_{m+1} (towards line m+1)
+        }
       }
-    }
     __syncthreads();
-    const bool mid_up = !top && !bottom && m > 0;          // S_{m-1}^-1 from the stored top line
-    const bool mid_dn = !top && !bottom && m + 1 < h;      // S_{m+1}^-1 still in Sp
-    const T* Sup = out + (size_t)(m > 0 ? m - 1 : 0) * LS;
-    for (int k = tid; k < npk; k += nt) {
-      const int i = tri_row(k), j = k - i * (i + 1) / 2;
-      T v = (i == j || i == j + 1) ? Sm[i * w + j] : (T)0;
-      if (has_prev) v -= ev[i] * ev[j] * Sp[i * w + j];
-      if (mid_up) v -= ev[i] * ev[j] * Sup[k];
-      if (mid_dn) v -= ev2[i] * ev2[j] * Sp[i * w + j];
-      Sm[i * w + j] = v;
+    if (active) {
+      const bool mid_up = mid && m > 0;          // S_{m-1}^-1: own Sp (nch = 2) or the stored top line
+      const bool mid_dn = mid && m + 1 < h;      // S_{m+1}^-1: the bottom recursion's Sp
+      const T* Sup = out + (size_t)(m > 0 ? m - 1 : 0) * LS;
+      int i, j;
+      tri_at(tidh, i, j);
+      for (int k = tidh; k < npk; k += nth, tri_advance(i, j, nth)) {
+        T v = (i == j || i == j + 1) ? Sm[i * w + j] : (T)0;
+        if (has_prev) v -= ev[i] * ev[j] * Sp[i * w + j];
+        if (mid_up) v -= ev[i] * ev[j] * (nch == 2 ? Sp[i * w + j] : Sup[k]);
+        if (mid_dn) v -= ev2[i] * ev2[j] * (nch == 2 ? Sp_bot[i * w + j] : Sp[i * w + j]);
+        Sm[i * w + j] = v;
+      }
     }
     __syncthreads();
     // (2) Cholesky of S_J: right-looking, column k of L written to Lm, trailing update in Sm
-    for (int k = 0; k < w; ++k) {
-      if (tid == 0) {
-        T p = Sm[k * w + k];
-        if (!(p > (T)0) || !isfinite((double)p)) {
-          bad = 1;
-          p = (T)1;
-        }
-        const T d = sqrt(p);
-        Lm[k * w + k] = d;
-        rinv[k] = (T)1 / d;
+    if (active && tidh == 0) {
+      T p = Sm[0];
+      if (!(p > (T)0) || !isfinite((double)p)) {
+        bad = 1;
+        p = (T)1;
       }
-      __syncthreads();
-      const T rd = rinv[k];
-      const int m = w - k - 1;
-      for (int i = tid; i < m; i += nt) Lm[(k + 1 + i) * w + k] = Sm[(k + 1 + i) * w + k] * rd;
-      const int nup = m * (m + 1) / 2;
-      for (int t = tid; t < nup; t += nt) {
-        const int ii = tri_row(t), jj = t - ii * (ii + 1) / 2;
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        Sm[i * w + j] -= (Sm[i * w + k] * rd) * (Sm[j * w + k] * rd);
+      const T d = sqrt(p);
+      Lm[0] = d;
+      rinv[0] = (T)1 / d;
+    }
+    __syncthreads();
+    for (int k = 0; k < w; ++k) {
+      if (active) {
+        const T rd = rinv[k];
+        const int mm = w - k - 1;
+        for (int i = tidh; i < mm; i += nth) Lm[(k + 1 + i) * w + k] = Sm[(k + 1 + i) * w + k] * rd;
+        const int nup = mm * (mm + 1) / 2;
+        int ii, jj;
+        tri_at(tidh, ii, jj);
+        for (int t = tidh; t < nup; t += nth, tri_advance(ii, jj, nth)) {
+          const int i = k + 1 + ii, j = k + 1 + jj;
+          const T v = Sm[i * w + j] - (Sm[i * w + k] * rd) * (Sm[j * w + k] * rd);
+          Sm[i * w + j] = v;
+          if (t == 0) {  // the next diagonal: its square root for column k + 1
+            T p = v;
+            if (!(p > (T)0) || !isfinite((double)p)) {
+              bad = 1;
+              p = (T)1;
+            }
+            const T d = sqrt(p);
+            Lm[(k + 1) * w + k + 1] = d;
+            rinv[k + 1] = (T)1 / d;
+          }
+        }
       }
       __syncthreads();
     }
     // (3) Lc = Lm^-1 by right-looking elimination on the identity (work rows in Sm)
-    for (int k = tid; k < w * w; k += nt) {
-      const int i = k / w, j = k % w;
-      Sm[k] = (i == j) ? (T)1 : (T)0;
-    }
+    if (active)
+      for (int k = tidh; k < w * w; k += nth) {
+        const int i = k / w, j = k - i * w;
+        Sm[k] = (i == j) ? (T)1 : (T)0;
+      }
     __syncthreads();
     for (int k = 0; k < w; ++k) {
-      const T rk = rinv[k];
-      for (int c = tid; c <= k; c += nt) Lc[k * w + c] = Sm[k * w + c] * rk;
-      const int rows = w - k - 1, cols = k + 1;
-      for (int t = tid; t < rows * cols; t += nt) {
-        const int i = k + 1 + t / cols, c = t % cols;
-        Sm[i * w + c] -= Lm[i * w + k] * (Sm[k * w + c] * rk);
+      if (active) {
+        const T rk = rinv[k];
+        for (int c = tidh; c <= k; c += nth) Lc[k * w + c] = Sm[k * w + c] * rk;
+        const int rows = w - k - 1, cols = k + 1;
+        for (int t = tidh; t < rows * cols; t += nth) {
+          const int i = k + 1 + t / cols, c = t % cols;
+          Sm[i * w + c] -= Lm[i * w + k] * (Sm[k * w + c] * rk);
+        }
       }
       __syncthreads();
     }
-    // (4) S_J^-1 = Lc^T Lc (lower part), store packed, keep for the next line's Schur complement
-    for (int k = tid; k < npk; k += nt) {
-      const int i = tri_row(k), j = k - i * (i + 1) / 2;
-      T acc = 0;
-      for (int r = i; r < w; ++r) acc += Lc[r * w + i] * Lc[r * w + j];
-      Sp[i * w + j] = acc;
-      out[(size_t)J * LS + k] = acc;
+    // (4) S_J^-1 = Lc^T Lc (lower part), store packed, keep for the next line's Schur complement;
+    //     two entries per pass for two independent sums
+    if (active) {
+      int i0, j0, i1, j1;
+      tri_at(tidh, i0, j0);
+      i1 = i0;
+      j1 = j0;
+      tri_advance(i1, j1, nth);
+      for (int k = tidh; k < npk; k += 2 * nth) {
+        const bool two = k + nth < npk;
+        T a0 = 0, a1 = 0;
+        if (two) {
+          // the second entry follows the first in packed order, so i1 >= i0: the first entry's
+          // head, then both together (each summed in increasing q, as a single sum would be)
+          for (int q = i0; q < i1; ++q) a0 += Lc[q * w + i0] * Lc[q * w + j0];
+          for (int q = i1; q < w; ++q) {
+            a0 += Lc[q * w + i0] * Lc[q * w + j0];
+            a1 += Lc[q * w + i1] * Lc[q * w + j1];
+          }
+        } else {
+          for (int q = i0; q < w; ++q) a0 += Lc[q * w + i0] * Lc[q * w + j0];
+        }
+        Sp[i0 * w + j0] = a0;
+        out[(size_t)J * LS + k] = a0;
+        if (two) {
+          Sp[i1 * w + j1] = a1;
+          out[(size_t)J * LS + k + nth] = a1;
+        }
+        tri_advance(i0, j0, 2 * nth);
+        tri_advance(i1, j1, 2 * nth);
+      }
     }
     __syncthreads();
   }
   if (tid == 0 && bad) atomicOr(flags, FLAG_SINGULAR_LOCAL);
 }
 
-size_t factor_smem_bytes(int w, bool fp32) {
+size_t factor_smem_bytes(int w, bool fp32, int nch) {
   const size_t e = fp32 ? 4 : 8;
-  return e * (4 * (size_t)w * w + 3 * (size_t)w) + 16;
+  return e * nch * (4 * (size_t)w * w + 4 * (size_t)w) + 16;
 }
 
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
                           cudaStream_t st) {
   (void)hgt;
   const int S = g.mx * g.my;
-  const size_t sm = factor_smem_bytes(w, fp32);
+  // both recursions at once when two sets of working arrays still leave room for two CTAs per SM
+  const int nch = factor_smem_bytes(w, fp32, 2) <= 112 * 1024 ? 2 : 1;
+  const size_t sm = factor_smem_bytes(w, fp32, nch);
   if (fp32) {
     const cudaError_t e = raise_smem_limit<k_factor<float>>();
     if (e != cudaSuccess) return e;
-    k_factor<float><<<S, 256, sm, st>>>(g, kind, LS, (float*)Linv, flags);
+    k_factor<float><<<S, 256, sm, st>>>(g, kind, LS, (float*)Linv, flags, nch);
     count_launch(1);
   } else {
     const cudaError_t e = raise_smem_limit<k_factor<double>>();
     if (e != cudaSuccess) return e;
-    k_factor<double><<<S, 256, sm, st>>>(g, kind, LS, (double*)Linv, flags);
+    k_factor<double><<<S, 256, sm, st>>>(g, kind, LS, (double*)Linv, flags, nch);
     count_launch(1);
   }
   return cudaGetLastError();
