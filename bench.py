@@ -200,14 +200,21 @@ def phase_model(prob, q, prec):
     def factor(w, h):  # per line: Schur update + Cholesky + triangular inverse = w^3 / 2 FMA
         return S * h * w ** 3, S * h * packed(w) * elt
 
-    def solve(w, h, nr):  # forward + backward: 4 triangular products of w^2/2 FMA per line
-        return S * h * 4 * w * w * nr, S * (2 * h * packed(w) * elt + 2 * w * h * 8 * nr)
+    def solve(w, h, nr, keep=0):
+        # twisted solve: h - 1 eliminations, the middle line, and back substitution over the kept
+        # lines (a restricted Schwarz solve keeps h - 2l of them); each step is one symmetric line
+        # product of w^2 FMA per right-hand side.  Bytes: each line block and the couplings once,
+        # the right-hand side and the result.
+        m = h // 2
+        products = (h - 1) + 1 + (m - keep) + (h - 1 - keep - m)
+        return (S * products * 2 * w * w * nr,
+                S * (h * packed(w) * elt + h * w * elt + 2 * w * h * 8 * nr))
 
     n = prob.cells
     return {
         "factor_ohat_robin": factor(wo, ho), "factor_omega": factor(wl, hl), "factor_ohat_dirichlet": factor(wo, ho),
         "informed": solve(wo, ho, 4), "basis": solve(wl, hl, 4), "particular": solve(wl, hl, 1),
-        "schwarz": solve(wo, ho, 1), "residual": (9 * n, 40 * n), "reconstruct": (8 * n, 56 * n),
+        "schwarz": solve(wo, ho, 1, keep=q.oversample), "residual": (9 * n, 40 * n), "reconstruct": (8 * n, 56 * n),
     }
 
 
