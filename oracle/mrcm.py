@@ -23,14 +23,19 @@ Apply z = T r (the modified MRCM-O of Sec. 3: homogeneous conditions, source r):
   psi_s0 = (A^R_{Omega_s})^-1 r|Omega_s with traces F_s0 = t_R psi_s0,c, |f| P_s0 = beta F_s0;
   G c = -g0 where g0 collects the particular traces row by row;
   z|Omega_s = psi_s0 + sum_k c_sk psi_sk;
-  then ``smooth_steps`` restricted additive Schwarz sweeps: rho = r - A z,
-  delta_s = A[hat-Omega_s, hat-Omega_s]^-1 rho|hat-Omega_s, z|Omega_s += delta_s|Omega_s.
+  then ``smooth_steps`` restricted Schwarz sweeps (the smoothing of MRCM-OS step 4, Sec. 2.1):
+  additive (smooth_kind 0): rho = r - A z, delta_s = A[hat-Omega_s, hat-Omega_s]^-1 rho|hat-Omega_s,
+  z|Omega_s += delta_s|Omega_s for all s at once; multiplicative multicolour (smooth_kind 1): the
+  subdomains are coloured by the parities of their grid coordinates (2^dim colours) and the
+  additive step is taken one colour after the other, each colour with the residual left by the
+  colours before it.
 
 Pinned by (tests/test_oracle_mrcm.py): one subdomain gives T = A^-1; l = 0 gives indicator phi;
 a monolithic dense solve of the whole coupled MRCM system equals the superposition; per-cell mass
 balance and weak flux / pressure continuity of the MRCM reconstruction; exactness of P0 Robin
 coupling on a field that is constant along the interfaces; linearity of T; the smoothing sweep
-leaves A^-1 r unchanged.
+leaves A^-1 r unchanged; the additive sweep equals a dense restricted additive Schwarz step; with
+l = 0 the multiplicative sweep equals block Gauss-Seidel over the colour-ordered subdomain blocks.
 """
 
 import numpy as np
@@ -48,7 +53,7 @@ class _Sub:
 
 
 class MRCMOS:
-    def __init__(self, K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0):
+    def __init__(self, K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0, smooth_kind=0):
         K = np.asarray(K, dtype=np.float64)
         self.K, self.h, self.dim = K, [float(v) for v in h], dim
         self.shape = K.shape
@@ -57,6 +62,9 @@ class MRCMOS:
         self.sub = [int(v) for v in sub]
         self.l = int(l)
         self.smooth_steps = int(smooth_steps)
+        if smooth_kind not in (0, 1):
+            raise ValueError("smooth_kind must be 0 (additive) or 1 (multiplicative multicolour)")
+        self.smooth_kind = int(smooth_kind)
         self.alpha = float(alpha)
         self.degree = int(iface_degree)
         self.nq = 1 + self.degree * (dim - 1)  # polynomial functions per side
@@ -227,14 +235,26 @@ class MRCMOS:
             z[d.op.sl] = zs.reshape(d.op.w[2], d.op.w[1], d.op.w[0])
         return z
 
+    def colour(self, s):
+        """Colour of subdomain s: the parities of its grid coordinates, x in bit 0, y in bit 1, z in bit 2."""
+        c = 0
+        for a in range(self.dim):
+            c |= (int(self.part.box[s, 0, a] // self.sub[a]) % 2) << a
+        return c
+
     def sweep(self, r, z):
-        """One restricted additive Schwarz sweep on A z = r."""
-        rho = r - matvec(self.T, z, self.dim)
+        """One restricted Schwarz sweep on A z = r: additive (all subdomains from one residual) or
+        multiplicative multicolour (the additive step per colour, colours in order 0 .. 2^dim - 1,
+        each from the residual after the previous colours)."""
+        groups = [list(self.subs)] if self.smooth_kind == 0 else \
+            [[d for d in self.subs if self.colour(d.s) == c] for c in range(2 ** self.dim)]
         z_new = z.copy()
-        for d in self.subs:
-            w = d.schwarz.w
-            delta = d.schwarz.solve(d.schwarz.restrict(rho)).reshape(w[2], w[1], w[0])
-            z_new[d.op.sl] += delta[d.inner]
+        for group in groups:
+            rho = r - matvec(self.T, z_new, self.dim)
+            for d in group:
+                w = d.schwarz.w
+                delta = d.schwarz.solve(d.schwarz.restrict(rho)).reshape(w[2], w[1], w[0])
+                z_new[d.op.sl] += delta[d.inner]
         return z_new
 
     def apply_parts(self, r):

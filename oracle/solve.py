@@ -3,7 +3,8 @@
 Arguments mirror the library's problem / parameter structs, as plain numpy data:
 K (nz, ny, nx) > 0; h = (hx, hy, hz); dim 2 or 3; bc_kind[6] (0 Dirichlet, 1 Neumann) for the sides
 -x, +x, -y, +y, -z, +z; bc_val[6] (None or the per-face data of that side); f (cell-integrated
-source or None); sub[3]; l; smooth_steps; alpha; tol; tol_relative; restart; max_iter.
+source or None); sub[3]; l; smooth_steps; alpha; tol; tol_relative; restart; max_iter;
+smooth_kind (0 additive, 1 multiplicative multicolour Schwarz sweeps).
 """
 
 import numpy as np
@@ -13,16 +14,16 @@ from .mrcm import MRCMOS
 from .gmres import fgmres
 
 
-def build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0):
-    return MRCMOS(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree)
+def build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0, smooth_kind=0):
+    return MRCMOS(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree, smooth_kind)
 
 
 def solve(K, h, dim, bc_kind, bc_val=None, f=None, sub=(16, 16, 1), l=2, smooth_steps=1,
           alpha=10.0, tol=1e-8, tol_relative=True, restart=30, max_iter=1000, p0=None, pre=None, check_every_step=True,
-          iface_degree=0):
+          iface_degree=0, smooth_kind=0):
     K = np.asarray(K, dtype=np.float64)
     if pre is None:
-        pre = build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree)
+        pre = build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree, smooth_kind)
     b = rhs(K, h, dim, bc_kind, bc_val, f)
     shape = K.shape
 
@@ -40,6 +41,6 @@ def solve(K, h, dim, bc_kind, bc_val=None, f=None, sub=(16, 16, 1), l=2, smooth_
     return p, info, pre
 
 
-def apply_precond(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, r):
-    pre = build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha)
+def apply_precond(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, r, smooth_kind=0):
+    pre = build(K, h, dim, bc_kind, sub, l, smooth_steps, alpha, smooth_kind=smooth_kind)
     return pre.apply(np.asarray(r, dtype=np.float64).reshape(np.asarray(K).shape))

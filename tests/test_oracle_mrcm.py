@@ -188,6 +188,68 @@ def test_schwarz_sweep_matches_dense_restricted_additive_schwarz():
     assert np.linalg.norm(pre.sweep(r, z_star) - z_star) <= 1e-11 * np.linalg.norm(z_star)
 
 
+def _colour_blocks(pre):
+    """Cells of each colour (independent of the oracle's colouring code: parity of the subdomain
+    coordinates of the cell itself)."""
+    nz, ny, nx = pre.shape
+    out = {}
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                c = ((i // pre.sub[0]) % 2) | (((j // pre.sub[1]) % 2) << 1) | (((k // pre.sub[2]) % 2) << 2)
+                out.setdefault(c, []).append(i + nx * (j + ny * k))
+    return [out[c] for c in sorted(out)]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_multiplicative_sweep_without_overlap_is_block_gauss_seidel(dim):
+    # l = 0: each colour's subdomains are pairwise uncoupled, so one multiplicative sweep is the
+    # textbook block Gauss-Seidel step z + M^-1 (r - A z), M the block lower triangle of A in colour
+    # order; the additive sweep is block Jacobi z + D^-1 (r - A z).
+    n, sub = ((16, 12, 1), (4, 3, 1)) if dim == 2 else ((8, 6, 4), (2, 3, 2))
+    prob = W.random_problem(n, dim=dim, seed=21, contrast=1e3)
+    A = None
+    for kind in (0, 1):
+        pre = MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, sub, 0, 1, 10.0, 0, kind)
+        if A is None:
+            A = _dense_A(pre)
+        blocks = _colour_blocks(pre)
+        order = np.concatenate(blocks)
+        Ap = A[np.ix_(order, order)]
+        M = np.zeros_like(Ap)
+        o = 0
+        for bl in blocks:
+            o2 = o + len(bl)
+            if kind == 1:
+                M[o:o2, :o2] = Ap[o:o2, :o2]
+            else:
+                M[o:o2, o:o2] = Ap[o:o2, o:o2]
+            o = o2
+        rng = np.random.default_rng(22 + kind)
+        r, z = rng.standard_normal(prob.K.shape), rng.standard_normal(prob.K.shape)
+        res = (r.ravel() - A @ z.ravel())[order]
+        z_ref = z.ravel().copy()
+        z_ref[order] += np.linalg.solve(M, res)
+        assert np.allclose(pre.sweep(r, z).ravel(), z_ref, rtol=1e-11, atol=1e-11), kind
+
+
+def test_multiplicative_sweep_fixed_point_and_energy_decrease():
+    prob = W.random_problem((16, 16, 1), seed=23, contrast=1e3)
+    pre = MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, (4, 4, 1), 2, 1, 10.0, 0, 1)
+    A = _dense_A(pre)
+    r = np.random.default_rng(24).standard_normal(prob.K.shape)
+    z_star = np.linalg.solve(A, r.ravel()).reshape(r.shape)
+    assert np.linalg.norm(pre.sweep(r, z_star) - z_star) <= 1e-11 * np.linalg.norm(z_star)
+    # repeated sweeps from z = 0 converge to A^-1 r
+    z = np.zeros_like(r)
+    errs = []
+    for _ in range(40):
+        z = pre.sweep(r, z)
+        e = (z - z_star).ravel()
+        errs.append(np.sqrt(e @ A @ e))
+    assert errs[-1] < 1e-3 * errs[0]
+
+
 @pytest.mark.parametrize("l,degree,dim", [(1, 0, 2), (3, 0, 2), (2, 1, 2), (1, 0, 3)])
 def test_basis_equals_restricted_oversampled_solution(l, degree, dim):
     # Eq. 15 and the Robin condition: phi_s^k is the Robin trace of q^k on Gamma_s, so the local
