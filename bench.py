@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--smooth", default="additive", choices=["additive", "multiplicative"],
+                    help="Schwarz sweeps: restricted additive (default) or multiplicative multicolour")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=8, help="GMRES iterations per reference-arm sample")
@@ -75,6 +77,7 @@ def workload(args, rank=0):
     prob, q = W.channels(args.N, seed=rank_seed(rank), prec=W.PREC_FP32 if args.prec == "fp32" else W.PREC_FP64)
     q.restart = args.restart
     q.max_iter = 3 * args.restart
+    q.smooth_kind = 1 if getattr(args, "smooth", "additive") == "multiplicative" else 0
     return prob, q
 
 
@@ -82,7 +85,7 @@ def config_dict(args, prob, q):
     return {"workload": f"channels-{args.N}x{args.N}-contrast1e6-fill0.30", "cells": prob.cells,
             "subdomains": f"{prob.n[0] // q.sub[0]}x{prob.n[1] // q.sub[1]} of {q.sub[0]}x{q.sub[1]}",
             "oversample": q.oversample, "smooth_steps": q.smooth_steps, "alpha": q.alpha, "restart": q.restart,
-            "tol_relative": q.tol, "local_prec": args.prec, "l2": "flushed between timed steps (256 MiB write)",
+            "tol_relative": q.tol, "local_prec": args.prec, "smoothing": getattr(args, "smooth", "additive"), "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single-gpu"}
 
 
@@ -94,7 +97,7 @@ from paper_2606_08883_gb300 import workloads as W
 from oracle.solve import build, solve
 prob, q = W.channels({N}, seed=1)
 t0 = time.perf_counter()
-pre = build(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha)
+pre = build(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha, smooth_kind={kind})
 t1 = time.perf_counter()
 p, info, _ = solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub, l=q.oversample,
                    smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol, restart={restart}, max_iter={iters},
@@ -105,11 +108,11 @@ print(json.dumps({{"setup_s": t1 - t0, "iter_s": t2 - t1, "iters": info["iterati
 """
 
 
-def run_oracle_sample(N, restart, iters, timeout=900):
+def run_oracle_sample(N, restart, iters, timeout=900, kind=0):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, N=N, restart=restart, iters=iters)
+    code = ORACLE_SNIPPET.format(root=ROOT, N=N, restart=restart, iters=iters, kind=int(kind))
     r = subprocess.run([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
                        env=env, timeout=timeout)
     if r.returncode != 0:
@@ -211,10 +214,13 @@ def phase_model(prob, q, prec):
                 S * (h * packed(w) * elt + h * w * elt + 2 * w * h * 8 * nr))
 
     n = prob.cells
+    schwarz = solve(wo, ho, 1, keep=q.oversample)
+    if getattr(q, "smooth_kind", 0) == 1:  # multiplicative: one launch per colour, a quarter of the boxes each
+        schwarz = (schwarz[0] / 4, schwarz[1] / 4)
     return {
         "factor_ohat_robin": factor(wo, ho), "factor_omega": factor(wl, hl), "factor_ohat_dirichlet": factor(wo, ho),
         "informed": solve(wo, ho, 4), "basis": solve(wl, hl, 4), "particular": solve(wl, hl, 1),
-        "schwarz": solve(wo, ho, 1, keep=q.oversample), "residual": (9 * n, 40 * n), "reconstruct": (8 * n, 56 * n),
+        "schwarz": schwarz, "residual": (9 * n, 40 * n), "reconstruct": (8 * n, 56 * n),
     }
 
 
@@ -288,7 +294,7 @@ def reference_arm(args):
         return
     rates = []
     for step in range(args.warmup + args.steps):
-        s = run_oracle_sample(args.N, args.restart, args.ref_iters)
+        s = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0)
         if step >= args.warmup:
             rates.append(s)
     need = ORACLE_FULL_ITERS.get((args.N, args.restart), None)
@@ -318,7 +324,7 @@ def mrcm_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # before any CUDA call: the oracle runs in its own process on the host cores
         try:
-            cpu = run_oracle_sample(args.N, args.restart, args.ref_iters)
+            cpu = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0)
         except Exception as exc:  # reported, never silently replaced
             cpu = {"error": str(exc)[:300]}
     import torch

@@ -81,7 +81,14 @@ typedef struct mrcm_params {
   int32_t restart;          /* Krylov dimension m, 1..256 */
   int32_t max_iter;         /* cap on preconditioner applications, >= 1 */
   int32_t local_prec;       /* MRCM_PREC_FP64 or MRCM_PREC_FP32 (local factors and solves) */
+  int32_t smooth_kind;      /* MRCM_SMOOTH_ADDITIVE (default) or MRCM_SMOOTH_MULTIPLICATIVE: how the
+                               smoothing sweeps of MRCM-OS step 4 (Sec. 2.1) visit the subdomains.
+                               Multiplicative: subdomains coloured by the parities of their grid
+                               coordinates (2^dim colours), one restricted step per colour in order,
+                               each from the residual left by the previous colours */
 } mrcm_params;
+
+enum { MRCM_SMOOTH_ADDITIVE = 0, MRCM_SMOOTH_MULTIPLICATIVE = 1 };
 
 typedef struct mrcm_result {
   int32_t iterations;       /* applications of T */

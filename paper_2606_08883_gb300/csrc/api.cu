@@ -370,20 +370,27 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   // reconstruction, into the buffer that makes the last smoothing sweep land in z: each sweep
   // reads one buffer (its residual needs the neighbours' values) and writes the other
   const int s = h->prm.smooth_steps;
+  const bool mult = h->prm.smooth_kind == MRCM_SMOOTH_MULTIPLICATIVE;
   double* zb[2] = {z, at<double>(h, L.zt)};
-  double* z_rec = zb[s & 1];
+  double* z_rec = mult ? z : zb[s & 1];
   {
     Phase ph(h, MRCM_PH_RECONSTRUCT, st);
     CK(h, launch_reconstruct(g, at<double>(h, L.psi0), at<double>(h, L.psi), tables(h).cidx, at<double>(h, L.gc),
                              z_rec, st));
   }
   if (h->keep_z0) CK(h, cudaMemcpyAsync(at<double>(h, L.z0), z_rec, 8 * ncell(h), cudaMemcpyDeviceToDevice, st));
-  // smoothing sweeps (restricted additive Schwarz; residual fused into the local solve)
+  // smoothing sweeps (residual fused into the local solve): additive, all boxes from one residual
+  // (ping-pong buffers); or multiplicative multicolour, one launch per colour updating z in place
   for (int it = 0; it < s; ++it) {
     Phase ph(h, MRCM_PH_SCHWARZ, st);
-    const double* zin = zb[(s - it) & 1];
-    double* zout = zb[(s - it - 1) & 1];
-    CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), st));
+    if (mult) {
+      for (int colour = 0; colour < (1 << P.dim); ++colour)
+        CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, z, z, at<int>(h, L.flags), colour, st));
+    } else {
+      const double* zin = zb[(s - it) & 1];
+      double* zout = zb[(s - it - 1) & 1];
+      CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), -1, st));
+    }
   }
   return MRCM_OK;
 }

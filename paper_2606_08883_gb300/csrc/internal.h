@@ -175,7 +175,7 @@ cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, cons
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, int* flags, cudaStream_t st);
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, cudaStream_t st);
+                           double* zout, int* flags, int colour, cudaStream_t st);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
 size_t factor_smem_bytes(int w, bool fp32, int nch);

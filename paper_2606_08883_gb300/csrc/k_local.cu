@@ -365,7 +365,17 @@ struct SolveArgs {
   double* mom;         // particular: mom0 [S][4][2]; basis: mom [S][4][4][2]
   const double* zin;   // schwarz: z before the sweep (read only)
   int* flags;          // device status word (FLAG_TIMEOUT if a bounded wait gives up)
+  int colour;          // schwarz: -1 all boxes, else only the boxes of this colour (see colour_box)
 };
+
+// Subdomain of the b-th box of a colour: colour bit 0 = parity of the x index, bit 1 = of the y
+// index; boxes of a colour in row-major order of their subdomains.
+__device__ __forceinline__ int colour_box(const Geo& g, int colour, int b) {
+  const int cx = colour & 1, cy = (colour >> 1) & 1;
+  const int nxc = (g.mx - cx + 1) / 2;
+  const int I = cx + 2 * (b % nxc), J = cy + 2 * (b / nxc);
+  return J * g.mx + I;
+}
 
 // Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.
 __device__ __forceinline__ void gamma_face(const Geo& g, int s, int k, int t, int& gx, int& gy, int& ox2, int& oy2,
@@ -471,7 +481,7 @@ template <typename T, int MODE, int NR, int NBUF>
 __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool RES = NBUF == 0;
-  const int s = blockIdx.x;
+  const int s = (MODE == MODE_SCHWARZ && a.colour >= 0) ? colour_box(g, a.colour, blockIdx.x) : (int)blockIdx.x;
   const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
@@ -828,7 +838,11 @@ static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, 
   const int w = g.sx + (ohat ? 2 * g.l : 0);
   int threads = (2 * w * LineTPR<T>::value + 31) / 32 * 32;
   if (threads < 128) threads = 128;
-  k_solve<T, MODE, NR, NBUF><<<g.mx * g.my, threads, sm, st>>>(g, a);
+  int grid = g.mx * g.my;
+  if (MODE == MODE_SCHWARZ && a.colour >= 0)
+    grid = ((g.mx - (a.colour & 1) + 1) / 2) * ((g.my - ((a.colour >> 1) & 1) + 1) / 2);
+  if (grid == 0) return cudaSuccess;
+  k_solve<T, MODE, NR, NBUF><<<grid, threads, sm, st>>>(g, a);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -878,25 +892,29 @@ cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, d
     count_launch(1);
     return cudaGetLastError();
   }
-  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags};
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags, -1};
   return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
 }
 
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
                          double* mom, int* flags, cudaStream_t st) {
-  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags};
+  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags, -1};
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, int* flags, cudaStream_t st) {
-  SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags};
+  SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags, -1};
   return launch_solve<MODE_PARTICULAR, 1>(g, a, false, fp32, st);
 }
 
+// colour -1: every box (additive sweep, zin and zout distinct); colour c: the boxes of colour c only,
+// in place allowed (zin == zout): boxes of one colour are two subdomains apart and the oversampling
+// is narrower than a subdomain, so no box reads (region plus the stencil's one-cell rim) a cell
+// that another box of its colour writes.
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, cudaStream_t st) {
-  SolveArgs a{Linv, LS, r, zout, nullptr, zin, flags};
+                           double* zout, int* flags, int colour, cudaStream_t st) {
+  SolveArgs a{Linv, LS, r, zout, nullptr, zin, flags, colour};
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 

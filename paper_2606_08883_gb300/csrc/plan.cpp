@@ -29,6 +29,8 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   if (q.restart < 1 || q.restart > 256) return "restart must be in 1..256";
   if (q.max_iter < 1) return "max_iter must be >= 1";
   if (q.local_prec != MRCM_PREC_FP64 && q.local_prec != MRCM_PREC_FP32) return "local_prec must be FP64 or FP32";
+  if (q.smooth_kind != MRCM_SMOOTH_ADDITIVE && q.smooth_kind != MRCM_SMOOTH_MULTIPLICATIVE)
+    return "smooth_kind must be MRCM_SMOOTH_ADDITIVE or MRCM_SMOOTH_MULTIPLICATIVE";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
     if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";

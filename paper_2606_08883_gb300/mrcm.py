@@ -21,6 +21,7 @@ if not os.path.exists(_LIB_PATH):
 _lib = C.CDLL(_LIB_PATH)
 
 MRCM_OK, MRCM_ERR_INVALID_ARG, MRCM_ERR_OOM, MRCM_ERR_SINGULAR, MRCM_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+MRCM_SMOOTH_ADDITIVE, MRCM_SMOOTH_MULTIPLICATIVE = 0, 1
 MRCM_ERR_TIMEOUT, MRCM_ERR_CUDA, MRCM_ERR_BUSY, MRCM_ERR_UNSUPPORTED, MRCM_ERR_CANCELLED = 5, 6, 7, 8, 9
 MRCM_BC_DIRICHLET, MRCM_BC_NEUMANN = 0, 1
 MRCM_PREC_FP64, MRCM_PREC_FP32 = 0, 1
@@ -35,7 +36,8 @@ class mrcm_problem(C.Structure):
 class mrcm_params(C.Structure):
     _fields_ = [("sub", C.c_int32 * 3), ("oversample", C.c_int32), ("smooth_steps", C.c_int32),
                 ("alpha", C.c_double), ("tol", C.c_double), ("tol_relative", C.c_int32),
-                ("restart", C.c_int32), ("max_iter", C.c_int32), ("local_prec", C.c_int32)]
+                ("restart", C.c_int32), ("max_iter", C.c_int32), ("local_prec", C.c_int32),
+                ("smooth_kind", C.c_int32)]
 
 
 class mrcm_result(C.Structure):
@@ -108,6 +110,7 @@ def make_params(params):
     q.restart = int(params.restart)
     q.max_iter = int(params.max_iter)
     q.local_prec = int(params.local_prec)
+    q.smooth_kind = int(getattr(params, "smooth_kind", 0))
     return q
 
 

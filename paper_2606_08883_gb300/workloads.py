@@ -48,6 +48,7 @@ class Params:
     restart: int = 30
     max_iter: int = 500
     local_prec: int = PREC_FP64
+    smooth_kind: int = 0          # 0 additive, 1 multiplicative multicolour Schwarz sweeps
 
 
 # ---------------------------------------------------------------------------------------------

@@ -49,7 +49,8 @@ def test_plan_export_matches_oracle_bit_exactly(lib, n, sub, l):
 
 
 @pytest.mark.parametrize("bad", [dict(sub=(5, 8, 1)), dict(oversample=8), dict(oversample=-1), dict(alpha=0.0),
-                                 dict(tol=-1.0), dict(restart=0), dict(max_iter=0), dict(local_prec=7)])
+                                 dict(tol=-1.0), dict(restart=0), dict(max_iter=0), dict(local_prec=7),
+                                 dict(smooth_kind=2)])
 def test_invalid_parameters_rejected(lib, bad):
     prob = W.random_problem((24, 16, 1), seed=0)
     kw = dict(sub=(8, 8, 1), oversample=2)

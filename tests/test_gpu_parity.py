@@ -132,6 +132,39 @@ def test_apply_precond_matches_oracle(mrcm, name):
         assert _rel(z, parts["z"]) < 1e-10, (name, trial, _rel(z, parts["z"]))
 
 
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "dirichlet-all"])
+def test_multiplicative_smoothing_matches_oracle(mrcm, name):
+    # the multicolour sweep: one launch per colour over that colour's boxes, z updated in place
+    prob, q = _case(name)
+    q.smooth_kind = 1
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    pre = MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha, 0, 1)
+    add = MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha, 0, 0)
+    rng = np.random.default_rng(31)
+    for trial in range(2):
+        r = rng.standard_normal(prob.K.shape)
+        z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+        ref = pre.apply(r)
+        assert _rel(z, ref) < 1e-10, (name, trial, _rel(z, ref))
+        assert _rel(add.apply(r), ref) > 1e-6  # the two sweeps really differ on this case
+    s.close()
+
+
+def test_multiplicative_smoothing_gmres_matches_oracle(mrcm):
+    prob, q = _case("os-96x64-l4s2")
+    q.smooth_kind, q.tol, q.restart = 1, 1e-9, 100
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve()
+    p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                      l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                      tol_relative=True, restart=q.restart, max_iter=q.max_iter, smooth_kind=1)
+    assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    s.close()
+
+
 # GMRES(8) where restarted GMRES converges for this operator (covers the restart path); a long
 # restart where it stagnates (A T has eigenvalues with negative real part once smoothing is on)
 @pytest.mark.parametrize("name,restart", [("os-96x64-l4s2", 8), ("mrcm-48x40", 8), ("dirichlet-all", 8),
