@@ -54,20 +54,34 @@ def face_area(h, a):
     return out
 
 
+def cell_shape(K):
+    """(nz, ny, nx) of a permeability given as a scalar field (nz, ny, nx) or as the diagonal of a
+    tensor, components stacked first (d, nz, ny, nx) in x, y, z order."""
+    return np.shape(K)[-3:]
+
+
+def k_axis(K, a):
+    """The permeability that acts across faces normal to axis a: the scalar field, or the a-th
+    diagonal component of the tensor."""
+    K = np.asarray(K, dtype=np.float64)
+    return K[a] if K.ndim == 4 else K
+
+
 def half_transmissibility(K, h, a):
-    """tau_{c,f} = 2 K_c |f| / h_a for the faces of every cell normal to axis a."""
-    return 2.0 * K * face_area(h, a) / h[a]
+    """tau_{c,f} = 2 K_c |f| / h_a for the faces of every cell normal to axis a (K_c the component
+    along a for a diagonal tensor)."""
+    return 2.0 * k_axis(K, a) * face_area(h, a) / h[a]
 
 
 def transmissibilities(K, h, dim, bc_kind):
     """Face transmissibilities [Tx, Ty, Tz]; axes at or beyond ``dim`` carry no flow (all zero)."""
     T = []
     for a in range(3):
-        shape = list(K.shape)
+        shape = list(cell_shape(K))
         shape[np_axis(a)] += 1
         Ta = np.zeros(shape)
         if a < dim:
-            n_a = K.shape[np_axis(a)]
+            n_a = cell_shape(K)[np_axis(a)]
             tau = half_transmissibility(K, h, a)
             if n_a > 1:
                 t_lo = take(tau, a, slice(0, n_a - 1))
@@ -88,9 +102,9 @@ def rhs(K, h, dim, bc_kind, bc_val=None, f=None):
     side: (nz, ny) for +-x, (nz, nx) for +-y, (ny, nx) for +-z.  Dirichlet data is the face
     pressure g, Neumann data the outward normal velocity z.
     """
-    b = np.zeros_like(K) if f is None else np.array(f, dtype=np.float64, copy=True)
+    b = np.zeros(cell_shape(K)) if f is None else np.array(f, dtype=np.float64, copy=True)
     for a in range(dim):
-        n_a = K.shape[np_axis(a)]
+        n_a = cell_shape(K)[np_axis(a)]
         tau = half_transmissibility(K, h, a)
         for d, cell in ((0, 0), (1, n_a - 1)):
             side = 2 * a + d

@@ -23,14 +23,15 @@ local solution including the Robin boundary fluxes (tests/test_oracle_local.py).
 import numpy as np
 import scipy.linalg as sla
 
-from .grid import face_area, np_axis
+from .grid import face_area, k_axis, np_axis
 
 
 def robin_face(K, h, a, inside, outside, alpha, sub):
     """(tau_in, beta, t_R, |f|) of the face between cell ``inside`` and cell ``outside`` (x,y,z)."""
     area = face_area(h, a)
-    k_in = K[inside[2], inside[1], inside[0]]
-    k_out = K[outside[2], outside[1], outside[0]]
+    Ka = k_axis(K, a)  # the component across the face for a diagonal tensor
+    k_in = Ka[inside[2], inside[1], inside[0]]
+    k_out = Ka[outside[2], outside[1], outside[0]]
     tau = 2.0 * k_in * area / h[a]
     k_h = 2.0 * k_in * k_out / (k_in + k_out)
     beta = alpha * (sub[a] * h[a]) / k_h

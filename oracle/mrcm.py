@@ -43,7 +43,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .grid import transmissibilities, matvec
+from .grid import cell_shape, transmissibilities, matvec
 from .local import BoxOperator, robin_face
 from .partition import Partition
 
@@ -54,10 +54,10 @@ class _Sub:
 
 class MRCMOS:
     def __init__(self, K, h, dim, bc_kind, sub, l, smooth_steps, alpha, iface_degree=0, smooth_kind=0):
-        K = np.asarray(K, dtype=np.float64)
+        K = np.asarray(K, dtype=np.float64)  # scalar field, or diagonal tensor components stacked first
         self.K, self.h, self.dim = K, [float(v) for v in h], dim
-        self.shape = K.shape
-        n = [K.shape[2], K.shape[1], K.shape[0]]
+        self.shape = cell_shape(K)
+        n = [self.shape[2], self.shape[1], self.shape[0]]
         self.n = n
         self.sub = [int(v) for v in sub]
         self.l = int(l)

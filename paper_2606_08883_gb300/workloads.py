@@ -191,12 +191,14 @@ def lognormal(N=2048, seed=1, variance=4.0, corr=0.05, sub=32, oversample=2, smo
     return prob, params
 
 
-def random_problem(n, dim=2, seed=0, contrast=10.0, bc_kind=None, source=True, dirichlet_data=True):
-    """Small random test problem: K = contrast ** U(0, 1) per cell, random boundary data and source."""
+def random_problem(n, dim=2, seed=0, contrast=10.0, bc_kind=None, source=True, dirichlet_data=True, tensor=False):
+    """Small random test problem: K = contrast ** U(0, 1) per cell, random boundary data and source.
+    tensor=True: a diagonal tensor, each of its dim components drawn independently (stacked first,
+    x, y, z order)."""
     rng = np.random.default_rng(seed)
     nx, ny, nz = n
     shape = (nz, ny, nx)
-    K = contrast ** rng.uniform(0.0, 1.0, size=shape)
+    K = contrast ** rng.uniform(0.0, 1.0, size=((dim,) + shape) if tensor else shape)
     h = (1.0 / nx, 1.0 / ny, 1.0 / nz if dim == 3 else 1.0)
     if bc_kind is None:
         bc_kind = [DIRICHLET, DIRICHLET, NEUMANN, NEUMANN, NEUMANN, NEUMANN]

@@ -107,10 +107,26 @@ def test_superposition_equals_monolithic_dense_solve(l, degree, dim):
     assert np.linalg.norm(parts["c"] - c_ref) <= 1e-9 * np.linalg.norm(c_ref)
 
 
-def test_mass_balance_and_weak_continuity():
-    prob = W.random_problem((16, 12, 1), seed=8, contrast=1e4)
+@pytest.mark.parametrize("l", [0, 2])
+def test_diagonal_tensor_superposition_and_single_subdomain(l):
+    # anisotropic K: the superposition still equals the monolithic coupled solve, and one subdomain
+    # still gives T = A^-1 for the tensor operator
+    prob = W.random_problem((12, 12, 1), seed=31, contrast=1e3, tensor=True)
+    pre = _pre(prob, (4, 4, 1), l, 0)
+    r = np.random.default_rng(32).standard_normal(pre.shape)
+    parts = pre.apply_parts(r)
+    z_ref, c_ref = _monolithic(pre, r)
+    assert np.linalg.norm(parts["z_mrcm"] - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
+    one = _pre(prob, (12, 12, 1), 0, 1)
+    ref = np.linalg.solve(_dense_A(one), r.ravel()).reshape(r.shape)
+    assert np.linalg.norm(one.apply(r) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("tensor", [False, True])
+def test_mass_balance_and_weak_continuity(tensor):
+    prob = W.random_problem((16, 12, 1), seed=8, contrast=1e4, tensor=tensor)
     pre = _pre(prob, (4, 4, 1), 2, 0)
-    r = np.random.default_rng(9).standard_normal(prob.K.shape)
+    r = np.random.default_rng(9).standard_normal(pre.shape)
     parts = pre.apply_parts(r)
     z, c = parts["z_mrcm"], parts["c"]
     P = pre.part
