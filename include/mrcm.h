@@ -68,6 +68,11 @@ typedef struct mrcm_problem {
                                laid out like the layer of cells touching the side (x fastest among
                                the remaining axes): Dirichlet pressure g or outward velocity z */
   const double* f;          /* device, cell-integrated source per cell, or NULL for zero */
+  const double* K_y;        /* device, or NULL: the y component of a diagonal permeability tensor,
+                               K then being its x component; each face uses the component along its
+                               normal (transmissibilities, Robin tau and the K_H of beta).  NULL: K
+                               is a scalar field acting on every axis */
+  const double* K_z;        /* device, or NULL: the z component (3-D; not used by the 2-D GPU path) */
 } mrcm_problem;
 
 /* Method and solver parameters (Table 1 notation: oversampling l*h, k smoothing steps). */
@@ -149,8 +154,8 @@ mrcm_status mrcm_rhs(mrcm_handle h, double* b, void* stream);
 mrcm_status mrcm_gmres_solve(mrcm_handle h, const double* b, double* p, double* ux, double* uy,
                              double* uz, mrcm_result* result, void* stream);
 
-/* End-to-end solve from host memory: copy K_host (n cells; NULL keeps the resident field) to the
- * device, run mrcm_factor_local and mrcm_gmres_solve from p0 = 0, copy p back to p_host (n
+/* End-to-end solve from host memory: copy K_host (n cells; NULL keeps the resident field; on a
+ * problem created with K_y it replaces the x component only) to the device, run mrcm_factor_local and mrcm_gmres_solve from p0 = 0, copy p back to p_host (n
  * doubles).  Use pinned host memory for asynchronous copies. */
 mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host, mrcm_result* result,
                             void* stream);
@@ -216,7 +221,7 @@ typedef struct mrcm_server* mrcm_server_handle;
 /* max_inflight in 1..64.  The current device at creation is the server's device. */
 mrcm_status mrcm_server_create(void* arena, size_t arena_bytes, int32_t max_inflight, mrcm_server_handle* out);
 
-/* Queue a solve.  problem->K, bc_val[] and f are HOST pointers here; they are copied before the
+/* Queue a solve.  problem->K, K_y, bc_val[] and f are HOST pointers here; they are copied before the
  * call returns.  Returns MRCM_ERR_OOM if the request could never fit in the arena, and the
  * validation errors of mrcm_footprint().  *ticket identifies the request. */
 mrcm_status mrcm_submit(mrcm_server_handle s, const mrcm_problem* problem, const mrcm_params* params, uint64_t* ticket);

@@ -107,6 +107,7 @@ Geo geo(mrcm_handle h) {
   g.hz = h->h[2];
   g.alpha = h->prm.alpha;
   g.K = at<double>(h, h->lay.K);
+  g.Ky = at<double>(h, h->lay.Ky);
   g.Tx = at<double>(h, h->lay.Tx);
   g.Ty = at<double>(h, h->lay.Ty);
   return g;
@@ -143,6 +144,8 @@ mrcm_status copy_problem(mrcm_handle h, const mrcm_problem* p, cudaStream_t st) 
   const size_t n = ncell(h);
   if (!p->K) return fail(h, MRCM_ERR_INVALID_ARG, "problem->K is null");
   CK(h, cudaMemcpyAsync(at<double>(h, h->lay.K), p->K, 8 * n, cudaMemcpyDeviceToDevice, st));
+  h->iso = p->K_y == nullptr;
+  CK(h, cudaMemcpyAsync(at<double>(h, h->lay.Ky), h->iso ? p->K : p->K_y, 8 * n, cudaMemcpyDeviceToDevice, st));
   h->has_f = p->f != nullptr;
   if (p->f) CK(h, cudaMemcpyAsync(at<double>(h, h->lay.f), p->f, 8 * n, cudaMemcpyDeviceToDevice, st));
   const size_t len = std::max(h->n[0], h->n[1]);
@@ -292,6 +295,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   CK(h, cudaMemsetAsync(flags, 0, 4 * 64, st));
   const size_t n = ncell(h);
   k_check_positive<<<256, 256, 0, st>>>(at<double>(h, L.K), n, flags);
+  k_check_positive<<<256, 256, 0, st>>>(at<double>(h, L.Ky), n, flags);
   CK(h, cudaGetLastError());
   Geo g = geo(h);
   const double* bcp[4];
@@ -586,7 +590,10 @@ mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host,
   if (!h || !p_host || !result) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = ncell(h);
-  if (K_host) CK(h, cudaMemcpyAsync(at<double>(h, h->lay.K), K_host, 8 * n, cudaMemcpyHostToDevice, st));
+  if (K_host) {
+    CK(h, cudaMemcpyAsync(at<double>(h, h->lay.K), K_host, 8 * n, cudaMemcpyHostToDevice, st));
+    if (h->iso) CK(h, cudaMemcpyAsync(at<double>(h, h->lay.Ky), K_host, 8 * n, cudaMemcpyHostToDevice, st));
+  }
   mrcm_status rc = mrcm_factor_local(h, stream);
   if (rc != MRCM_OK) return rc;
   double* p = at<double>(h, h->lay.tmpv);

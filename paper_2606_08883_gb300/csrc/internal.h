@@ -45,7 +45,7 @@ std::vector<int32_t> export_plan(const Plan& plan);
 // Workspace layout (byte offsets, 256-byte aligned).
 // ------------------------------------------------------------------------------------------
 struct Layout {
-  size_t K, Tx, Ty, b, f, bcv;            // problem data (bcv: 4 side arrays in 2-D)
+  size_t K, Ky, Tx, Ty, b, f, bcv;        // problem data (Ky: y component of K; bcv: 4 side arrays)
   size_t Linv_loc, Linv_ohat_r, Linv_ohat_d;   // line-block inverse factors
   size_t phi, psi, mom, psi0, z0, mom0;   // informed spaces, basis, side moments, apply scratch
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
@@ -89,7 +89,8 @@ struct Geo {
   int smax;
   double hx, hy, hz;
   double alpha;
-  const double* K;
+  const double* K;         // scalar permeability, or the x component of a diagonal tensor
+  const double* Ky;        // the y component (equal to K for a scalar field)
   const double* Tx;        // ny x (nx+1)
   const double* Ty;        // (ny+1) x nx
 };
@@ -121,6 +122,7 @@ struct mrcm_ctx {
   int bc_kind[6];
   int has_bc[6];
   int has_f;
+  bool iso = true;    // K is a scalar field (Ky mirrors it)
   char* ws;           // workspace base (device)
   size_t ws_bytes;
   bool factored = false;

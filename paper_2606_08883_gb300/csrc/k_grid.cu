@@ -35,12 +35,12 @@ __global__ void k_trans_y(Geo g, BcDev bc, double* Ty) {
   const double area = g.hx * g.hz;
   double t;
   if (j == 0) {
-    t = bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(g.K[i], area, g.hy) : 0.0;
+    t = bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(g.Ky[i], area, g.hy) : 0.0;
   } else if (j == g.ny) {
-    t = bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(g.K[(size_t)(g.ny - 1) * g.nx + i], area, g.hy) : 0.0;
+    t = bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(g.Ky[(size_t)(g.ny - 1) * g.nx + i], area, g.hy) : 0.0;
   } else {
-    const double tl = half_trans(g.K[(size_t)(j - 1) * g.nx + i], area, g.hy);
-    const double tr = half_trans(g.K[(size_t)j * g.nx + i], area, g.hy);
+    const double tl = half_trans(g.Ky[(size_t)(j - 1) * g.nx + i], area, g.hy);
+    const double tr = half_trans(g.Ky[(size_t)j * g.nx + i], area, g.hy);
     t = 1.0 / (1.0 / tl + 1.0 / tr);
   }
   Ty[(size_t)j * g.nx + i] = t;
@@ -53,13 +53,13 @@ __global__ void k_rhs(Geo g, BcDev bc, const double* f, double* b) {
   if (i >= g.nx || j >= g.ny) return;
   const size_t c = (size_t)j * g.nx + i;
   double v = f ? f[c] : 0.0;
-  const double k = g.K[c];
+  const double k = g.K[c], ky = g.Ky[c];  // components across x faces and across y faces
   const double ax = g.hy * g.hz, ay = g.hx * g.hz;
   // same side order as the oracle: x sides, then y sides
   if (i == 0 && bc.val[0]) v += bc.kind[0] == MRCM_BC_DIRICHLET ? half_trans(k, ax, g.hx) * bc.val[0][j] : -(ax * bc.val[0][j]);
   if (i == g.nx - 1 && bc.val[1]) v += bc.kind[1] == MRCM_BC_DIRICHLET ? half_trans(k, ax, g.hx) * bc.val[1][j] : -(ax * bc.val[1][j]);
-  if (j == 0 && bc.val[2]) v += bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(k, ay, g.hy) * bc.val[2][i] : -(ay * bc.val[2][i]);
-  if (j == g.ny - 1 && bc.val[3]) v += bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(k, ay, g.hy) * bc.val[3][i] : -(ay * bc.val[3][i]);
+  if (j == 0 && bc.val[2]) v += bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(ky, ay, g.hy) * bc.val[2][i] : -(ay * bc.val[2][i]);
+  if (j == g.ny - 1 && bc.val[3]) v += bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(ky, ay, g.hy) * bc.val[3][i] : -(ay * bc.val[3][i]);
   b[c] = v;
 }
 

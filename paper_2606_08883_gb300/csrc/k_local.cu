@@ -46,7 +46,10 @@ __device__ __forceinline__ bool active(const Geo& g, int gx, int gy) {
   return gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
 }
 
-__device__ __forceinline__ double Kc(const Geo& g, int gx, int gy) { return g.K[(size_t)gy * g.nx + gx]; }
+// permeability across faces normal to axis a (the tensor component along a)
+__device__ __forceinline__ double Kc(const Geo& g, int a, int gx, int gy) {
+  return (a == 0 ? g.K : g.Ky)[(size_t)gy * g.nx + gx];
+}
 
 // Robin coefficient t_R of the face between (gx, gy) inside and its neighbour along axis a / dir.
 __device__ __forceinline__ double face_tr(const Geo& g, int gx, int gy, int a, int dir, double* beta, double* tau) {
@@ -54,7 +57,7 @@ __device__ __forceinline__ double face_tr(const Geo& g, int gx, int gy, int a, i
   const double area = a == 0 ? g.hy * g.hz : g.hx * g.hz;
   const double ha = a == 0 ? g.hx : g.hy;
   const double Hs = a == 0 ? g.sx * g.hx : g.sy * g.hy;
-  return robin_tr(Kc(g, gx, gy), Kc(g, nx2, ny2), area, ha, Hs, g.alpha, beta, tau);
+  return robin_tr(Kc(g, a, gx, gy), Kc(g, a, nx2, ny2), area, ha, Hs, g.alpha, beta, tau);
 }
 
 // Line-block coefficients at local (x, J): diagonal, coupling to x+1 (value T, entry -T),

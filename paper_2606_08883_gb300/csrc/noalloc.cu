@@ -115,6 +115,7 @@ extern "C" mrcm_status mrcm_residual_norm_noalloc(mrcm_handle h, const double* b
   g.hz = h->h[2];
   g.alpha = h->prm.alpha;
   g.K = reinterpret_cast<const double*>(h->ws + h->lay.K);
+  g.Ky = reinterpret_cast<const double*>(h->ws + h->lay.Ky);
   g.Tx = reinterpret_cast<const double*>(h->ws + h->lay.Tx);
   g.Ty = reinterpret_cast<const double*>(h->ws + h->lay.Ty);
   const size_t want = (n + mrcm::RED_THREADS - 1) / mrcm::RED_THREADS;

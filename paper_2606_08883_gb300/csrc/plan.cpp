@@ -183,6 +183,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
     return at;
   };
   L.K = take(8 * n);
+  L.Ky = take(8 * n);
   L.Tx = take(8 * (nx + 1) * ny);
   L.Ty = take(8 * nx * (ny + 1));
   L.b = take(8 * n);

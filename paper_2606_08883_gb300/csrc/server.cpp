@@ -82,7 +82,7 @@ struct Request {
   mrcm_problem prob{};
   mrcm_params prm{};
   size_t n = 0, footprint = 0, block = 0, off = 0;
-  std::vector<double> K, f, p, hist;
+  std::vector<double> K, Ky, f, p, hist;
   std::vector<double> bc[6];
   int state = QUEUED;
   int skipped = 0;
@@ -129,6 +129,8 @@ void run_request(mrcm_server* S, Request* r, cudaStream_t st) {
   double* p = reinterpret_cast<double*>(base + o);
   o = align256(o + 8 * n);
   double* bcv = reinterpret_cast<double*>(base + o);
+  o = align256(o + 8 * 4 * len);
+  double* Ky = reinterpret_cast<double*>(base + o);  // only when the request has a tensor
   mrcm_problem dp = r->prob;
   auto set_err = [&](mrcm_status s, const char* what) {
     r->status = s;
@@ -136,6 +138,9 @@ void run_request(mrcm_server* S, Request* r, cudaStream_t st) {
   };
   cudaError_t e = cudaMemcpyAsync(K, r->K.data(), 8 * n, cudaMemcpyHostToDevice, st);
   dp.K = K;
+  if (e == cudaSuccess && !r->Ky.empty()) e = cudaMemcpyAsync(Ky, r->Ky.data(), 8 * n, cudaMemcpyHostToDevice, st);
+  dp.K_y = r->Ky.empty() ? nullptr : Ky;
+  dp.K_z = nullptr;
   if (e == cudaSuccess && !r->f.empty()) e = cudaMemcpyAsync(f, r->f.data(), 8 * n, cudaMemcpyHostToDevice, st);
   dp.f = r->f.empty() ? nullptr : f;
   for (int s = 0; s < 6 && e == cudaSuccess; ++s) {
@@ -283,9 +288,10 @@ mrcm_status mrcm_submit(mrcm_server_handle S, const mrcm_problem* problem, const
   r->n = (size_t)problem->n[0] * problem->n[1] * problem->n[2];
   r->footprint = fp;
   const size_t len = (size_t)std::max(problem->n[0], problem->n[1]);
-  r->block = align256(fp) + 3 * align256(8 * r->n) + align256(8 * 4 * len);
+  r->block = align256(fp) + 3 * align256(8 * r->n) + align256(8 * 4 * len) + (problem->K_y ? align256(8 * r->n) : 0);
   if (r->block > S->arena->size()) return MRCM_ERR_OOM;
   r->K.assign(problem->K, problem->K + r->n);
+  if (problem->K_y) r->Ky.assign(problem->K_y, problem->K_y + r->n);
   if (problem->f) r->f.assign(problem->f, problem->f + r->n);
   for (int side = 0; side < 4; ++side)
     if (problem->bc_val[side]) {

@@ -30,7 +30,8 @@ MRCM_DBG_TRANS, MRCM_DBG_PHI, MRCM_DBG_PSI, MRCM_DBG_MOMENTS, MRCM_DBG_G, MRCM_D
 
 class mrcm_problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int32 * 3), ("h", C.c_double * 3), ("K", C.c_void_p),
-                ("bc_kind", C.c_int32 * 6), ("bc_val", C.c_void_p * 6), ("f", C.c_void_p)]
+                ("bc_kind", C.c_int32 * 6), ("bc_val", C.c_void_p * 6), ("f", C.c_void_p),
+                ("K_y", C.c_void_p), ("K_z", C.c_void_p)]
 
 
 class mrcm_params(C.Structure):
@@ -114,7 +115,7 @@ def make_params(params):
     return q
 
 
-def make_problem(problem, K_ptr=0, bc_ptrs=None, f_ptr=0):
+def make_problem(problem, K_ptr=0, bc_ptrs=None, f_ptr=0, Ky_ptr=0):
     p = mrcm_problem()
     p.dim = int(problem.dim)
     p.n[:] = [int(v) for v in problem.n]
@@ -125,6 +126,8 @@ def make_problem(problem, K_ptr=0, bc_ptrs=None, f_ptr=0):
     for s in range(6):
         p.bc_val[s] = ptrs[s] or None
     p.f = f_ptr or None
+    p.K_y = Ky_ptr or None
+    p.K_z = None
     return p
 
 
@@ -173,13 +176,16 @@ class Solver:
 
     def _upload(self, problem):
         t = self.torch
-        self.K = t.as_tensor(np.ascontiguousarray(problem.K, dtype=np.float64).ravel(), device=self.device)
+        K = np.asarray(problem.K, dtype=np.float64)  # scalar field, or diagonal tensor components stacked first
+        self.K = t.as_tensor(np.ascontiguousarray(K[0] if K.ndim == 4 else K).ravel(), device=self.device)
+        self.Ky = t.as_tensor(np.ascontiguousarray(K[1]).ravel(), device=self.device) if K.ndim == 4 else None
         self.bc = [None if v is None else t.as_tensor(np.ascontiguousarray(v, dtype=np.float64).ravel(),
                                                       device=self.device) for v in problem.bc_val]
         self.f = None if problem.f is None else t.as_tensor(np.ascontiguousarray(problem.f, dtype=np.float64).ravel(),
                                                              device=self.device)
         self.p = make_problem(problem, self.K.data_ptr(), [0 if v is None else v.data_ptr() for v in self.bc],
-                              0 if self.f is None else self.f.data_ptr())
+                              0 if self.f is None else self.f.data_ptr(),
+                              0 if self.Ky is None else self.Ky.data_ptr())
 
     def update(self, problem):
         self._upload(problem)
@@ -287,11 +293,13 @@ class Server:
 
     def submit(self, problem, params):
         """Queue a solve of a ``workloads.Problem`` (host numpy data); returns the ticket."""
-        K = np.ascontiguousarray(problem.K, dtype=np.float64).ravel()
+        Kall = np.asarray(problem.K, dtype=np.float64)
+        K = np.ascontiguousarray(Kall[0] if Kall.ndim == 4 else Kall).ravel()
+        Ky = np.ascontiguousarray(Kall[1]).ravel() if Kall.ndim == 4 else None
         bcs = [None if v is None else np.ascontiguousarray(v, dtype=np.float64).ravel() for v in problem.bc_val]
         f = None if problem.f is None else np.ascontiguousarray(problem.f, dtype=np.float64).ravel()
         p = make_problem(problem, K.ctypes.data, [0 if v is None else v.ctypes.data for v in bcs],
-                         0 if f is None else f.ctypes.data)
+                         0 if f is None else f.ctypes.data, 0 if Ky is None else Ky.ctypes.data)
         q = make_params(params)
         t = C.c_uint64()
         _check(mrcm_submit(self.handle, C.byref(p), C.byref(q), C.byref(t)))
