@@ -2,11 +2,14 @@
 
 Integer work, compared bit-exactly with the CUDA library's host planner.
 
-* Omega_s: box of ``sub`` cells per axis; s = I + m0 (J + m1 K) with m_a = n_a / sub_a.
+* Omega_s: box of ``sub`` cells per axis; s = I + m0 (J + m1 K) with m_a = ceil(n_a / sub_a).
+  When sub_a does not divide n_a the last subdomain along axis a takes the remainder
+  n_a - (m_a - 1) sub_a (a reading: the paper's grids are divisible).
 * hat-Omega_s (oversampled region): Omega_s grown by l cells per side, clipped to the domain.
 * Sides in the order -x, +x, -y, +y, -z, +z; a side is a Robin side (part of Gamma_s) iff it is
-  not on the domain boundary.  N_s = number of Robin sides.  Because 0 <= l < sub_a, the Robin
-  sides of hat-Omega_s are exactly those of Omega_s.
+  not on the domain boundary.  N_s = number of Robin sides.  Because l is below the size of every
+  subdomain along every axis that has interfaces, the Robin sides of hat-Omega_s are exactly
+  those of Omega_s.
 * Coarse unknowns c_{s,k}: index off_s + rank of side k among the Robin sides of s, where off_s is
   the exclusive prefix sum of N_s.
 * Interfaces Gamma_{s,s'}: x-normal first, ordered by the lower subdomain index (K, J, I
@@ -32,13 +35,13 @@ class Partition:
             raise ValueError("dim must be 2 or 3")
         if dim == 2 and (n[2] != 1 or sub[2] != 1):
             raise ValueError("2-D problems have n[2] == sub[2] == 1")
-        for a in range(3):
-            if sub[a] < 1 or n[a] % sub[a] != 0:
-                raise ValueError("subdomain size must divide the grid")
-        if l < 0 or any(l >= sub[a] for a in range(dim)):
-            raise ValueError("oversampling must satisfy 0 <= l < sub")
+        if any(sub[a] < 1 or n[a] < 1 for a in range(3)):
+            raise ValueError("grid and subdomain sizes must be positive")
+        m = [-(-n[a] // sub[a]) for a in range(3)]
+        last = [n[a] - (m[a] - 1) * sub[a] for a in range(3)]
+        if l < 0 or any(l >= sub[a] or (m[a] > 1 and l >= last[a]) for a in range(dim)):
+            raise ValueError("oversampling must satisfy 0 <= l < the size of every subdomain")
         self.dim, self.n, self.sub, self.l = dim, n, sub, int(l)
-        m = [n[a] // sub[a] for a in range(3)]
         self.m = m
         S = m[0] * m[1] * m[2]
         self.S = S
@@ -51,7 +54,7 @@ class Partition:
             self.coord[s] = idx
             for a in range(3):
                 lo = idx[a] * sub[a]
-                hi = lo + sub[a]
+                hi = min(lo + sub[a], n[a])
                 self.box[s, 0, a], self.box[s, 1, a] = lo, hi
                 if a < dim:
                     self.obox[s, 0, a] = max(lo - l, 0)

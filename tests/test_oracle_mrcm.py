@@ -91,15 +91,20 @@ def _monolithic(pre, r):
     return z, x[nz:]
 
 
-@pytest.mark.parametrize("l,degree,dim", [(0, 0, 2), (1, 0, 2), (2, 0, 2), (2, 1, 2), (1, 0, 3)])
-def test_superposition_equals_monolithic_dense_solve(l, degree, dim):
+# n2: the 2-D grid; (14, 11) is not divisible by the 4 x 4 subdomains (last sizes 2 and 3)
+@pytest.mark.parametrize("l,degree,dim,n2", [(0, 0, 2, (12, 12)), (1, 0, 2, (12, 12)), (2, 0, 2, (12, 12)),
+                                             (2, 1, 2, (12, 12)), (1, 0, 3, None), (0, 0, 2, (14, 11)),
+                                             (1, 0, 2, (14, 11)), (1, 1, 2, (14, 11))])
+def test_superposition_equals_monolithic_dense_solve(l, degree, dim, n2):
     if dim == 2:
-        prob = W.random_problem((12, 12, 1), seed=11, contrast=1e3)
+        prob = W.random_problem(n2 + (1,), seed=11, contrast=1e3)
         sub = (4, 4, 1)
     else:
         prob = W.random_problem((6, 6, 4), dim=3, seed=11, contrast=1e3, bc_kind=[0, 0, 1, 1, 1, 1])
         sub = (3, 3, 2)
     pre = _pre(prob, sub, l, 0, degree)
+    if dim == 2:
+        assert tuple(pre.part.m[:2]) == tuple(-(-v // 4) for v in n2)
     r = np.random.default_rng(3).standard_normal(prob.K.shape)
     parts = pre.apply_parts(r)
     z_ref, c_ref = _monolithic(pre, r)
@@ -122,9 +127,9 @@ def test_diagonal_tensor_superposition_and_single_subdomain(l):
     assert np.linalg.norm(one.apply(r) - ref) <= 1e-11 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("tensor", [False, True])
-def test_mass_balance_and_weak_continuity(tensor):
-    prob = W.random_problem((16, 12, 1), seed=8, contrast=1e4, tensor=tensor)
+@pytest.mark.parametrize("tensor,n", [(False, (16, 12, 1)), (True, (16, 12, 1)), (False, (19, 15, 1))])
+def test_mass_balance_and_weak_continuity(tensor, n):
+    prob = W.random_problem(n, seed=8, contrast=1e4, tensor=tensor)
     pre = _pre(prob, (4, 4, 1), 2, 0)
     r = np.random.default_rng(9).standard_normal(pre.shape)
     parts = pre.apply_parts(r)
@@ -151,12 +156,12 @@ def test_mass_balance_and_weak_continuity(tensor):
         assert abs(Pside[(s, 2 * a + 1)] - Pside[(s2, 2 * a)]) <= 1e-10 * pscale     # Eq. 14
 
 
-@pytest.mark.parametrize("l,smooth", [(0, 0), (1, 0), (2, 1), (3, 2)])
-def test_exact_on_fields_constant_along_interfaces(l, smooth):
+@pytest.mark.parametrize("l,smooth,nx", [(0, 0, 20), (1, 0, 20), (2, 1, 20), (3, 2, 20), (2, 1, 23)])
+def test_exact_on_fields_constant_along_interfaces(l, smooth, nx):
     # stripes along x spanning the whole y range; K and the target pressure depend on x only, so
     # the true Robin data is constant on every interface and lies in the P0 multiplier space
     rng = np.random.default_rng(21)
-    nx, ny = 20, 6
+    ny = 6
     kx = 10.0 ** rng.uniform(-2, 2, size=nx)
     prob = W.Problem(2, (nx, ny, 1), (1.0 / nx, 1.0 / ny, 1.0), np.tile(kx, (ny, 1))[None],
                      [0, 0, 1, 1, 1, 1])
@@ -177,13 +182,14 @@ def test_linearity():
     assert np.linalg.norm(lhs - rhs) <= 1e-11 * np.linalg.norm(rhs)
 
 
-def test_schwarz_sweep_matches_dense_restricted_additive_schwarz():
-    prob = W.random_problem((12, 10, 1), seed=14, contrast=1e3)
+@pytest.mark.parametrize("n", [(12, 10, 1), (15, 13, 1)])
+def test_schwarz_sweep_matches_dense_restricted_additive_schwarz(n):
+    prob = W.random_problem(n, seed=14, contrast=1e3)
     pre = _pre(prob, (4, 5, 1), 2, 1)
     A = _dense_A(pre)
     rng = np.random.default_rng(15)
     r, z = rng.standard_normal(prob.K.shape), rng.standard_normal(prob.K.shape)
-    n = pre.n
+    n = np.array(pre.n)
     rho = r.ravel() - A @ z.ravel()
     z_ref = z.ravel().copy()
     for s in range(pre.part.S):
@@ -217,12 +223,14 @@ def _colour_blocks(pre):
     return [out[c] for c in sorted(out)]
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_multiplicative_sweep_without_overlap_is_block_gauss_seidel(dim):
+@pytest.mark.parametrize("dim,ragged", [(2, False), (3, False), (2, True)])
+def test_multiplicative_sweep_without_overlap_is_block_gauss_seidel(dim, ragged):
     # l = 0: each colour's subdomains are pairwise uncoupled, so one multiplicative sweep is the
     # textbook block Gauss-Seidel step z + M^-1 (r - A z), M the block lower triangle of A in colour
     # order; the additive sweep is block Jacobi z + D^-1 (r - A z).
     n, sub = ((16, 12, 1), (4, 3, 1)) if dim == 2 else ((8, 6, 4), (2, 3, 2))
+    if ragged:
+        n = (17, 13, 1)
     prob = W.random_problem(n, dim=dim, seed=21, contrast=1e3)
     A = None
     for kind in (0, 1):
@@ -266,13 +274,14 @@ def test_multiplicative_sweep_fixed_point_and_energy_decrease():
     assert errs[-1] < 1e-3 * errs[0]
 
 
-@pytest.mark.parametrize("l,degree,dim", [(1, 0, 2), (3, 0, 2), (2, 1, 2), (1, 0, 3)])
-def test_basis_equals_restricted_oversampled_solution(l, degree, dim):
+@pytest.mark.parametrize("l,degree,dim,n2", [(1, 0, 2, (16, 12)), (3, 0, 2, (16, 12)), (2, 1, 2, (16, 12)),
+                                             (1, 0, 3, None), (1, 0, 2, (18, 14)), (1, 1, 2, (18, 14))])
+def test_basis_equals_restricted_oversampled_solution(l, degree, dim, n2):
     # Eq. 15 and the Robin condition: phi_s^k is the Robin trace of q^k on Gamma_s, so the local
     # Robin solve with data phi_s^k reproduces q^k on Omega_s exactly.
     from oracle.local import BoxOperator, robin_face
     if dim == 2:
-        prob = W.random_problem((16, 12, 1), seed=31, contrast=1e4)
+        prob = W.random_problem(n2 + (1,), seed=31, contrast=1e4)
         sub = (4, 4, 1)
     else:
         prob = W.random_problem((6, 6, 4), dim=3, seed=31, contrast=1e3, bc_kind=[0, 0, 1, 1, 1, 1])

@@ -14,6 +14,11 @@ CASES = [
     (2, (40, 24, 1), (8, 12, 1), 7),
     (3, (8, 6, 4), (4, 3, 2), 1),
     (3, (12, 12, 8), (4, 4, 4), 3),
+    # grids the subdomain size does not divide: the last subdomain along an axis is shorter
+    (2, (13, 9, 1), (4, 4, 1), 0),
+    (2, (14, 11, 1), (4, 3, 1), 1),
+    (2, (30, 7, 1), (8, 16, 1), 5),
+    (3, (10, 8, 6), (4, 3, 4), 1),
 ]
 
 
@@ -26,7 +31,12 @@ def test_partition_invariants(dim, n, sub, l):
         sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         assert (owner[sl] == -1).all()
         owner[sl] = s
-        assert tuple(hi - lo) == tuple(sub)
+        # full size, except the last subdomain along an axis, which ends on the grid boundary
+        for a in range(3):
+            assert lo[a] == P.coord[s, a] * sub[a]
+            assert hi[a] - lo[a] == (sub[a] if lo[a] + sub[a] <= n[a] else n[a] - lo[a])
+            assert a >= dim or P.m[a] == 1 or hi[a] - lo[a] > l
+            assert (hi[a] == n[a]) == (P.coord[s, a] == P.m[a] - 1)
         olo, ohi = P.obox[s, 0], P.obox[s, 1]
         for a in range(3):
             assert 0 <= olo[a] <= lo[a] and hi[a] <= ohi[a] <= n[a]
@@ -83,7 +93,8 @@ def test_face_order_and_export_header():
     assert P.face_id(1, (3, 4, 0)) == 9 * 8 + 3 + 8 * 4
 
 
-@pytest.mark.parametrize("bad", [((12, 8, 1), (5, 4, 1), 1), ((12, 8, 1), (4, 4, 1), 4), ((12, 8, 1), (4, 4, 1), -1)])
+@pytest.mark.parametrize("bad", [((13, 8, 1), (4, 4, 1), 1), ((12, 8, 1), (4, 4, 1), 4), ((12, 8, 1), (4, 4, 1), -1),
+                                 ((12, 8, 1), (0, 4, 1), 0), ((14, 8, 1), (5, 4, 1), 4)])
 def test_invalid_partition_rejected(bad):
     n, sub, l = bad
     with pytest.raises(ValueError):
