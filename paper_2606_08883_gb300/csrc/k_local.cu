@@ -46,6 +46,14 @@ __device__ __forceinline__ bool active(const Geo& g, int gx, int gy) {
   return gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
 }
 
+// Cells of subdomain s along x and along y: the subdomain size, except for the last subdomain of a
+// row or column of a grid that the size does not divide, which takes the remainder.  Its box keeps
+// the full padded shape; the cells past the grid are identity rows.
+__device__ __forceinline__ int sub_w(const Geo& g, int s) { return min(g.sx, g.nx - (s % g.mx) * g.sx); }
+__device__ __forceinline__ int sub_h(const Geo& g, int s) { return min(g.sy, g.ny - (s / g.mx) * g.sy); }
+// faces on side k (-x, +x, -y, +y) of Omega_s
+__device__ __forceinline__ int side_len(const Geo& g, int s, int k) { return k < 2 ? sub_h(g, s) : sub_w(g, s); }
+
 // permeability across faces normal to axis a (the tensor component along a)
 __device__ __forceinline__ double Kc(const Geo& g, int a, int gx, int gy) {
   return (a == 0 ? g.K : g.Ky)[(size_t)gy * g.nx + gx];
@@ -380,7 +388,9 @@ __device__ __forceinline__ int colour_box(const Geo& g, int colour, int b) {
   return J * g.mx + I;
 }
 
-// Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.
+// Gamma face t of side k of Omega_s: inside cell (global) and face transmissibility T_f.  A +x or
+// +y side is a Robin side only when the subdomain is not the last along that axis, so it has the
+// full subdomain size there.
 __device__ __forceinline__ void gamma_face(const Geo& g, int s, int k, int t, int& gx, int& gy, int& ox2, int& oy2,
                                            double& Tf) {
   const int I = s % g.mx, J = s / g.mx;
@@ -628,7 +638,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   } else {  // MODE_BASIS: t_R phi^r on the Gamma faces of each Robin side
     for (int k = 0; k < 4; ++k) {
       if (!robin_side(g, s, k)) continue;
-      const int len = (k < 2) ? g.sy : g.sx;
+      const int len = side_len(g, s, k);
       for (int t = tid; t < len; t += nt) {
         int gx, gy, ox2, oy2;
         double Tf;
@@ -740,12 +750,12 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   if (MODE == MODE_PARTICULAR) {
     for (int k = tid; k < hgt * w; k += nt) {
       const int J = k / w, x = k % w;
-      a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+      if (active(g, b.ox + x, b.oy + J)) a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
     for (int kside = wid; kside < 4; kside += nw) {
       double F = 0.0, Pw = 0.0;
       if (robin_side(g, s, kside)) {
-        const int len = (kside < 2) ? g.sy : g.sx;
+        const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
           int gx, gy, ox2, oy2;
           double Tf, beta;
@@ -764,8 +774,9 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       }
     }
   } else if (MODE == MODE_SCHWARZ) {
-    for (int k = tid; k < g.sx * g.sy; k += nt) {
-      const int y = k / g.sx, x = k % g.sx;
+    const int ws = sub_w(g, s), hs = sub_h(g, s);
+    for (int k = tid; k < ws * hs; k += nt) {
+      const int y = k / ws, x = k % ws;
       const int gx = b.ox + g.l + x, gy = b.oy + g.l + y;
       const size_t c = (size_t)gy * g.nx + gx;
       a.out[c] = a.zin[c] + (double)Y[(g.l + y) * w + g.l + x];
@@ -773,14 +784,15 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   } else if (MODE == MODE_BASIS) {
     for (int k = tid; k < hgt * w * NR; k += nt) {
       const int r = k % NR, c = k / NR, J = c / w, x = c % w;
-      a.out[(size_t)r * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+      if (active(g, b.ox + x, b.oy + J))
+        a.out[(size_t)r * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
     // moments: 16 (side, function) pairs, one warp each
     for (int pr = wid; pr < 16; pr += nw) {
       const int kside = pr / 4, r = pr % 4;
       double F = 0.0, Pw = 0.0;
       if (robin_side(g, s, kside)) {
-        const int len = (kside < 2) ? g.sy : g.sx;
+        const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
           int gx, gy, ox2, oy2;
           double Tf, beta;
@@ -802,7 +814,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
     }
   } else {  // MODE_INFORMED: phi_s^r on every Gamma face
     for (int k = 0; k < 4; ++k) {
-      const int len = (k < 2) ? g.sy : g.sx;
+      const int len = side_len(g, s, k);
       const bool rs = robin_side(g, s, k);
       for (int t = tid; t < len * NR; t += nt) {
         const int r = t % NR, f = t / NR;
@@ -882,7 +894,7 @@ __global__ void k_phi_indicator(Geo g, double* phi) {
   const int s = blockIdx.x;
   for (int t = threadIdx.x; t < 16 * g.smax; t += blockDim.x) {
     const int r = t / (4 * g.smax), k = (t / g.smax) % 4, f = t % g.smax;
-    const int len = (k < 2) ? g.sy : g.sx;
+    const int len = side_len(g, s, k);
     double v = 0.0;
     if (r == k && f < len && robin_side(g, s, k)) v = 1.0;
     phi[(size_t)s * 16 * g.smax + t] = v;

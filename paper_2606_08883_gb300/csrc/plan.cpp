@@ -16,12 +16,17 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   for (int a = 0; a < 3; ++a) {
     if (p.n[a] < 1) return "grid sizes must be >= 1";
     if (!finite_pos(p.h[a])) return "cell sizes must be positive and finite";
-    if (q.sub[a] < 1 || p.n[a] % q.sub[a] != 0) return "subdomain size must divide the grid on every axis";
+    if (q.sub[a] < 1) return "subdomain sizes must be >= 1";
   }
   if (p.dim == 2 && (p.n[2] != 1 || q.sub[2] != 1)) return "2-D problems need n[2] == 1 and sub[2] == 1";
   if ((long long)p.n[0] * p.n[1] * p.n[2] > (1LL << 31) - 1) return "grid too large";
-  for (int a = 0; a < p.dim; ++a)
-    if (q.oversample < 0 || q.oversample >= q.sub[a]) return "oversampling must satisfy 0 <= l < sub on every axis";
+  // the last subdomain along an axis takes the remainder when sub does not divide the grid; the
+  // oversampling stays below the size of every subdomain so hat-Omega keeps the Robin sides of Omega
+  for (int a = 0; a < p.dim; ++a) {
+    const int m = (p.n[a] + q.sub[a] - 1) / q.sub[a], last = p.n[a] - (m - 1) * q.sub[a];
+    if (q.oversample < 0 || q.oversample >= q.sub[a] || (m > 1 && q.oversample >= last))
+      return "oversampling must satisfy 0 <= l < the size of every subdomain on every axis";
+  }
   if (q.oversample < 0) return "oversampling must be >= 0";
   if (q.smooth_steps < 0) return "smooth_steps must be >= 0";
   if (!finite_pos(q.alpha)) return "alpha must be positive and finite";
@@ -43,7 +48,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   for (int a = 0; a < 3; ++a) {
     P.n[a] = p.n[a];
     P.sub[a] = q.sub[a];
-    P.m[a] = p.n[a] / q.sub[a];
+    P.m[a] = (p.n[a] + q.sub[a] - 1) / q.sub[a];
   }
   P.l = q.oversample;
   P.S = P.m[0] * P.m[1] * P.m[2];
@@ -59,7 +64,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
     const int idx[3] = {s % P.m[0], (s / P.m[0]) % P.m[1], s / (P.m[0] * P.m[1])};
     for (int a = 0; a < 3; ++a) {
       coord[3 * s + a] = idx[a];
-      const int lo = idx[a] * P.sub[a], hi = lo + P.sub[a];
+      const int lo = idx[a] * P.sub[a], hi = std::min(lo + P.sub[a], P.n[a]);
       P.box[6 * s + a] = lo;
       P.box[6 * s + 3 + a] = hi;
       if (a < P.dim) {

@@ -38,7 +38,9 @@ def test_exports_every_declared_symbol(lib):
 
 @pytest.mark.parametrize("n,sub,l", [((24, 16, 1), (8, 8, 1), 2), ((64, 64, 1), (16, 16, 1), 4),
                                      ((40, 24, 1), (8, 12, 1), 7), ((10, 10, 1), (10, 10, 1), 0),
-                                     ((12, 8, 4), (4, 4, 2), 1)])
+                                     ((12, 8, 4), (4, 4, 2), 1), ((61, 45, 1), (16, 12, 1), 3),
+                                     ((50, 37, 1), (16, 12, 1), 0), ((40, 20, 1), (16, 32, 1), 2),
+                                     ((14, 11, 6), (4, 3, 4), 1)])
 def test_plan_export_matches_oracle_bit_exactly(lib, n, sub, l):
     dim = 3 if n[2] > 1 else 2
     prob = W.random_problem(n, dim=dim, seed=0)
@@ -48,7 +50,7 @@ def test_plan_export_matches_oracle_bit_exactly(lib, n, sub, l):
     assert got.dtype == want.dtype and np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("bad", [dict(sub=(5, 8, 1)), dict(oversample=8), dict(oversample=-1), dict(alpha=0.0),
+@pytest.mark.parametrize("bad", [dict(sub=(5, 8, 1), oversample=4), dict(sub=(0, 8, 1)), dict(oversample=8), dict(oversample=-1), dict(alpha=0.0),
                                  dict(tol=-1.0), dict(restart=0), dict(max_iter=0), dict(local_prec=7),
                                  dict(smooth_kind=2)])
 def test_invalid_parameters_rejected(lib, bad):

@@ -48,6 +48,11 @@ CASES = {
                       dict(sub=(16, 12, 1), oversample=2, smooth_steps=2)),
     "neumann-data": (dict(n=(40, 40, 1), seed=9, bc_kind=[0, 1, 1, 0, 1, 1]),
                      dict(sub=(10, 8, 1), oversample=1, smooth_steps=1)),
+    # grids the subdomain size does not divide: the last subdomain of each row / column is shorter
+    "uneven-61x45": (dict(n=(61, 45, 1), seed=10), dict(sub=(16, 12, 1), oversample=3, smooth_steps=1)),
+    "uneven-50x37-l0": (dict(n=(50, 37, 1), seed=11, bc_kind=[0, 1, 0, 1, 1, 1]),
+                        dict(sub=(16, 12, 1), oversample=0, smooth_steps=1)),
+    "uneven-40x20-tall": (dict(n=(40, 20, 1), seed=12), dict(sub=(16, 32, 1), oversample=2, smooth_steps=2)),
 }
 
 
@@ -59,7 +64,7 @@ def _case(name):
     return prob, q
 
 
-@pytest.mark.parametrize("name", ["os-48x40", "ragged-60x36", "dirichlet-all", "neumann-data"])
+@pytest.mark.parametrize("name", ["os-48x40", "ragged-60x36", "dirichlet-all", "neumann-data", "uneven-61x45"])
 def test_transmissibilities_rhs_operator(mrcm, name):
     prob, q = _case(name)
     s = mrcm.Solver(prob, q)
@@ -89,7 +94,8 @@ def _phi_gpu_layout(pre, s_idx, smax):
     return out
 
 
-@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "stripes-128x64"])
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "stripes-128x64",
+                                  "uneven-61x45", "uneven-50x37-l0"])
 def test_informed_spaces_basis_moments_and_coupling_matrix(mrcm, name):
     prob, q = _case(name)
     s = mrcm.Solver(prob, q)
@@ -132,7 +138,7 @@ def test_apply_precond_matches_oracle(mrcm, name):
         assert _rel(z, parts["z"]) < 1e-10, (name, trial, _rel(z, parts["z"]))
 
 
-@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "dirichlet-all"])
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "dirichlet-all", "uneven-61x45"])
 def test_multiplicative_smoothing_matches_oracle(mrcm, name):
     # the multicolour sweep: one launch per colour over that colour's boxes, z updated in place
     prob, q = _case(name)
@@ -168,7 +174,8 @@ def test_multiplicative_smoothing_gmres_matches_oracle(mrcm):
 # GMRES(8) where restarted GMRES converges for this operator (covers the restart path); a long
 # restart where it stagnates (A T has eigenvalues with negative real part once smoothing is on)
 @pytest.mark.parametrize("name,restart", [("os-96x64-l4s2", 8), ("mrcm-48x40", 8), ("dirichlet-all", 8),
-                                          ("os-48x40", 100), ("ragged-60x36", 100)])
+                                          ("os-48x40", 100), ("ragged-60x36", 100), ("uneven-61x45", 100),
+                                          ("uneven-50x37-l0", 100)])
 def test_gmres_matches_oracle(mrcm, name, restart):
     prob, q = _case(name)
     q.tol = 1e-9
