@@ -77,8 +77,9 @@ typedef struct mrcm_problem {
 
 /* Method and solver parameters (Table 1 notation: oversampling l*h, k smoothing steps). */
 typedef struct mrcm_params {
-  int32_t sub[3];           /* cells per subdomain per axis; must divide n (sub[2] = 1 in 2-D) */
-  int32_t oversample;       /* l, cells: 0 <= l < sub[a] on every active axis */
+  int32_t sub[3];           /* cells per subdomain per axis (sub[2] = 1 in 2-D); where sub[a] does
+                               not divide n[a], the last subdomain along axis a takes the remainder */
+  int32_t oversample;       /* l, cells: 0 <= l < the size of every subdomain on every active axis */
   int32_t smooth_steps;     /* Schwarz sweeps after the multiscale solve, >= 0 */
   double alpha;             /* Robin parameter of Eq. 6, > 0 (the paper uses 10) */
   double tol;               /* GMRES tolerance on ||b - A p||_2, > 0 */

@@ -123,6 +123,7 @@ CoarseDev coarse(mrcm_handle h) {
   c.ldab = h->lay.ldab;
   c.ab = at<double>(h, h->lay.G);
   c.ipiv = at<int>(h, h->lay.ipiv);
+  c.rdiag = at<double>(h, h->lay.rdiag);
   c.g = at<double>(h, h->lay.gc);
   c.iface = t.iface;
   c.home = t.home;
@@ -367,8 +368,7 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
     if (P.E2 <= COARSE_DENSE_MAX) {
       CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
     } else {
-      CK(h, launch_coarse_rhs(c, at<double>(h, L.mom0), P.E, st));
-      CK(h, launch_coarse_solve(c, st));
+      CK(h, launch_coarse_solve(c, at<double>(h, L.mom0), P.E, st));
     }
   }
   // reconstruction, into the buffer that makes the last smoothing sweep land in z: each sweep

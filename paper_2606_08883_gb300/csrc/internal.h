@@ -49,6 +49,7 @@ struct Layout {
   size_t Linv_loc, Linv_ohat_r, Linv_ohat_d;   // line-block inverse factors
   size_t phi, psi, mom, psi0, z0, mom0;   // informed spaces, basis, side moments, apply scratch
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
+  size_t rdiag;                           // reciprocals of the diagonal of U
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
@@ -188,6 +189,7 @@ struct CoarseDev {
   int kl, ku, ldab;
   double* ab;       // band LU storage, column-major, ldab x n
   int* ipiv;
+  double* rdiag;    // 1 / U(j, j), written by the factorisation
   double* g;        // rhs / solution (banded row order in, canonical unknowns out)
   const int* iface; // [E][3]
   const int* home;  // [2E] canonical row -> banded row
@@ -197,7 +199,8 @@ struct CoarseDev {
 cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st);
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st);
 cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
-cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st);
+// per apply without an explicit inverse: right-hand side from mom0, then the band solve
+cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st);
 cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,

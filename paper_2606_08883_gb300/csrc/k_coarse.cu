@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(512) k_gbtf2(CoarseDev c, int* flags) {
           b2 = sv[w];
           i2 = si[w];
         }
+      if (i2 > km) i2 = 0;  // NaN column: pivot in place, reported as singular
       const double piv = ab[(size_t)(kv + i2) + (size_t)j * ld];
       s_ok = (piv != 0.0 && isfinite(piv)) ? 1 : 0;
       if (!s_ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(512) k_gbtf2(CoarseDev c, int* flags) {
     }
     const double piv = ab[(size_t)kv + (size_t)j * ld];
     const double rp = 1.0 / piv;
+    if (tid == 0) c.rdiag[j] = rp;
     for (int i = 1 + tid; i <= km; i += nt) ab[(size_t)(kv + i) + (size_t)j * ld] *= rp;
     __syncthreads();
     const int ncol = ju - j;
@@ -242,7 +244,8 @@ __device__ __forceinline__ void gb_wait() {
 // column j below the diagonal, l_i = A(j+i, j) / piv as a product with 1/piv, read before the
 // interchange; writes ipiv[j] and the step's column reach.
 __device__ __forceinline__ void gb_pivot(const double* cj, int j, int km, int n, int ku, int ju_prev, int lane,
-                                         double* sl, int* s_jp, int* s_ju, int* s_ok, int* ipiv, int* flags) {
+                                         double* sl, int* s_jp, int* s_ju, int* s_ok, int* ipiv, double* rdiag,
+                                         int* flags) {
   double best = -1.0;
   int bi = 0x7fffffff;
   for (int i = lane; i <= km; i += 32) {
@@ -260,10 +263,12 @@ __device__ __forceinline__ void gb_pivot(const double* cj, int j, int km, int n,
       bi = oi;
     }
   }
+  if (bi > km) bi = 0;  // no comparable entry (NaN column): pivot in place, reported as singular below
   const double piv = cj[bi];
   const bool ok = piv != 0.0 && isfinite(piv);
   if (ok) {
     const double rp = 1.0 / piv;
+    if (lane == 0) rdiag[j] = rp;
     const double old0 = cj[0];
     for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi ? old0 : cj[i]) * rp;
   }
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* 
   gb_wait<0>();
   __syncthreads();
   if (warp == 0 && n > 0)
-    gb_pivot(slot(0) + kv, 0, min(kl, n - 1), n, ku, 0, lane, sl[0], &s_jp[0], &s_ju[0], &s_ok[0], c.ipiv, flags);
+    gb_pivot(slot(0) + kv, 0, min(kl, n - 1), n, ku, 0, lane, sl[0], &s_jp[0], &s_ju[0], &s_ok[0], c.ipiv, c.rdiag, flags);
   for (int j = 0; j < n; ++j) {
     const int pj = j & 1, pn = pj ^ 1;
     gb_wait<1>();  // columns up to j + W - 1 (requested two steps ago) have landed
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* 
       }
       if (warp == 1 && col == j + 1 && j + 1 < n)
         gb_pivot(slot(j + 1) + kv, j + 1, min(kl, n - 2 - j), n, ku, ju, lane, sl[pn], &s_jp[pn], &s_ju[pn], &s_ok[pn],
-                 c.ipiv, flags);
+                 c.ipiv, c.rdiag, flags);
     }
   }
   gb_wait<0>();
@@ -432,6 +437,125 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __
   for (int i = lane; i < n; i += 32) Ginv[(size_t)i * n + col] = b[i];
 }
 
+// Per apply when 2E is above the explicit-inverse limit: the right-hand side from the particular
+// side moments, then L U c = P g by one CTA with g resident in shared memory.  The band data (and
+// the pivot index) of the next GBS_DEPTH - 2 steps are in flight in a cp.async ring; a thread
+// loads its R band entries and right-hand-side rows into registers before it updates them, so its
+// R updates are independent; the reciprocal of the next diagonal is taken one step ahead.  One SM's
+// FP64 pipe bounds the step, which is why the rows are spread over all four of its schedulers.
+constexpr int GBS_THREADS = 128;
+
+__device__ __forceinline__ void gb_cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+static size_t gbtrs_smem(const CoarseDev& c, int depth) {
+  return sizeof(double) * (((size_t)c.n + 1) / 2 * 2 + (size_t)depth * (c.kl + c.ku + 2));
+}
+
+// R: rows per thread, GBS_THREADS R >= kl + ku + 1; GBS_DEPTH ring slots (steps in flight + 2)
+template <int R, int GBS_DEPTH>
+__global__ void __launch_bounds__(GBS_THREADS) k_gbtrs_smem(CoarseDev c, const double* __restrict__ mom0, int E) {
+  extern __shared__ __align__(16) double gsm[];
+  constexpr int NT = GBS_THREADS;
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const int stride = kv + 2;  // kv + 1 band entries, then the pivot index
+  const int tid = threadIdx.x;
+  double* b = gsm;
+  double* ring = gsm + ((size_t)n + 1) / 2 * 2;
+  const double* __restrict__ ab = c.ab;
+  for (int e = tid; e < E; e += NT) {
+    const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
+    const int ks = 2 * a + 1, ks2 = 2 * a;
+    b[c.home[2 * e]] = -(mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2]);
+    b[c.home[2 * e + 1]] = -(mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1]);
+  }
+  // forward: interchange of step j, then b[j + 1 + k] -= L(j + 1 + k, j) b[j].  Step j's slot is
+  // refilled (for step j + GBS_DEPTH) only after the barrier of step j + 1, when no thread reads it.
+  auto issueL = [&](int j) {
+    if (j < n) {
+      double* dst = ring + (size_t)(j % GBS_DEPTH) * stride;
+      const double* src = ab + (size_t)(kv + 1) + (size_t)j * ld;
+      const int lm = min(kl, n - 1 - j);
+      for (int k = tid; k < lm; k += NT) gb_cp_async8(dst + k, src + k);
+      if (tid == 0) gb_cp_async4(dst + kv + 1, c.ipiv + j);
+    }
+    gb_commit();
+  };
+  for (int t = 0; t < GBS_DEPTH - 1; ++t) issueL(t);
+  for (int j = 0; j < n; ++j) {
+    gb_wait<GBS_DEPTH - 2>();
+    __syncthreads();
+    issueL(j + GBS_DEPTH - 1);
+    const double* Lc = ring + (size_t)(j % GBS_DEPTH) * stride;
+    const int l = *reinterpret_cast<const int*>(Lc + kv + 1);
+    const int lm = min(kl, n - 1 - j);
+    double lv[R], bv[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) lv[q] = tid + NT * q < lm ? Lc[tid + NT * q] : 0.0;
+    if (l != j) {
+      if (tid == 0) {
+        const double t = b[l];
+        b[l] = b[j];
+        b[j] = t;
+      }
+      __syncthreads();
+    }
+    const double bj = b[j];
+#pragma unroll
+    for (int q = 0; q < R; ++q) bv[q] = tid + NT * q < lm ? b[j + 1 + tid + NT * q] : 0.0;
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (tid + NT * q < lm) b[j + 1 + tid + NT * q] = bv[q] - lv[q] * bj;
+  }
+  // backward, step t on column j = n - 1 - t: x_j = b[j] is final when the step starts; b[i] -=
+  // U(i, j) x_j for i = max(0, j - kv) .. j - 1, and the thread of row j - 1 then scales it by
+  // 1 / U(j-1, j-1), so the next step starts from x_{j-1} (ring slot: rows i0 .. j - 1, then 1 / U(j, j)
+  // at position kv)
+  auto issueU = [&](int t) {
+    if (t < n) {
+      const int j = n - 1 - t, i0 = max(0, j - kv);
+      double* dst = ring + (size_t)(t % GBS_DEPTH) * stride;
+      const double* src = ab + (size_t)(kv + i0 - j) + (size_t)j * ld;
+      for (int k = tid; k < j - i0; k += NT) gb_cp_async8(dst + k, src + k);
+      if (tid == 0) gb_cp_async8(dst + kv, c.rdiag + j);
+    }
+    gb_commit();
+  };
+  gb_wait<0>();
+  __syncthreads();
+  for (int t = 0; t < GBS_DEPTH - 1; ++t) issueU(t);
+  gb_wait<GBS_DEPTH - 2>();
+  __syncthreads();
+  if (tid == 0 && n > 0) b[n - 1] *= ring[kv];
+  for (int t = 0; t < n; ++t) {
+    const int j = n - 1 - t, i0 = max(0, j - kv), len = j - i0;
+    gb_wait<GBS_DEPTH - 3>();  // this step's slot and the next one's
+    __syncthreads();
+    issueU(t + GBS_DEPTH - 1);
+    const double* Uc = ring + (size_t)(t % GBS_DEPTH) * stride;
+    double uv[R], bv[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) uv[q] = tid + NT * q < len ? Uc[tid + NT * q] : 0.0;
+    const double bj = b[j];
+#pragma unroll
+    for (int q = 0; q < R; ++q) bv[q] = tid + NT * q < len ? b[i0 + tid + NT * q] : 0.0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int k = tid + NT * q;
+      if (k < len) {
+        double v = bv[q] - uv[q] * bj;
+        if (k == len - 1) v *= ring[(size_t)((t + 1) % GBS_DEPTH) * stride + kv];  // row j - 1
+        b[i0 + k] = v;
+      }
+    }
+  }
+  gb_wait<0>();
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) c.g[i] = b[i];
+}
+
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
   const size_t sm4 = sizeof(double) * 4 * (size_t)c.n;
@@ -485,8 +609,39 @@ cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(const CoarseDev& c, cudaStream_t st) {
+cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the deepest ring that fits next to the right-hand side: the band data come from HBM and one
+  // step is short, so several steps must be in flight
+  const int rows = (c.kl + c.ku + 1 + GBS_THREADS - 1) / GBS_THREADS;
+  int depth = 0;
+  for (int d : {8, 4})
+    if (gbtrs_smem(c, d) <= (size_t)optin) {
+      depth = d;
+      break;
+    }
+  if (depth > 0 && rows <= 8) {
+    const size_t sm = gbtrs_smem(c, depth);
+    cudaError_t e = cudaSuccess;
+    const int R = rows <= 2 ? 2 : rows <= 4 ? 4 : 8;
+#define MRCM_GBTRS(RR, DD)                                                               \
+  if (R == RR && depth == DD) {                                                          \
+    if ((e = raise_smem_limit<k_gbtrs_smem<RR, DD>>()) == cudaSuccess)                   \
+      k_gbtrs_smem<RR, DD><<<1, GBS_THREADS, sm, st>>>(c, mom0, E);                      \
+  }
+    MRCM_GBTRS(2, 4) MRCM_GBTRS(2, 8)
+    MRCM_GBTRS(4, 4) MRCM_GBTRS(4, 8)
+    MRCM_GBTRS(8, 4) MRCM_GBTRS(8, 8)
+#undef MRCM_GBTRS
+    if (e != cudaSuccess) return e;
+    count_launch(1);
+    return cudaGetLastError();
+  }
+  const cudaError_t e = launch_coarse_rhs(c, mom0, E, st);
+  if (e != cudaSuccess) return e;
   k_gbtrs<<<1, 256, 0, st>>>(c);
   count_launch(1);
   return cudaGetLastError();

@@ -206,6 +206,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.G = take(8 * (size_t)L.ldab * E2);
   L.ipiv = take(4 * E2);
   L.gc = take(8 * E2);
+  L.rdiag = take(8 * E2);
   L.Ginv = take(E2 <= (size_t)COARSE_DENSE_MAX ? 8 * E2 * E2 : 0);
   L.rho = take(8 * n);
   L.zt = take(8 * n);

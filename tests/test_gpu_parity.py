@@ -343,3 +343,27 @@ def test_diagonal_tensor_with_equal_components_is_the_scalar_path(mrcm):
     assert torch.equal(a.apply_precond(r), b.apply_precond(r))
     a.close()
     b.close()
+
+
+def test_banded_coupling_solve_above_the_dense_limit(mrcm):
+    # 44 x 44 subdomains: 2E = 7,568 coupling unknowns, above the explicit-inverse limit, so every
+    # apply runs the band LU solve (the path of the 2048 x 2048 workload's 16,128 unknowns)
+    prob = W.random_problem((264, 264, 1), seed=13, contrast=1e3)
+    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=100, max_iter=300)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+    pre = _oracle(prob, q)
+    assert pre.part.E2 == 7568
+    r = np.random.default_rng(17).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    parts = pre.apply_parts(r)
+    assert _rel(s.debug(mrcm.MRCM_DBG_COARSE), parts["c"]) < 1e-9
+    assert _rel(z, parts["z"]) < 1e-10
+    p, info = s.solve()
+    p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                      l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                      tol_relative=True, restart=q.restart, max_iter=q.max_iter)
+    assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    s.close()
