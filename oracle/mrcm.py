@@ -68,8 +68,19 @@ class MRCMOS:
         self.alpha = float(alpha)
         self.degree = int(iface_degree)
         self.nq = 1 + self.degree * (dim - 1)  # polynomial functions per side
+        if self.degree not in (0, 1):
+            raise ValueError("iface_degree must be 0 or 1")
         self.T = transmissibilities(K, self.h, dim, bc_kind)
         self.part = P = Partition(dim, n, self.sub, self.l)
+        if self.degree == 1:
+            # a linear function along a side needs two faces there, else it vanishes and the
+            # coupling matrix loses a column and a row (a side of one face carries only constants)
+            for s in range(P.S):
+                for side in range(2 * dim):
+                    if P.robin[s, side]:
+                        for b in range(dim):
+                            if b != side // 2 and P.box[s, 1, b] - P.box[s, 0, b] < 2:
+                                raise ValueError("iface_degree 1 needs at least two faces on every Robin side")
         self.subs = []
         for s in range(P.S):
             self.subs.append(self._setup_subdomain(s))

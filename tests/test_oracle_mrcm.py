@@ -301,3 +301,20 @@ def test_basis_equals_restricted_oversampled_solution(l, degree, dim, n2):
             inner = tuple(slice(int(P.box[d.s, 0, a] - olo[a]), int(P.box[d.s, 1, a] - olo[a])) for a in (2, 1, 0))
             ref = qk[inner].ravel()
             assert np.allclose(d.psi[:, j], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_piecewise_linear_sides_need_two_faces():
+    # 13 = 3 * 4 + 1: the last row of subdomains is one cell high, so its -x / +x Robin sides have a
+    # single face, on which the linear side function vanishes (2 (0 + 1/2) / 1 - 1 = 0)
+    prob = W.random_problem((12, 13, 1), seed=4)
+    _pre(prob, (4, 4, 1), 0, 0, 0)
+    with pytest.raises(ValueError):
+        _pre(prob, (4, 4, 1), 0, 0, 1)
+    # a one-cell-high grid: the -x / +x sides have one face each
+    with pytest.raises(ValueError):
+        _pre(W.random_problem((12, 1, 1), seed=4), (4, 1, 1), 0, 0, 1)
+    # a single row of subdomains two cells high has no -y / +y Robin sides and two faces on the others
+    pre = _pre(W.random_problem((12, 2, 1), seed=4), (4, 2, 1), 0, 0, 1)
+    assert pre.nq == 2 and pre.n_coarse == 2 * pre.part.E2 == 8
+    with pytest.raises(ValueError):
+        _pre(prob, (4, 4, 1), 0, 0, 2)
