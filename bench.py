@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=200)
     ap.add_argument("--smooth", default="additive", choices=["additive", "multiplicative"],
                     help="Schwarz sweeps: restricted additive (default) or multiplicative multicolour")
+    ap.add_argument("--degree", type=int, default=0, choices=[0, 1],
+                    help="interface-space degree: 0 piecewise constant (default), 1 piecewise linear")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=8, help="GMRES iterations per reference-arm sample")
@@ -78,6 +80,7 @@ def workload(args, rank=0):
     q.restart = args.restart
     q.max_iter = 3 * args.restart
     q.smooth_kind = 1 if getattr(args, "smooth", "additive") == "multiplicative" else 0
+    q.iface_degree = int(getattr(args, "degree", 0))
     return prob, q
 
 
@@ -85,7 +88,8 @@ def config_dict(args, prob, q):
     return {"workload": f"channels-{args.N}x{args.N}-contrast1e6-fill0.30", "cells": prob.cells,
             "subdomains": f"{prob.n[0] // q.sub[0]}x{prob.n[1] // q.sub[1]} of {q.sub[0]}x{q.sub[1]}",
             "oversample": q.oversample, "smooth_steps": q.smooth_steps, "alpha": q.alpha, "restart": q.restart,
-            "tol_relative": q.tol, "local_prec": args.prec, "smoothing": getattr(args, "smooth", "additive"), "l2": "flushed between timed steps (256 MiB write)",
+            "tol_relative": q.tol, "local_prec": args.prec, "smoothing": getattr(args, "smooth", "additive"),
+            "iface_degree": int(getattr(args, "degree", 0)), "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single-gpu"}
 
 
@@ -97,7 +101,8 @@ from paper_2606_08883_gb300 import workloads as W
 from oracle.solve import build, solve
 prob, q = W.channels({N}, seed=1)
 t0 = time.perf_counter()
-pre = build(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha, smooth_kind={kind})
+pre = build(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha, iface_degree={degree},
+            smooth_kind={kind})
 t1 = time.perf_counter()
 p, info, _ = solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub, l=q.oversample,
                    smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol, restart={restart}, max_iter={iters},
@@ -108,11 +113,11 @@ print(json.dumps({{"setup_s": t1 - t0, "iter_s": t2 - t1, "iters": info["iterati
 """
 
 
-def run_oracle_sample(N, restart, iters, timeout=900, kind=0):
+def run_oracle_sample(N, restart, iters, timeout=900, kind=0, degree=0):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, N=N, restart=restart, iters=iters, kind=int(kind))
+    code = ORACLE_SNIPPET.format(root=ROOT, N=N, restart=restart, iters=iters, kind=int(kind), degree=int(degree))
     r = subprocess.run([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
                        env=env, timeout=timeout)
     if r.returncode != 0:
@@ -294,10 +299,11 @@ def reference_arm(args):
         return
     rates = []
     for step in range(args.warmup + args.steps):
-        s = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0)
+        s = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0,
+                              degree=args.degree)
         if step >= args.warmup:
             rates.append(s)
-    need = ORACLE_FULL_ITERS.get((args.N, args.restart), None)
+    need = ORACLE_FULL_ITERS.get((args.N, args.restart, 1 if args.smooth == "multiplicative" else 0, args.degree))
     iters_needed = need if need else rates[-1]["iters"]
     vals = [oracle_rate(s, iters_needed)[0] for s in rates]
     v = statistics.median(vals)
@@ -313,7 +319,9 @@ def reference_arm(args):
 
 
 # iterations the FP64 oracle needs for a full solve of the default workload (measured, GMRES(200))
-ORACLE_FULL_ITERS = {(512, 200): 178}
+# GMRES iterations of a full oracle solve of the channel workload, keyed by (N, restart, smoothing
+# kind, interface degree)
+ORACLE_FULL_ITERS = {(512, 200, 0, 0): 178, (512, 200, 1, 0): 179, (512, 200, 0, 1): 132}
 
 
 def mrcm_arm(args):
@@ -324,7 +332,8 @@ def mrcm_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # before any CUDA call: the oracle runs in its own process on the host cores
         try:
-            cpu = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0)
+            cpu = run_oracle_sample(args.N, args.restart, args.ref_iters, kind=1 if args.smooth == "multiplicative" else 0,
+                                    degree=args.degree)
         except Exception as exc:  # reported, never silently replaced
             cpu = {"error": str(exc)[:300]}
     import torch

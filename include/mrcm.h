@@ -92,6 +92,12 @@ typedef struct mrcm_params {
                                Multiplicative: subdomains coloured by the parities of their grid
                                coordinates (2^dim colours), one restricted step per colour in order,
                                each from the residual left by the previous colours */
+  int32_t iface_degree;     /* polynomial degree of the multiplier and test spaces on each Robin side
+                               (lambda^k, M_H, V_H of Sec. 2.1): 0 piecewise constant (the default),
+                               1 piecewise linear (constant plus the linear function along the side,
+                               scaled to [-1, 1] over the side); each Robin side then carries
+                               1 + iface_degree coupling unknowns and each interface 2 (1 + iface_degree)
+                               rows of Eq. 13-14 */
 } mrcm_params;
 
 enum { MRCM_SMOOTH_ADDITIVE = 0, MRCM_SMOOTH_MULTIPLICATIVE = 1 };
@@ -176,11 +182,13 @@ mrcm_status mrcm_plan_export(const mrcm_problem* problem, const mrcm_params* par
 
 /* Debug / parity access to internal device arrays, copied to host (synchronises `stream`):
  *   MRCM_DBG_TRANS   face transmissibilities, x faces then y faces
- *   MRCM_DBG_PHI     informed spaces, [S][4 functions][4 sides][max(sub0, sub1)]
- *   MRCM_DBG_PSI     basis functions, [4 sides][n cells] (global layout)
- *   MRCM_DBG_MOMENTS side moments of the basis traces, [S][4 sides][4 functions][F, |f|P]
- *   MRCM_DBG_G       coupling matrix G, dense 2E x 2E row-major in the canonical row order
- *   MRCM_DBG_COARSE  coefficients c of the last apply, [2E]
+ *   MRCM_DBG_PHI     informed spaces, [S][4 nq functions][4 sides][max(sub0, sub1)]
+ *   MRCM_DBG_PSI     basis functions, [4 nq functions][n cells] (global layout)
+ *   MRCM_DBG_MOMENTS side moments of the basis traces, [S][4 sides][4 nq functions][nq tests][F, |f|P]
+ *   MRCM_DBG_G       coupling matrix G, dense (2E nq)^2 row-major in the canonical row order
+ *   MRCM_DBG_COARSE  coefficients c of the last apply, [2E nq]
+ * with nq = 1 + iface_degree and function r nq + q the degree-q function of side r (sides -x, +x,
+ * -y, +y); canonical rows of interface e: 2 nq e + q (flux, test q), 2 nq e + nq + q (pressure).
  *   MRCM_DBG_ZMRCM   last apply's multiscale solution before smoothing, [n cells]
  * *len receives the element count; at most cap doubles are written. */
 enum { MRCM_DBG_TRANS = 0, MRCM_DBG_PHI = 1, MRCM_DBG_PSI = 2, MRCM_DBG_MOMENTS = 3, MRCM_DBG_G = 4,

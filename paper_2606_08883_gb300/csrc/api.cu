@@ -102,6 +102,7 @@ Geo geo(mrcm_handle h) {
   g.my = P.m[1];
   g.l = P.l;
   g.smax = h->lay.smax;
+  g.nq = P.nq;
   g.hx = h->h[0];
   g.hy = h->h[1];
   g.hz = h->h[2];
@@ -117,7 +118,8 @@ CoarseDev coarse(mrcm_handle h) {
   CoarseDev c;
   const Plan& P = h->plan;
   Tables t = tables(h);
-  c.n = P.E2;
+  c.n = P.NC;
+  c.nq = P.nq;
   c.kl = P.kl;
   c.ku = P.ku;
   c.ldab = h->lay.ldab;
@@ -307,14 +309,15 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
   }
   // MRCM-OS step 2: informed multiplier spaces from the oversampled Robin problems (Eq. 15)
-  CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * L.smax, st));
+  CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * P.nq * L.smax, st));
   if (P.l > 0) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
     CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
   }
   {
     Phase ph(h, MRCM_PH_INFORMED, st);
-    CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), at<int>(h, L.flags), st));
+    for (int q = 0; q < P.nq; ++q)
+      CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st));
   }
   // MRCM-OS step 3: local Robin factors and multiscale basis functions
   {
@@ -323,8 +326,9 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   }
   {
     Phase ph(h, MRCM_PH_BASIS, st);
-    CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), at<double>(h, L.psi),
-                       at<double>(h, L.mom), at<int>(h, L.flags), st));
+    for (int q = 0; q < P.nq; ++q)
+      CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), q, at<double>(h, L.psi),
+                         at<double>(h, L.mom), at<int>(h, L.flags), st));
   }
   // coupling system (Eq. 13-14)
   CoarseDev c = coarse(h);
@@ -332,7 +336,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
     CK(h, launch_coarse_factor(c, flags, st));
-    if (P.E2 <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
+    if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
   }
   // smoothing: Dirichlet factors of the oversampled regions
   if (h->prm.smooth_steps > 0) {
@@ -365,7 +369,7 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   CoarseDev c = coarse(h);
   {
     Phase ph(h, MRCM_PH_COARSE_SOLVE, st);
-    if (P.E2 <= COARSE_DENSE_MAX) {
+    if (P.NC <= COARSE_DENSE_MAX) {
       CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
     } else {
       CK(h, launch_coarse_solve(c, at<double>(h, L.mom0), P.E, st));
@@ -656,10 +660,10 @@ mrcm_status mrcm_debug_get(mrcm_handle h, int32_t what, double* host_out, size_t
       CK(h, cudaStreamSynchronize(st));
       return MRCM_OK;
     }
-    case MRCM_DBG_PHI: off = L.phi; cnt = (size_t)P.S * 16 * L.smax; break;
-    case MRCM_DBG_PSI: off = L.psi; cnt = 4 * n; break;
-    case MRCM_DBG_MOMENTS: off = L.mom; cnt = (size_t)P.S * 32; break;
-    case MRCM_DBG_COARSE: off = L.gc; cnt = P.E2; break;
+    case MRCM_DBG_PHI: off = L.phi; cnt = (size_t)P.S * 16 * P.nq * L.smax; break;
+    case MRCM_DBG_PSI: off = L.psi; cnt = 4 * P.nq * n; break;
+    case MRCM_DBG_MOMENTS: off = L.mom; cnt = (size_t)P.S * 32 * P.nq * P.nq; break;
+    case MRCM_DBG_COARSE: off = L.gc; cnt = P.NC; break;
     case MRCM_DBG_ZMRCM:
       if (!host_out) {
         h->keep_z0 = true;  // capture the multiscale solution from now on
@@ -670,26 +674,35 @@ mrcm_status mrcm_debug_get(mrcm_handle h, int32_t what, double* host_out, size_t
       cnt = n;
       break;
     case MRCM_DBG_G: {
-      const size_t E2 = P.E2;
-      *len = E2 * E2;
+      const size_t NC = P.NC;
+      const int nq = P.nq, nf = 4 * nq;
+      *len = NC * NC;
       if (!host_out) return MRCM_OK;
-      std::vector<double> mom((size_t)P.S * 32);
+      std::vector<double> mom((size_t)P.S * 32 * nq * nq);
       CK(h, cudaMemcpyAsync(mom.data(), at<double>(h, L.mom), 8 * mom.size(), cudaMemcpyDeviceToHost, st));
       CK(h, cudaStreamSynchronize(st));
-      std::vector<double> G(E2 * E2, 0.0);
+      // moment of function fn of subdomain t on side k against test qt: [F, |f|P]
+      auto M = [&](int t, int k, int fn, int qt, int which) {
+        return mom[((((size_t)t * 4 + k) * nf + fn) * nq + qt) * 2 + which];
+      };
+      std::vector<double> G(NC * NC, 0.0);
       for (int e = 0; e < P.E; ++e) {
         const int a = P.iface[3 * e], s = P.iface[3 * e + 1], s2 = P.iface[3 * e + 2];
-        for (int r = 0; r < 4; ++r) {
-          if (P.rank[6 * s + r] >= 0) {
-            const size_t col = P.off[s] + P.rank[6 * s + r];
-            G[(2 * e) * E2 + col] += mom[(((size_t)s * 4 + 2 * a + 1) * 4 + r) * 2];
-            G[(2 * e + 1) * E2 + col] += mom[(((size_t)s * 4 + 2 * a + 1) * 4 + r) * 2 + 1];
-          }
-          if (P.rank[6 * s2 + r] >= 0) {
-            const size_t col = P.off[s2] + P.rank[6 * s2 + r];
-            G[(2 * e) * E2 + col] += mom[(((size_t)s2 * 4 + 2 * a) * 4 + r) * 2];
-            G[(2 * e + 1) * E2 + col] -= mom[(((size_t)s2 * 4 + 2 * a) * 4 + r) * 2 + 1];
-          }
+        for (int qt = 0; qt < nq; ++qt) {
+          const size_t rf = (size_t)2 * nq * e + qt, rp = rf + nq;
+          for (int r = 0; r < 4; ++r)
+            for (int q = 0; q < nq; ++q) {
+              if (P.rank[6 * s + r] >= 0) {
+                const size_t col = (size_t)(P.off[s] + P.rank[6 * s + r]) * nq + q;
+                G[rf * NC + col] += M(s, 2 * a + 1, r * nq + q, qt, 0);
+                G[rp * NC + col] += M(s, 2 * a + 1, r * nq + q, qt, 1);
+              }
+              if (P.rank[6 * s2 + r] >= 0) {
+                const size_t col = (size_t)(P.off[s2] + P.rank[6 * s2 + r]) * nq + q;
+                G[rf * NC + col] += M(s2, 2 * a, r * nq + q, qt, 0);
+                G[rp * NC + col] -= M(s2, 2 * a, r * nq + q, qt, 1);
+              }
+            }
         }
       }
       std::memcpy(host_out, G.data(), 8 * std::min(cap, G.size()));

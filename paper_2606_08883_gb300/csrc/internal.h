@@ -23,7 +23,9 @@ struct Plan {
   int l = 0;
   int S = 0;                // subdomains
   int E = 0;                // interfaces
-  int E2 = 0;               // coarse unknowns = 2E
+  int E2 = 0;               // Robin sides = 2E
+  int nq = 1;               // polynomial functions per Robin side (1 + interface degree)
+  int NC = 0;               // coupling unknowns = 2E nq
   std::vector<int> box;     // [S][6] lo[3] hi[3]
   std::vector<int> obox;    // [S][6] oversampled box clipped to the grid
   std::vector<int> mask;    // [S] Robin side bits
@@ -88,6 +90,7 @@ struct Geo {
   int mx, my;              // subdomain counts
   int l;                   // oversampling
   int smax;
+  int nq;                  // functions per Robin side
   double hx, hy, hz;
   double alpha;
   const double* K;         // scalar permeability, or the x component of a diagonal tensor
@@ -172,8 +175,8 @@ cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const*
 enum BoxKind : int { BOX_OMEGA_ROBIN = 0, BOX_OHAT_ROBIN = 1, BOX_OHAT_DIRICHLET = 2 };
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
                           cudaStream_t st);
-cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int* flags, cudaStream_t st);
-cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st);
+cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
                          double* mom, int* flags, cudaStream_t st);
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, int* flags, cudaStream_t st);
@@ -185,7 +188,8 @@ size_t factor_smem_bytes(int w, bool fp32, int nch);
 
 // coupling system (k_coarse.cu)
 struct CoarseDev {
-  int n;            // 2E
+  int n;            // 2E nq
+  int nq;           // functions per Robin side
   int kl, ku, ldab;
   double* ab;       // band LU storage, column-major, ldab x n
   int* ipiv;

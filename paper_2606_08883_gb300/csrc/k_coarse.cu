@@ -8,43 +8,65 @@
 // they mostly depend on (flux row at (s, +a), pressure row at (s', -a)), which makes G banded with
 // half-bandwidth about 4 m_x; it is factored by band LU with partial pivoting (row interchanges
 // only) in LAPACK band layout: A(i, j) at ab[kv + i - j + j * ldab], kv = kl + ku, ldab = 2 kl + ku + 1.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace mrcm {
 
-// G entries from the side moments mom[s][side][function][F, |f|P]; ab must be zeroed.
+// G entries from the side moments mom[s][side][function r nq + q][test qt][F, |f|P]; ab must be
+// zeroed.  Interface e has nq flux rows and nq pressure rows (one per test function qt), homed at
+// row_home * nq + qt; unknown (t, side r, degree q) is column (off_t + rank_t(r)) nq + q.
 __global__ void k_coarse_assemble(CoarseDev c, const double* __restrict__ mom, int E) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
-  const int kv = c.kl + c.ku;
+  const int kv = c.kl + c.ku, nq = c.nq, nf = 4 * nq;
   const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
-  const int rf = c.home[2 * e], rp = c.home[2 * e + 1];
   const int ks = 2 * a + 1, ks2 = 2 * a;  // +a side of s, -a side of s'
-  for (int r = 0; r < 4; ++r) {
-    const int q = c.rank[6 * s + r];
-    if (q >= 0) {
-      const int col = c.off[s] + q;
-      c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = mom[(((size_t)s * 4 + ks) * 4 + r) * 2];
-      c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = mom[(((size_t)s * 4 + ks) * 4 + r) * 2 + 1];
-    }
-    const int q2 = c.rank[6 * s2 + r];
-    if (q2 >= 0) {
-      const int col = c.off[s2] + q2;
-      c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = mom[(((size_t)s2 * 4 + ks2) * 4 + r) * 2];
-      c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = -mom[(((size_t)s2 * 4 + ks2) * 4 + r) * 2 + 1];
-    }
+  for (int qt = 0; qt < nq; ++qt) {
+    const int rf = c.home[2 * e] * nq + qt, rp = c.home[2 * e + 1] * nq + qt;
+    for (int r = 0; r < 4; ++r)
+      for (int q = 0; q < nq; ++q) {
+        const int k1 = c.rank[6 * s + r];
+        if (k1 >= 0) {
+          const int col = (c.off[s] + k1) * nq + q;
+          const double* m = mom + ((((size_t)s * 4 + ks) * nf + r * nq + q) * nq + qt) * 2;
+          c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = m[0];
+          c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = m[1];
+        }
+        const int k2 = c.rank[6 * s2 + r];
+        if (k2 >= 0) {
+          const int col = (c.off[s2] + k2) * nq + q;
+          const double* m = mom + ((((size_t)s2 * 4 + ks2) * nf + r * nq + q) * nq + qt) * 2;
+          c.ab[(size_t)(kv + rf - col) + (size_t)col * c.ldab] = m[0];
+          c.ab[(size_t)(kv + rp - col) + (size_t)col * c.ldab] = -m[1];
+        }
+      }
   }
 }
 
-__global__ void k_coarse_rhs(CoarseDev c, const double* __restrict__ mom0, int E) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
+// Rows of test function qt of interface e (banded order) and their right-hand sides -(F_s + F_s'),
+// -(P_s - P_s') from the particular side moments mom0[S][4 sides][nq tests][F, |f|P].
+__device__ __forceinline__ void coarse_rhs_rows(const CoarseDev& c, const double* __restrict__ mom0, int e, int qt,
+                                                int& rf, double& gf, int& rp, double& gp) {
   const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
-  const int ks = 2 * a + 1, ks2 = 2 * a;
-  const double F = mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2];
-  const double P = mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1];
-  c.g[c.home[2 * e]] = -F;
-  c.g[c.home[2 * e + 1]] = -P;
+  const int nq = c.nq;
+  const double* m1 = mom0 + (((size_t)s * 4 + 2 * a + 1) * nq + qt) * 2;
+  const double* m2 = mom0 + (((size_t)s2 * 4 + 2 * a) * nq + qt) * 2;
+  rf = c.home[2 * e] * nq + qt;
+  rp = c.home[2 * e + 1] * nq + qt;
+  gf = -(m1[0] + m2[0]);
+  gp = -(m1[1] - m2[1]);
+}
+
+__global__ void k_coarse_rhs(CoarseDev c, const double* __restrict__ mom0, int E) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * c.nq) return;
+  int rf, rp;
+  double gf, gp;
+  coarse_rhs_rows(c, mom0, t / c.nq, t % c.nq, rf, gf, rp, gp);
+  c.g[rf] = gf;
+  c.g[rp] = gp;
 }
 
 // Unblocked band LU with partial pivoting, one CTA.
@@ -201,11 +223,12 @@ __global__ void __launch_bounds__(256) k_coarse_apply(CoarseDev c, const double*
                                                       const double* __restrict__ mom0, int E, double* __restrict__ out) {
   extern __shared__ double gs[];
   const int n = c.n;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
-    const int ks = 2 * a + 1, ks2 = 2 * a;
-    gs[c.home[2 * e]] = -(mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2]);
-    gs[c.home[2 * e + 1]] = -(mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1]);
+  for (int t = threadIdx.x; t < E * c.nq; t += blockDim.x) {
+    int rf, rp;
+    double gf, gp;
+    coarse_rhs_rows(c, mom0, t / c.nq, t % c.nq, rf, gf, rp, gp);
+    gs[rf] = gf;
+    gs[rp] = gp;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -347,6 +370,150 @@ __global__ void __launch_bounds__(GBW_THREADS, 1) k_gbtf2_win(CoarseDev c, int* 
   }
 }
 
+// ---- Band LU over a thread-block cluster ------------------------------------------------------
+// The same steps as k_gbtf2_win, with the window spread over the CL CTAs of one cluster: column c
+// belongs to CTA c mod CL, which keeps it in a ring of NS column slots in its shared memory from
+// two steps before it can first be touched (column j + kl + ku + 2 is requested at step j) until
+// it is final, and then writes it back.  Per step j, after a cluster barrier, every CTA copies the
+// pivot and the multipliers of step j from the shared memory of the owner of column j, applies
+// the interchange and the rank-one update to its own columns j .. ju, and the owner of column
+// j + 1 chooses the pivot of step j + 1 as soon as that column is final for step j (look-ahead),
+// so a step costs one cluster barrier and the arithmetic of a step is spread over CL SMs.
+constexpr int GBC_THREADS = 512;
+
+__global__ void __launch_bounds__(GBC_THREADS, 1) k_gbtrf_cluster(CoarseDev c, int* flags, int NS) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double cwin[];
+  __shared__ double sl[2][GBW_MAX_KL + 1];  // this CTA's multipliers of the step it chose the pivot of
+  __shared__ int s_jp[2], s_ju[2], s_ok[2];
+  __shared__ int t_jp, t_ju, t_ok;          // the current step's pivot, copied from its owner
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  const int W = kl + ku + 1;
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  double* ab = c.ab;
+  double* lb = cwin + (size_t)NS * ld;      // [kl + 1] multipliers of the current step
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nw = GBC_THREADS / 32;
+  auto slot = [&](int col) { return cwin + (size_t)((col / CL) % NS) * ld; };
+  auto load_col = [&](int col) {
+    double* dst = slot(col);
+    const double* src = ab + (size_t)col * ld;
+    for (int r = tid; r < ld; r += GBC_THREADS) gb_cp_async8(dst + r, src + r);
+  };
+  auto store_col = [&](int col) {
+    const double* src = slot(col);
+    double* dst = ab + (size_t)col * ld;
+    for (int r = tid; r < ld; r += GBC_THREADS) dst[r] = src[r];
+  };
+  for (int col = rank; col < n && col <= W; col += CL) load_col(col);
+  gb_commit();
+  gb_wait<0>();
+  __syncthreads();
+  if (rank == 0 && warp == 0 && n > 0)
+    gb_pivot(slot(0) + kv, 0, min(kl, n - 1), n, ku, 0, lane, sl[0], &s_jp[0], &s_ju[0], &s_ok[0], c.ipiv, c.rdiag,
+             flags);
+  for (int j = 0; j < n; ++j) {
+    const int pj = j & 1, pn = pj ^ 1;
+    const int owner = j % CL;
+    gb_wait<1>();  // this CTA's columns up to j + W - 1 (requested two steps ago) have landed
+    cl.sync();     // publishes the pivot and multipliers of step j, and orders the previous step
+    const int km = min(kl, n - 1 - j);
+    if (tid == 0) {
+      t_jp = *cl.map_shared_rank(&s_jp[pj], owner);
+      t_ju = *cl.map_shared_rank(&s_ju[pj], owner);
+      t_ok = *cl.map_shared_rank(&s_ok[pj], owner);
+    }
+    {
+      const double* rl = cl.map_shared_rank(&sl[pj][0], owner);
+      for (int i = 1 + tid; i <= km; i += GBC_THREADS) lb[i] = rl[i];
+    }
+    if (j >= 1 && (j - 1) % CL == rank) store_col(j - 1);  // column j - 1 is final
+    if (j + W + 1 < n && (j + W + 1) % CL == rank) load_col(j + W + 1);
+    gb_commit();
+    __syncthreads();
+    const bool ok = t_ok != 0;
+    const int ju = t_ju, jp = t_jp;
+    // this CTA's columns from j on, warp w taking the w-th of them (the owner of column j + 1 meets
+    // it first, in warp 0, and chooses the pivot of step j + 1 on it right after its update)
+    const int first = j + ((rank - j) % CL + CL) % CL;
+    for (int col = first + warp * CL; col <= ju || (col == j + 1 && j + 1 < n); col += nw * CL) {
+      if (ok && col <= ju) {
+        double* cc = slot(col) + kv + j - col;  // cc[i] = A(j + i, col)
+        const double up = cc[jp], old0 = cc[0];
+        __syncwarp();
+        if (col == j) {
+          if (lane == 0) cc[0] = up;
+          for (int i = 1 + lane; i <= km; i += 32) cc[i] = lb[i];
+        } else {
+          if (lane == 0) cc[0] = up;
+          for (int i = 1 + lane; i <= km; i += 32) cc[i] = (i == jp ? old0 : cc[i]) - lb[i] * up;
+        }
+        __syncwarp();
+      }
+      if (col == j + 1 && j + 1 < n)
+        gb_pivot(slot(j + 1) + kv, j + 1, min(kl, n - 2 - j), n, ku, ju, lane, sl[pn], &s_jp[pn], &s_ju[pn], &s_ok[pn],
+                 c.ipiv, c.rdiag, flags);
+    }
+  }
+  gb_wait<0>();
+  cl.sync();
+  if (n >= 1 && (n - 1) % CL == rank) store_col(n - 1);
+}
+
+static size_t gbtrf_cluster_smem(const CoarseDev& c, int CL, int* NS) {
+  const int kv = c.kl + c.ku;
+  *NS = (kv + 4 + CL - 1) / CL + 1;
+  return sizeof(double) * ((size_t)(*NS) * c.ldab + c.kl + 2);
+}
+
+// Launches the cluster factorisation with the largest cluster (16, else 8) that the device can
+// schedule with the ring in shared memory; returns false (nothing launched) when none fits.
+static bool launch_gbtrf_cluster(const CoarseDev& c, int* flags, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (c.kl > GBW_MAX_KL) return false;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t static_smem = sizeof(double) * 2 * (GBW_MAX_KL + 1) + 64;
+  // once per process: the shared-memory limit, and clusters of 16 where the device allows them
+  static const int max_cl = [] {
+    if (raise_smem_limit<k_gbtrf_cluster>() != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(k_gbtrf_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return 8;
+    }
+    return 16;
+  }();
+  for (int CL : {16, 8}) {
+    if (CL > max_cl) continue;
+    int NS = 0;
+    const size_t sm = gbtrf_cluster_smem(c, CL, &NS);
+    if (sm + static_smem > (size_t)optin) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(GBC_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_gbtrf_cluster, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();  // clear a refusal of this cluster size; try the next one
+      continue;
+    }
+    *err = cudaLaunchKernelEx(&cfg, k_gbtrf_cluster, c, flags, NS);
+    count_launch(1);
+    return true;
+  }
+  return false;
+}
+
 // Columns of G^-1, one warp per column and no block barriers: the band entries of the next step
 // are loaded while the current step runs (at most four rows per lane, i.e. kl + ku <= 128).
 constexpr int GBC_ROWS = 4;
@@ -465,11 +632,12 @@ __global__ void __launch_bounds__(GBS_THREADS) k_gbtrs_smem(CoarseDev c, const d
   double* b = gsm;
   double* ring = gsm + ((size_t)n + 1) / 2 * 2;
   const double* __restrict__ ab = c.ab;
-  for (int e = tid; e < E; e += NT) {
-    const int a = c.iface[3 * e], s = c.iface[3 * e + 1], s2 = c.iface[3 * e + 2];
-    const int ks = 2 * a + 1, ks2 = 2 * a;
-    b[c.home[2 * e]] = -(mom0[(size_t)s * 8 + ks * 2] + mom0[(size_t)s2 * 8 + ks2 * 2]);
-    b[c.home[2 * e + 1]] = -(mom0[(size_t)s * 8 + ks * 2 + 1] - mom0[(size_t)s2 * 8 + ks2 * 2 + 1]);
+  for (int t = tid; t < E * c.nq; t += NT) {
+    int rf, rp;
+    double gf, gp;
+    coarse_rhs_rows(c, mom0, t / c.nq, t % c.nq, rf, gf, rp, gp);
+    b[rf] = gf;
+    b[rp] = gp;
   }
   // forward: interchange of step j, then b[j + 1 + k] -= L(j + 1 + k, j) b[j].  Step j's slot is
   // refilled (for step j + GBS_DEPTH) only after the barrier of step j + 1, when no thread reads it.
@@ -586,6 +754,8 @@ cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E,
 
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
+  cudaError_t ce = cudaSuccess;
+  if (launch_gbtrf_cluster(c, flags, st, &ce)) return ce != cudaSuccess ? ce : cudaGetLastError();
   const size_t win = sizeof(double) * (size_t)(c.kl + c.ku + 4) * c.ldab;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -604,7 +774,7 @@ cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st
 
 cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st) {
   if (E == 0) return cudaSuccess;
-  k_coarse_rhs<<<(E + 127) / 128, 128, 0, st>>>(c, mom0, E);
+  k_coarse_rhs<<<(E * c.nq + 127) / 128, 128, 0, st>>>(c, mom0, E);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -373,11 +373,18 @@ struct SolveArgs {
   int LS;
   const double* in;    // particular, schwarz: r; basis: phi
   double* out;         // particular: psi0; schwarz: z after the sweep; basis: psi; informed: phi
-  double* mom;         // particular: mom0 [S][4][2]; basis: mom [S][4][4][2]
+  double* mom;         // particular: mom0 [S][4 sides][nq tests][2]; basis: mom [S][4 sides][4 nq][nq tests][2]
   const double* zin;   // schwarz: z before the sweep (read only)
   int* flags;          // device status word (FLAG_TIMEOUT if a bounded wait gives up)
   int colour;          // schwarz: -1 all boxes, else only the boxes of this colour (see colour_box)
+  int q;               // informed, basis: the degree of the side functions this launch handles
 };
+
+// Degree-q function of a box side at its face t of len: 1, or the linear function of the position
+// along the side scaled to [-1, 1] over the side (the multiplier and test functions of Sec. 2.1)
+__device__ __forceinline__ double side_fn(int q, int t, int len) {
+  return q == 0 ? 1.0 : 2.0 * (t + 0.5) / len - 1.0;
+}
 
 // Subdomain of the b-th box of a colour: colour bit 0 = parity of the x index, bit 1 = of the y
 // index; boxes of a colour in row-major order of their subdomains.
@@ -631,7 +638,13 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
         }
         const int gx = b.ox + x, gy = b.oy + J;
         if (!active(g, gx, gy)) continue;
-        Y[(J * w + x) * NR + r] += (T)face_tr(g, gx, gy, ax, dir, nullptr, nullptr);
+        double lam = 1.0;
+        if (a.q) {  // position along the side of the oversampled region (clipped to the grid)
+          const int lo = ax == 0 ? max(b.oy, 0) : max(b.ox, 0);
+          const int hi = ax == 0 ? min(b.oy + hgt, g.ny) : min(b.ox + w, g.nx);
+          lam = side_fn(a.q, (ax == 0 ? gy : gx) - lo, hi - lo);
+        }
+        Y[(J * w + x) * NR + r] += (T)(face_tr(g, gx, gy, ax, dir, nullptr, nullptr) * lam);
       }
       __syncthreads();
     }
@@ -647,7 +660,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
         const int x = gx - b.ox, J = gy - b.oy;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const double ph = a.in[(((size_t)s * 4 + r) * 4 + k) * g.smax + t];
+          const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + t];
           Y[(J * w + x) * NR + r] += (T)(tr * ph);
         }
       }
@@ -753,7 +766,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       if (active(g, b.ox + x, b.oy + J)) a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
     for (int kside = wid; kside < 4; kside += nw) {
-      double F = 0.0, Pw = 0.0;
+      double F[2] = {0.0, 0.0}, Pw[2] = {0.0, 0.0};  // against the test functions of degree 0, 1
       if (robin_side(g, s, kside)) {
         const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
@@ -762,15 +775,23 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
           gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
           const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
           const double fl = tr * (double)Y[(gy - b.oy) * w + (gx - b.ox)];
-          F += fl;
-          Pw += beta * fl;
+#pragma unroll
+          for (int qt = 0; qt < 2; ++qt)
+            if (qt < g.nq) {
+              const double wt = side_fn(qt, t, len);
+              F[qt] += wt * fl;
+              Pw[qt] += wt * (beta * fl);
+            }
         }
       }
-      F = warp_sum(F);
-      Pw = warp_sum(Pw);
-      if (lane == 0) {
-        a.mom[(size_t)s * 8 + kside * 2] = F;
-        a.mom[(size_t)s * 8 + kside * 2 + 1] = Pw;
+#pragma unroll
+      for (int qt = 0; qt < 2; ++qt) {
+        if (qt >= g.nq) break;
+        const double Fs = warp_sum(F[qt]), Ps = warp_sum(Pw[qt]);
+        if (lane == 0) {
+          a.mom[(((size_t)s * 4 + kside) * g.nq + qt) * 2] = Fs;
+          a.mom[(((size_t)s * 4 + kside) * g.nq + qt) * 2 + 1] = Ps;
+        }
       }
     }
   } else if (MODE == MODE_SCHWARZ) {
@@ -785,12 +806,12 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
     for (int k = tid; k < hgt * w * NR; k += nt) {
       const int r = k % NR, c = k / NR, J = c / w, x = c % w;
       if (active(g, b.ox + x, b.oy + J))
-        a.out[(size_t)r * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+        a.out[((size_t)r * g.nq + a.q) * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
     }
     // moments: 16 (side, function) pairs, one warp each
     for (int pr = wid; pr < 16; pr += nw) {
       const int kside = pr / 4, r = pr % 4;
-      double F = 0.0, Pw = 0.0;
+      double F[2] = {0.0, 0.0}, Pw[2] = {0.0, 0.0};  // against the test functions of degree 0, 1
       if (robin_side(g, s, kside)) {
         const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
@@ -798,18 +819,28 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
           double Tf, beta;
           gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
           const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
-          const double ph = a.in[(((size_t)s * 4 + r) * 4 + kside) * g.smax + t];
+          const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + kside) * g.smax + t];
           const double fl = tr * ((double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r] - ph);
           const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
-          F += fl;
-          Pw += area * ph + beta * fl;
+          const double pw = area * ph + beta * fl;
+#pragma unroll
+          for (int qt = 0; qt < 2; ++qt)
+            if (qt < g.nq) {
+              const double wt = side_fn(qt, t, len);
+              F[qt] += wt * fl;
+              Pw[qt] += wt * pw;
+            }
         }
       }
-      F = warp_sum(F);
-      Pw = warp_sum(Pw);
-      if (lane == 0) {
-        a.mom[(((size_t)s * 4 + kside) * 4 + r) * 2] = F;
-        a.mom[(((size_t)s * 4 + kside) * 4 + r) * 2 + 1] = Pw;
+      const int fn = r * g.nq + a.q;
+#pragma unroll
+      for (int qt = 0; qt < 2; ++qt) {
+        if (qt >= g.nq) break;
+        const double Fs = warp_sum(F[qt]), Ps = warp_sum(Pw[qt]);
+        if (lane == 0) {
+          a.mom[((((size_t)s * 4 + kside) * 4 * g.nq + fn) * g.nq + qt) * 2] = Fs;
+          a.mom[((((size_t)s * 4 + kside) * 4 * g.nq + fn) * g.nq + qt) * 2 + 1] = Ps;
+        }
       }
     }
   } else {  // MODE_INFORMED: phi_s^r on every Gamma face
@@ -831,7 +862,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
           const double area = k < 2 ? g.hy * g.hz : g.hx * g.hz;
           ph = -beta * F / area + pi;
         }
-        a.out[(((size_t)s * 4 + r) * 4 + k) * g.smax + f] = ph;
+        a.out[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + f] = ph;
       }
     }
   }
@@ -890,30 +921,35 @@ static cudaError_t launch_solve(const Geo& g, const SolveArgs& a, bool ohat, boo
   return fp32 ? launch_solve_t<float, MODE, NR>(g, a, ohat, st) : launch_solve_t<double, MODE, NR>(g, a, ohat, st);
 }
 
+// l = 0: the informed space is the side functions themselves, phi_s^{k,q} = degree-q function on side k
 __global__ void k_phi_indicator(Geo g, double* phi) {
   const int s = blockIdx.x;
-  for (int t = threadIdx.x; t < 16 * g.smax; t += blockDim.x) {
-    const int r = t / (4 * g.smax), k = (t / g.smax) % 4, f = t % g.smax;
+  const int per = 16 * g.nq * g.smax;
+  for (int t = threadIdx.x; t < per; t += blockDim.x) {
+    const int fn = t / (4 * g.smax), k = (t / g.smax) % 4, f = t % g.smax;
+    const int r = fn / g.nq, q = fn % g.nq;
     const int len = side_len(g, s, k);
     double v = 0.0;
-    if (r == k && f < len && robin_side(g, s, k)) v = 1.0;
-    phi[(size_t)s * 16 * g.smax + t] = v;
+    if (r == k && f < len && robin_side(g, s, k)) v = side_fn(q, f, len);
+    phi[(size_t)s * per + t] = v;
   }
 }
 
-cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int* flags, cudaStream_t st) {
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags,
+                            cudaStream_t st) {
   if (g.l == 0) {
+    if (q > 0) return cudaSuccess;  // one launch writes the functions of every degree
     k_phi_indicator<<<g.mx * g.my, 128, 0, st>>>(g, phi);
     count_launch(1);
     return cudaGetLastError();
   }
-  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags, -1};
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags, -1, q};
   return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
 }
 
-cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, double* psi,
+cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
                          double* mom, int* flags, cudaStream_t st) {
-  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags, -1};
+  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags, -1, q};
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 
@@ -933,7 +969,7 @@ cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, co
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 
-// z = psi0 + sum over Robin sides k of c_{s,k} psi_k   (reconstruction, per cell)
+// z = psi0 + sum over Robin sides k and degrees q of c_{s,k,q} psi_{k,q}   (reconstruction, per cell)
 __global__ void k_reconstruct(Geo g, const double* __restrict__ psi0, const double* __restrict__ psi,
                               const int* __restrict__ cidx, const double* __restrict__ c, double* __restrict__ z) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -946,7 +982,8 @@ __global__ void k_reconstruct(Geo g, const double* __restrict__ psi0, const doub
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int ci = cidx[s * 4 + k];
-    if (ci >= 0) v += c[ci] * psi[k * n + cell];
+    if (ci >= 0)
+      for (int q = 0; q < g.nq; ++q) v += c[(size_t)ci * g.nq + q] * psi[(size_t)(k * g.nq + q) * n + cell];
   }
   z[cell] = v;
 }

@@ -110,6 +110,7 @@ extern "C" mrcm_status mrcm_residual_norm_noalloc(mrcm_handle h, const double* b
   g.my = P.m[1];
   g.l = P.l;
   g.smax = h->lay.smax;
+  g.nq = P.nq;
   g.hx = h->h[0];
   g.hy = h->h[1];
   g.hz = h->h[2];

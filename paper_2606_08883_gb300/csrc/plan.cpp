@@ -36,6 +36,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   if (q.local_prec != MRCM_PREC_FP64 && q.local_prec != MRCM_PREC_FP32) return "local_prec must be FP64 or FP32";
   if (q.smooth_kind != MRCM_SMOOTH_ADDITIVE && q.smooth_kind != MRCM_SMOOTH_MULTIPLICATIVE)
     return "smooth_kind must be MRCM_SMOOTH_ADDITIVE or MRCM_SMOOTH_MULTIPLICATIVE";
+  if (q.iface_degree != 0 && q.iface_degree != 1) return "iface_degree must be 0 or 1";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
     if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";
@@ -51,6 +52,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
     P.m[a] = (p.n[a] + q.sub[a] - 1) / q.sub[a];
   }
   P.l = q.oversample;
+  P.nq = 1 + q.iface_degree * (p.dim - 1);
   P.S = P.m[0] * P.m[1] * P.m[2];
   const int S = P.S;
   P.box.assign(6 * S, 0);
@@ -98,20 +100,31 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
       }
   P.E = (int)P.iface.size() / 3;
   if (2 * P.E != P.E2) return "internal: coupling system is not square";
-  // banded home order and band widths of G
+  // a linear side function needs two faces on its side, else it vanishes there and G is singular
+  if (P.nq > 1)
+    for (int s = 0; s < S; ++s)
+      for (int k = 0; k < 2 * P.dim; ++k)
+        if (P.mask[s] >> k & 1)
+          for (int b = 0; b < P.dim; ++b)
+            if (b != k / 2 && P.box[6 * s + 3 + b] - P.box[6 * s + b] < 2)
+              return "iface_degree 1 needs at least two faces on every Robin side";
+  P.NC = P.E2 * P.nq;
+  // banded home order and band widths of G: row q of the flux (pressure) rows of interface e sits
+  // at unknown q of the side it is homed at, i.e. at row_home * nq + q
   P.row_home.assign(P.E2, 0);
   P.kl = P.ku = 0;
+  const int nq = P.nq;
   for (int e = 0; e < P.E; ++e) {
     const int a = P.iface[3 * e], s = P.iface[3 * e + 1], s2 = P.iface[3 * e + 2];
     const int rf = P.off[s] + P.rank[6 * s + 2 * a + 1];
     const int rp = P.off[s2] + P.rank[6 * s2 + 2 * a];
     P.row_home[2 * e] = rf;
     P.row_home[2 * e + 1] = rp;
-    for (int row : {rf, rp}) {
+    for (int row0 : {rf, rp}) {
       for (int t : {s, s2}) {
-        const int c0 = P.off[t], c1 = P.off[t] + P.N[t] - 1;
-        P.kl = std::max(P.kl, row - c0);
-        P.ku = std::max(P.ku, c1 - row);
+        const int c0 = P.off[t] * nq, c1 = (P.off[t] + P.N[t]) * nq - 1;
+        P.kl = std::max(P.kl, row0 * nq + nq - 1 - c0);
+        P.ku = std::max(P.ku, c1 - row0 * nq);
       }
     }
   }
@@ -180,7 +193,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.smax = std::max(P.sub[0], P.sub[1]);
   L.m = q.restart;
   L.nred = RED_BLOCKS;
-  const size_t E2 = P.E2;
+  const size_t E2 = P.E2, NC = P.NC, nq = P.nq;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -197,17 +210,17 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.Linv_loc = take(L.elt * S * box_stride(L.wl, L.hl, L.LSl));
   L.Linv_ohat_r = take(P.l > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
   L.Linv_ohat_d = take(q.smooth_steps > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
-  L.phi = take(8 * S * 16 * L.smax);
-  L.psi = take(8 * 4 * n);
-  L.mom = take(8 * S * 32);
+  L.phi = take(8 * S * 16 * nq * L.smax);
+  L.psi = take(8 * 4 * nq * n);
+  L.mom = take(8 * S * 32 * nq * nq);
   L.psi0 = take(8 * n);
   L.z0 = take(8 * n);
-  L.mom0 = take(8 * S * 8);
-  L.G = take(8 * (size_t)L.ldab * E2);
-  L.ipiv = take(4 * E2);
-  L.gc = take(8 * E2);
-  L.rdiag = take(8 * E2);
-  L.Ginv = take(E2 <= (size_t)COARSE_DENSE_MAX ? 8 * E2 * E2 : 0);
+  L.mom0 = take(8 * S * 8 * nq);
+  L.G = take(8 * (size_t)L.ldab * NC);
+  L.ipiv = take(4 * NC);
+  L.gc = take(8 * NC);
+  L.rdiag = take(8 * NC);
+  L.Ginv = take(NC <= (size_t)COARSE_DENSE_MAX ? 8 * NC * NC : 0);
   L.rho = take(8 * n);
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);

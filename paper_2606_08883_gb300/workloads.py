@@ -49,6 +49,7 @@ class Params:
     max_iter: int = 500
     local_prec: int = PREC_FP64
     smooth_kind: int = 0          # 0 additive, 1 multiplicative multicolour Schwarz sweeps
+    iface_degree: int = 0         # 0 piecewise-constant, 1 piecewise-linear side functions
 
 
 # ---------------------------------------------------------------------------------------------

@@ -52,7 +52,7 @@ def test_plan_export_matches_oracle_bit_exactly(lib, n, sub, l):
 
 @pytest.mark.parametrize("bad", [dict(sub=(5, 8, 1), oversample=4), dict(sub=(0, 8, 1)), dict(oversample=8), dict(oversample=-1), dict(alpha=0.0),
                                  dict(tol=-1.0), dict(restart=0), dict(max_iter=0), dict(local_prec=7),
-                                 dict(smooth_kind=2)])
+                                 dict(smooth_kind=2), dict(iface_degree=2), dict(iface_degree=-1)])
 def test_invalid_parameters_rejected(lib, bad):
     prob = W.random_problem((24, 16, 1), seed=0)
     kw = dict(sub=(8, 8, 1), oversample=2)
@@ -82,3 +82,13 @@ def test_footprint_grows_with_restart_and_smoothing(lib):
     params.smooth_steps = 0
     c = lib.footprint(prob, params)
     assert c < b
+
+
+def test_piecewise_linear_sides_need_two_faces(lib):
+    # 37 = 3 * 12 + 1: the last row of subdomains is one cell high, so its -x / +x Robin sides have
+    # one face and the linear side function vanishes there
+    prob = W.random_problem((50, 37, 1), seed=0)
+    lib.plan_export(prob, W.Params(sub=(16, 12, 1), oversample=0))
+    with pytest.raises(lib.MRCMError) as ei:
+        lib.plan_export(prob, W.Params(sub=(16, 12, 1), oversample=0, iface_degree=1))
+    assert ei.value.status == lib.MRCM_ERR_INVALID_ARG

@@ -33,7 +33,8 @@ def _rel(a, b):
 
 
 def _oracle(prob, q):
-    return MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha)
+    return MRCMOS(prob.K, prob.h, prob.dim, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha,
+                  q.iface_degree)
 
 
 CASES = {
@@ -82,42 +83,54 @@ def test_transmissibilities_rhs_operator(mrcm, name):
 
 
 def _phi_gpu_layout(pre, s_idx, smax):
-    """Oracle phi of subdomain s in the library layout [4 functions][4 sides][smax]."""
+    """Oracle phi of subdomain s in the library layout [4 nq functions][4 sides][smax], function
+    r nq + q the degree-q function of side r."""
     d = pre.subs[s_idx]
-    out = np.zeros((4, 4, smax))
-    for jj, (r, _q) in enumerate(d.funcs):
+    nq = pre.nq
+    out = np.zeros((4 * nq, 4, smax))
+    for jj, (r, qd) in enumerate(d.funcs):
         off = 0
         for k in d.sides:
             ln = int((d.gamma_side == k).sum())
-            out[r, k, :ln] = d.phi[jj, off:off + ln]
+            out[r * nq + qd, k, :ln] = d.phi[jj, off:off + ln]
             off += ln
     return out
 
 
-@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "stripes-128x64",
-                                  "uneven-61x45", "uneven-50x37-l0"])
-def test_informed_spaces_basis_moments_and_coupling_matrix(mrcm, name):
+# degree 1: piecewise-linear multiplier and test spaces on every Robin side (two functions a side)
+@pytest.mark.parametrize("name,degree", [("os-48x40", 0), ("os-96x64-l4s2", 0), ("ragged-60x36", 0),
+                                         ("mrcm-48x40", 0), ("stripes-128x64", 0), ("uneven-61x45", 0),
+                                         ("uneven-50x37-l0", 0), ("os-48x40", 1), ("ragged-60x36", 1),
+                                         ("mrcm-48x40", 1), ("uneven-61x45", 1)])
+def test_informed_spaces_basis_moments_and_coupling_matrix(mrcm, name, degree):
     prob, q = _case(name)
+    q.iface_degree = degree
     s = mrcm.Solver(prob, q)
     s.factor()
     pre = _oracle(prob, q)
     P = pre.part
+    nq = pre.nq
+    assert nq == 1 + degree
     smax = max(q.sub[0], q.sub[1])
-    phi = s.debug(mrcm.MRCM_DBG_PHI).reshape(P.S, 4, 4, smax)
-    psi = s.debug(mrcm.MRCM_DBG_PSI).reshape(4, -1)
-    mom = s.debug(mrcm.MRCM_DBG_MOMENTS).reshape(P.S, 4, 4, 2)
+    phi = s.debug(mrcm.MRCM_DBG_PHI).reshape(P.S, 4 * nq, 4, smax)
+    psi = s.debug(mrcm.MRCM_DBG_PSI).reshape(4 * nq, -1)
+    mom = s.debug(mrcm.MRCM_DBG_MOMENTS).reshape(P.S, 4, 4 * nq, nq, 2)
     ref_phi = np.stack([_phi_gpu_layout(pre, i, smax) for i in range(P.S)])
     assert _rel(phi, ref_phi) < 1e-11
     nx = prob.n[0]
     for d in pre.subs:
         lo, hi = P.box[d.s, 0], P.box[d.s, 1]
         cells = (np.arange(lo[1], hi[1])[:, None] * nx + np.arange(lo[0], hi[0])[None, :]).ravel()
-        for jj, (r, _q) in enumerate(d.funcs):
-            assert _rel(psi[r, cells], d.psi[:, jj]) < 1e-10
+        for jj, (r, qd) in enumerate(d.funcs):
+            fn = r * nq + qd
+            assert _rel(psi[fn, cells], d.psi[:, jj]) < 1e-10
             for k in d.sides:
-                assert np.isclose(mom[d.s, k, r, 0], d.Fbar[k, 0, jj], rtol=1e-9, atol=1e-12 * np.abs(d.Fbar).max())
-                assert np.isclose(mom[d.s, k, r, 1], d.Pbar[k, 0, jj], rtol=1e-9, atol=1e-12 * np.abs(d.Pbar).max())
-    G = s.debug(mrcm.MRCM_DBG_G).reshape(P.E2, P.E2)
+                for qt in range(nq):
+                    assert np.isclose(mom[d.s, k, fn, qt, 0], d.Fbar[k, qt, jj], rtol=1e-9,
+                                      atol=1e-12 * np.abs(d.Fbar).max())
+                    assert np.isclose(mom[d.s, k, fn, qt, 1], d.Pbar[k, qt, jj], rtol=1e-9,
+                                      atol=1e-12 * np.abs(d.Pbar).max())
+    G = s.debug(mrcm.MRCM_DBG_G).reshape(P.E2 * nq, P.E2 * nq)
     assert _rel(G, pre.G) < 1e-10
 
 
@@ -366,4 +379,54 @@ def test_banded_coupling_solve_above_the_dense_limit(mrcm):
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
     assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["os-48x40", "os-96x64-l4s2", "ragged-60x36", "mrcm-48x40", "dirichlet-all",
+                                  "uneven-61x45", "uneven-40x20-tall", "single-32"])
+def test_piecewise_linear_interface_spaces_match_oracle(mrcm, name):
+    prob, q = _case(name)
+    q.iface_degree = 1
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+    pre = _oracle(prob, q)
+    rng = np.random.default_rng(51)
+    for trial in range(2):
+        r = rng.standard_normal(prob.K.shape)
+        z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+        parts = pre.apply_parts(r)
+        if pre.part.E2:
+            assert _rel(s.debug(mrcm.MRCM_DBG_COARSE), parts["c"]) < 1e-9
+        assert _rel(s.debug(mrcm.MRCM_DBG_ZMRCM), parts["z_mrcm"]) < 1e-10
+        assert _rel(z, parts["z"]) < 1e-10, (name, trial, _rel(z, parts["z"]))
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["os-96x64-l4s2", "uneven-61x45"])
+def test_piecewise_linear_gmres_matches_oracle(mrcm, name):
+    prob, q = _case(name)
+    q.iface_degree, q.tol, q.restart = 1, 1e-9, 100
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve()
+    p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                      l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                      tol_relative=True, restart=q.restart, max_iter=q.max_iter, iface_degree=1)
+    assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    s.close()
+
+
+# the Robin parameter alpha of Eq. 6 enters beta = alpha H / K_H on every interface face
+@pytest.mark.parametrize("alpha,degree", [(0.5, 0), (3.0, 0), (100.0, 0), (3.0, 1)])
+def test_alpha_sweep_matches_oracle(mrcm, alpha, degree):
+    prob, q = _case("os-96x64-l4s2")
+    q.alpha, q.iface_degree = alpha, degree
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    pre = _oracle(prob, q)
+    r = np.random.default_rng(61).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    assert _rel(z, pre.apply(r)) < 1e-10
     s.close()
