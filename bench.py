@@ -435,10 +435,25 @@ def mrcm_arm(args):
         "setup_ms": setup_ms, "solve_ms": solve_ms,
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
         "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "autotuned": autotune_summary(),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def autotune_summary():
+    """The launch variants the library's autotuner chose during the warm-up (identical results)."""
+    from paper_2606_08883_gb300 import mrcm
+    out = []
+    for e in mrcm.autotune_table():
+        k = e["key"]
+        if e["kind"] == 0:
+            shape = f"local solve fp{8 * k[0]} mode {k[1]} x{k[2]} rhs, {k[3]}x{k[4]} boxes x{k[5]}"
+        else:
+            shape = f"coupling LU n={k[0]} kl={k[1]} ku={k[2]}"
+        out.append(f"{shape}: variant {e['choice'] + 1} of {e['ncand']}, {e['best_us']:.1f} us")
+    return out
 
 
 def serve_arm(args):

@@ -171,6 +171,21 @@ void mrcm_destroy(mrcm_handle h);
 const char* mrcm_status_string(mrcm_status s);
 const char* mrcm_last_error(mrcm_handle h);
 
+/* Launch-shape autotuning (no counterpart in the paper).  Some kernels have variants that compute
+ * identical results and differ only in how they stage data: the line-block ring depth of the local
+ * solves, and the cluster size of the coupling factorisation (16 or 8 CTAs, or one CTA).  While
+ * autotuning is on (the default), the first launch of a shape in the process times every variant
+ * that fits on the caller's data and stream (a few extra launches, synchronising the stream once)
+ * and keeps the fastest for every later launch of that shape, from any thread.
+ * mode: 0 off (every launch takes the built-in choice; the table is kept), 1 on, 2 forget the tuned
+ * shapes and turn on. */
+void mrcm_autotune(int32_t mode);
+/* The tuned shapes, 10 doubles each: kind (0 local solve, 1 coupling factorisation), six key fields
+ * (local solve: element bytes, solve mode, right-hand sides, box width, box height, boxes;
+ * factorisation: unknowns, kl, ku, 0, 0, 0), the chosen variant's index among the ncand that fit,
+ * ncand, and the chosen variant's time in microseconds.  buf (host) may be NULL to query *len. */
+mrcm_status mrcm_autotune_table(double* buf, size_t cap, size_t* len);
+
 /* Integer partition tables of MRCM-OS step 1, computed on the host without a GPU, as a flat int32
  * array: header {dim, n0, n1, n2, sub0, sub1, sub2, l, S, 2E, E}; per subdomain {box lo[3] hi[3],
  * oversampled box lo[3] hi[3] (clipped to the grid), Robin side mask, N_s, coarse offset}; per

@@ -14,7 +14,7 @@ OBJDIR = os.path.join(ROOT, "_build", "libmrcm")
 LIB = os.path.join(LIBDIR, "libmrcm.so")
 
 CUDA_SOURCES = ["api.cu", "k_grid.cu", "k_local.cu", "k_coarse.cu", "k_krylov.cu", "noalloc.cu"]
-CXX_SOURCES = ["plan.cpp", "server.cpp"]
+CXX_SOURCES = ["plan.cpp", "server.cpp", "tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

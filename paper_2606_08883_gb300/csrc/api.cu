@@ -181,6 +181,16 @@ void bc_ptrs(mrcm_handle h, const double* ptrs[4]) {
 
 extern "C" {
 
+void mrcm_autotune(int32_t mode) { mrcm::autotune_mode(mode); }
+
+mrcm_status mrcm_autotune_table(double* buf, size_t cap, size_t* len) {
+  if (!len) return MRCM_ERR_INVALID_ARG;
+  const std::vector<double> t = mrcm::autotune_table();
+  *len = t.size();
+  if (buf) std::memcpy(buf, t.data(), sizeof(double) * std::min(cap, t.size()));
+  return MRCM_OK;
+}
+
 const char* mrcm_status_string(mrcm_status s) {
   switch (s) {
     case MRCM_OK: return "ok";
@@ -335,7 +345,19 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
-    CK(h, launch_coarse_factor(c, flags, st));
+    // the factorisation variants give identical factors; the autotuner times each once per band
+    // shape (re-assembling G before every run, since the factorisation works in place)
+    int vars[4];
+    const int nv = coarse_factor_variants(c, vars);
+    const int key[6] = {c.n, c.kl, c.ku, 0, 0, 0};
+    cudaError_t terr = cudaSuccess;
+    const int pick = autotune(TUNE_COARSE_FACTOR, key, nv, st, [&](int i) {
+      const cudaError_t e = launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st);
+      return e != cudaSuccess ? e : launch_coarse_factor(c, flags, st, vars[i]);
+    }, &terr);
+    CK(h, terr);
+    if (pick >= 0) CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
+    CK(h, launch_coarse_factor(c, flags, st, pick >= 0 ? vars[pick] : -1));
     if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
   }
   // smoothing: Dirichlet factors of the oversampled regions

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -201,7 +202,9 @@ struct CoarseDev {
   const int* rank;  // [S][6]
 };
 cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st);
-cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st);
+// variant: see k_coarse.cu (-1: the first that runs); coarse_factor_variants lists those that run
+cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st, int variant = -1);
+int coarse_factor_variants(const CoarseDev& c, int* v);
 cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 // per apply without an explicit inverse: right-hand side from mom0, then the band solve
 cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
@@ -225,4 +228,14 @@ cudaError_t launch_update(double* p, const double* Z, size_t n, const double* H,
                           double* ybuf, cudaStream_t st);
 cudaError_t launch_residual_norm(const Geo& g, const double* b, const double* p, double* r, double* partials,
                                  unsigned* counter, double* out, cudaStream_t st);
+// Launch-shape autotuning (tune.cpp).  autotune() returns the index of the fastest of ncand
+// variants of shape (kind, key) -- timing them on the stream with run(i), which must give the same
+// result for every i and may be repeated -- or -1 for the caller's built-in choice (tuning off,
+// the shape being timed by another thread, or a stream under capture).
+int autotune(int kind, const int key[6], int ncand, cudaStream_t st, const std::function<cudaError_t(int)>& run,
+             cudaError_t* err);
+void autotune_mode(int mode);            // 0 off (built-in choices), 1 on, 2 forget the tuned shapes and turn on
+std::vector<double> autotune_table();    // per tuned shape: kind, key[6], choice, ncand, best us
+enum : int { TUNE_LOCAL_SOLVE = 0, TUNE_COARSE_FACTOR = 1 };
+
 }  // namespace mrcm

@@ -467,10 +467,10 @@ static size_t gbtrf_cluster_smem(const CoarseDev& c, int CL, int* NS) {
   return sizeof(double) * ((size_t)(*NS) * c.ldab + c.kl + 2);
 }
 
-// Launches the cluster factorisation with the largest cluster (16, else 8) that the device can
-// schedule with the ring in shared memory; returns false (nothing launched) when none fits.
-static bool launch_gbtrf_cluster(const CoarseDev& c, int* flags, cudaStream_t st, cudaError_t* err) {
-  *err = cudaSuccess;
+// Cluster launch configuration for the band LU: false when clusters of CL CTAs with the ring in
+// shared memory cannot be scheduled on this device.
+static bool gbtrf_cluster_config(const CoarseDev& c, int CL, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr,
+                                 int* NS) {
   if (c.kl > GBW_MAX_KL) return false;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -485,33 +485,47 @@ static bool launch_gbtrf_cluster(const CoarseDev& c, int* flags, cudaStream_t st
     }
     return 16;
   }();
-  for (int CL : {16, 8}) {
-    if (CL > max_cl) continue;
-    int NS = 0;
-    const size_t sm = gbtrf_cluster_smem(c, CL, &NS);
-    if (sm + static_smem > (size_t)optin) continue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(GBC_THREADS);
-    cfg.dynamicSmemBytes = sm;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_gbtrf_cluster, &cfg) != cudaSuccess || ncl < 1) {
-      cudaGetLastError();  // clear a refusal of this cluster size; try the next one
-      continue;
-    }
-    *err = cudaLaunchKernelEx(&cfg, k_gbtrf_cluster, c, flags, NS);
-    count_launch(1);
-    return true;
+  if (CL > max_cl) return false;
+  const size_t sm = gbtrf_cluster_smem(c, CL, NS);
+  if (sm + static_smem > (size_t)optin) return false;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(CL);
+  cfg->blockDim = dim3(GBC_THREADS);
+  cfg->dynamicSmemBytes = sm;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, k_gbtrf_cluster, cfg) != cudaSuccess || ncl < 1) {
+    cudaGetLastError();  // clear a refusal of this cluster size
+    return false;
   }
-  return false;
+  return true;
+}
+
+static size_t gbtf2_win_smem(const CoarseDev& c) { return sizeof(double) * (size_t)(c.kl + c.ku + 4) * c.ldab; }
+
+static bool gbtf2_win_fits(const CoarseDev& c) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t static_smem = sizeof(double) * 2 * (GBW_MAX_KL + 1) + 64;
+  return c.kl <= GBW_MAX_KL && gbtf2_win_smem(c) + static_smem <= (size_t)optin;
+}
+
+int coarse_factor_variants(const CoarseDev& c, int* v) {
+  int nv = 0;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  int NS = 0;
+  for (int CL : {16, 8})
+    if (gbtrf_cluster_config(c, CL, &cfg, attr, &NS)) v[nv++] = CL;
+  if (gbtf2_win_fits(c)) v[nv++] = 1;
+  if (nv == 0) v[nv++] = 0;
+  return nv;
 }
 
 // Columns of G^-1, one warp per column and no block barriers: the band entries of the next step
@@ -752,19 +766,30 @@ cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E,
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st) {
+// variant: 16 or 8, the cluster LU with that many CTAs; 1, the single-CTA window; 0, the
+// global-memory kernel; -1, the first of these that the device runs for this band.  All variants
+// take the same steps in the same order, so they give identical factors.
+cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st, int variant) {
   if (c.n == 0) return cudaSuccess;
-  cudaError_t ce = cudaSuccess;
-  if (launch_gbtrf_cluster(c, flags, st, &ce)) return ce != cudaSuccess ? ce : cudaGetLastError();
-  const size_t win = sizeof(double) * (size_t)(c.kl + c.ku + 4) * c.ldab;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t static_smem = sizeof(double) * 2 * (GBW_MAX_KL + 1) + 64;
-  if (c.kl <= GBW_MAX_KL && win + static_smem <= (size_t)optin) {
+  if (variant < 0) {
+    int v[4];
+    coarse_factor_variants(c, v);
+    variant = v[0];
+  }
+  if (variant >= 8) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    int NS = 0;
+    if (!gbtrf_cluster_config(c, variant, &cfg, attr, &NS)) return cudaErrorInvalidConfiguration;
+    cfg.stream = st;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gbtrf_cluster, c, flags, NS);
+    count_launch(1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  if (variant == 1) {
     const cudaError_t e = raise_smem_limit<k_gbtf2_win>();
     if (e != cudaSuccess) return e;
-    k_gbtf2_win<<<1, GBW_THREADS, win, st>>>(c, flags);
+    k_gbtf2_win<<<1, GBW_THREADS, gbtf2_win_smem(c), st>>>(c, flags);
   } else {
     k_gbtf2<<<1, 512, 0, st>>>(c, flags);
   }

@@ -893,27 +893,51 @@ static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, 
   return cudaGetLastError();
 }
 
-// Line blocks: FP32 solves keep the whole box resident when two CTAs still fit on an SM (their
-// steps are short, so a prefetch ring cannot run far enough ahead of memory latency), else eight
-// steps in flight; FP64
-// solves keep four steps in flight; fewer when they would not fit next to the right-hand sides, down
-// to one (no prefetch) for the widest boxes with four right-hand sides.
+// Line blocks: the built-in choice keeps the whole box resident for FP32 solves when two CTAs still
+// fit on an SM (their steps are short, so a prefetch ring cannot run far enough ahead of memory
+// latency), else eight steps in flight; FP64 solves keep four steps in flight; fewer when they would
+// not fit next to the right-hand sides, down to one (no prefetch) for the widest boxes with four
+// right-hand sides.  The depth changes no arithmetic, so the autotuner may replace that choice by
+// the fastest depth that fits, timed on the first launch of the shape; a sweep that updates in
+// place (one colour of a multiplicative sweep) is not repeatable and keeps the built-in choice.
+template <typename T, int MODE, int NR>
+static cudaError_t launch_solve_depth(const Geo& g, const SolveArgs& a, bool ohat, int nbuf, cudaStream_t st) {
+  switch (nbuf) {
+    case 0: return launch_solve_nb<T, MODE, NR, 0>(g, a, solve_smem<T, MODE, NR, 0>(g, a, ohat), ohat, st);
+    case 8: return launch_solve_nb<T, MODE, NR, 8>(g, a, solve_smem<T, MODE, NR, 8>(g, a, ohat), ohat, st);
+    case 4: return launch_solve_nb<T, MODE, NR, 4>(g, a, solve_smem<T, MODE, NR, 4>(g, a, ohat), ohat, st);
+    case 2: return launch_solve_nb<T, MODE, NR, 2>(g, a, solve_smem<T, MODE, NR, 2>(g, a, ohat), ohat, st);
+    default: return launch_solve_nb<T, MODE, NR, 1>(g, a, solve_smem<T, MODE, NR, 1>(g, a, ohat), ohat, st);
+  }
+}
+
 template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   constexpr size_t kMaxSmem = 227 * 1024;
   constexpr size_t kBudget = 100 * 1024;  // keep two CTAs per SM when possible
-  if (sizeof(T) == 4) {
-    // FP32 solves wait on memory, not on arithmetic: keep the whole box on chip when it fits
-    const size_t sm0 = solve_smem<T, MODE, NR, 0>(g, a, ohat);
-    if (sm0 <= kBudget + 14 * 1024) return launch_solve_nb<T, MODE, NR, 0>(g, a, sm0, ohat, st);
-    const size_t sm8 = solve_smem<T, MODE, NR, 8>(g, a, ohat);
-    if (sm8 <= kBudget) return launch_solve_nb<T, MODE, NR, 8>(g, a, sm8, ohat, st);
+  const size_t sm[5] = {solve_smem<T, MODE, NR, 0>(g, a, ohat), solve_smem<T, MODE, NR, 8>(g, a, ohat),
+                        solve_smem<T, MODE, NR, 4>(g, a, ohat), solve_smem<T, MODE, NR, 2>(g, a, ohat),
+                        solve_smem<T, MODE, NR, 1>(g, a, ohat)};
+  const int depth[5] = {0, 8, 4, 2, 1};
+  int builtin = 1;
+  if (sizeof(T) == 4 && sm[0] <= kBudget + 14 * 1024) builtin = 0;
+  else if (sizeof(T) == 4 && sm[1] <= kBudget) builtin = 8;
+  else if (sm[2] <= kMaxSmem) builtin = 4;
+  else if (sm[3] <= kMaxSmem) builtin = 2;
+  int cand[5], nc = 0;
+  for (int i = 0; i < 5; ++i)
+    if (sm[i] <= kMaxSmem) cand[nc++] = depth[i];
+  const bool repeatable = !(MODE == MODE_SCHWARZ && a.zin == a.out);
+  if (repeatable && nc > 1) {
+    const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
+    const int key[6] = {(int)sizeof(T), MODE, NR, w, h, a.colour >= 0 ? -1 - a.colour : g.mx * g.my};
+    cudaError_t err = cudaSuccess;
+    const int pick = autotune(TUNE_LOCAL_SOLVE, key, nc, st,
+                              [&](int i) { return launch_solve_depth<T, MODE, NR>(g, a, ohat, cand[i], st); }, &err);
+    if (err != cudaSuccess) return err;
+    if (pick >= 0) return launch_solve_depth<T, MODE, NR>(g, a, ohat, cand[pick], st);
   }
-  const size_t sm4 = solve_smem<T, MODE, NR, 4>(g, a, ohat);
-  if (sm4 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 4>(g, a, sm4, ohat, st);
-  const size_t sm2 = solve_smem<T, MODE, NR, 2>(g, a, ohat);
-  if (sm2 <= kMaxSmem) return launch_solve_nb<T, MODE, NR, 2>(g, a, sm2, ohat, st);
-  return launch_solve_nb<T, MODE, NR, 1>(g, a, solve_smem<T, MODE, NR, 1>(g, a, ohat), ohat, st);
+  return launch_solve_depth<T, MODE, NR>(g, a, ohat, builtin, st);
 }
 
 template <int MODE, int NR>

@@ -76,6 +76,8 @@ _SIGS = {
     "mrcm_server_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_size_t,
                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
     "mrcm_server_destroy": ([C.c_void_p], None),
+    "mrcm_autotune": ([C.c_int32], None),
+    "mrcm_autotune_table": ([C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
 }
 PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
           "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
@@ -86,6 +88,25 @@ for _name, (_args, _res) in _SIGS.items():
     globals()[_name] = _fn
 
 EXPORTED = tuple(_SIGS)
+
+
+def autotune(mode):
+    """0 off, 1 on (the default), 2 forget the tuned shapes and turn on."""
+    mrcm_autotune(int(mode))
+
+
+def autotune_table():
+    """The tuned launch shapes: list of dicts (kind, key, choice, ncand, best_us)."""
+    n = C.c_size_t()
+    _check(mrcm_autotune_table(None, 0, C.byref(n)))
+    buf = (C.c_double * max(n.value, 1))()
+    _check(mrcm_autotune_table(buf, n.value, C.byref(n)))
+    out = []
+    for i in range(0, n.value, 10):
+        e = buf[i:i + 10]
+        out.append({"kind": int(e[0]), "key": tuple(int(v) for v in e[1:7]), "choice": int(e[7]),
+                    "ncand": int(e[8]), "best_us": float(e[9])})
+    return out
 
 
 class MRCMError(RuntimeError):

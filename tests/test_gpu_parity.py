@@ -430,3 +430,29 @@ def test_alpha_sweep_matches_oracle(mrcm, alpha, degree):
     z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
     assert _rel(z, pre.apply(r)) < 1e-10
     s.close()
+
+
+def test_autotuned_launch_shapes_give_identical_results(mrcm):
+    # the tuned variants (line-block ring depth of the local solves, cluster size of the coupling
+    # factorisation) change how data is staged, never the arithmetic
+    prob, q = _case("os-96x64-l4s2")
+    q.restart = 100
+    r = torch.as_tensor(np.random.default_rng(71).standard_normal(prob.cells), device="cuda")
+    out = {}
+    try:
+        for mode in (0, 2):  # built-in choices, then freshly tuned shapes
+            mrcm.autotune(mode)
+            s = mrcm.Solver(prob, q)
+            s.factor()
+            z = s.apply_precond(r)
+            p, info = s.solve()
+            out[mode] = (z.clone(), p.clone(), info["iterations"])
+            s.close()
+    finally:
+        mrcm.autotune(1)
+    assert torch.equal(out[0][0], out[2][0]) and torch.equal(out[0][1], out[2][1]) and out[0][2] == out[2][2]
+    table = mrcm.autotune_table()
+    kinds = {e["kind"] for e in table}
+    assert {0, 1} <= kinds, table
+    for e in table:
+        assert 0 <= e["choice"] < e["ncand"] and e["ncand"] >= 2 and e["best_us"] > 0.0, e
