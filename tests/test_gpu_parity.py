@@ -456,3 +456,45 @@ def test_autotuned_launch_shapes_give_identical_results(mrcm):
     assert {0, 1} <= kinds, table
     for e in table:
         assert 0 <= e["choice"] < e["ncand"] and e["ncand"] >= 2 and e["best_us"] > 0.0, e
+
+
+def test_full_size_quarter_five_spot_64_matches_oracle(mrcm):
+    """The 64 x 64 quarter-five-spot workload (log-normal field, 4 x 4 subdomains of 16 x 16, l = 2,
+    one sweep, FP64) at its full size against the oracle: iterations equal, p and u to 1e-9."""
+    prob, q = W.quarter_five_spot(64, seed=1)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve(fluxes=True)
+    p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                      l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                      tol_relative=True, restart=q.restart, max_iter=q.max_iter)
+    assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-9
+    assert _rel(info["u"][0].cpu().numpy(), info_ref["u"][0]) < 1e-9
+    assert _rel(info["u"][1].cpu().numpy(), info_ref["u"][1]) < 1e-9
+    s.close()
+
+
+def test_full_size_lognormal_2048_mixed_precision(mrcm):
+    """The 2048 x 2048 log-normal workload (variance 4, correlation length 0.05, 64 x 64 subdomains of
+    32 x 32, l = 2; two sweeps, as one leaves GMRES stagnating on these fields) at full size, with
+    16,128 coupling unknowns on the band path.  Properties that hold at any size: the true FP64
+    residual of the returned p meets 1e-8 for FP64 and for FP32 local solves, and the mixed form
+    needs at most one iteration more than the FP64 one (whose counts equal the oracle's on every
+    case small enough to run it)."""
+    prob, q = W.lognormal(2048, seed=1)
+    q.smooth_steps, q.restart, q.max_iter = 2, 100, 300
+    T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    its = {}
+    for prec in (W.PREC_FP64, W.PREC_FP32):
+        q.local_prec = prec
+        s = mrcm.Solver(prob, q)
+        s.factor()
+        p, info = s.solve()
+        assert info["status"] == 0, (prec, info)
+        r = b - grid.matvec(T, p.cpu().numpy().reshape(prob.K.shape), 2)
+        assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(b), prec
+        its[prec] = info["iterations"]
+        s.close()
+    assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 1, its
