@@ -54,6 +54,14 @@ CASES = {
     "uneven-50x37-l0": (dict(n=(50, 37, 1), seed=11, bc_kind=[0, 1, 0, 1, 1, 1]),
                         dict(sub=(16, 12, 1), oversample=0, smooth_steps=1)),
     "uneven-40x20-tall": (dict(n=(40, 20, 1), seed=12), dict(sub=(16, 32, 1), oversample=2, smooth_steps=2)),
+    # one row / one column of subdomains (interfaces along one axis only), the largest oversampling
+    # a subdomain allows (l = sub - 1), and boxes of a few cells
+    "strip-96x12": (dict(n=(96, 12, 1), seed=13), dict(sub=(12, 12, 1), oversample=3, smooth_steps=1)),
+    "column-12x96": (dict(n=(12, 96, 1), seed=16, bc_kind=[1, 1, 0, 0, 1, 1]),
+                     dict(sub=(12, 16, 1), oversample=2, smooth_steps=1)),
+    "max-oversample-48": (dict(n=(48, 48, 1), seed=14), dict(sub=(8, 8, 1), oversample=7, smooth_steps=1)),
+    "tiny-boxes-8x8": (dict(n=(8, 8, 1), seed=15, bc_kind=[0, 0, 0, 0, 1, 1]),
+                       dict(sub=(4, 4, 1), oversample=1, smooth_steps=2)),
 }
 
 
@@ -498,3 +506,23 @@ def test_full_size_lognormal_2048_mixed_precision(mrcm):
         its[prec] = info["iterations"]
         s.close()
     assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 1, its
+
+
+@pytest.mark.parametrize("contrast", [1e6, 1e9])
+def test_high_contrast_matches_oracle_within_conditioning(mrcm, contrast):
+    # K spread over 6 and 9 decades: local condition numbers reach about contrast * (box size)^2,
+    # so the two elimination orders agree to eps times that, not to 1e-10
+    prob = W.random_problem((48, 40, 1), seed=17, contrast=contrast)
+    q = W.Params(sub=(8, 8, 1), oversample=2, smooth_steps=1, tol=1e-9, restart=100)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    pre = _oracle(prob, q)
+    r = np.random.default_rng(18).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    assert _rel(z, pre.apply(r)) < 1e-16 * contrast * 64 ** 2
+    p, info = s.solve()
+    T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    resid = b - grid.matvec(T, p.cpu().numpy().reshape(prob.K.shape), 2)
+    assert info["status"] == 0 and np.linalg.norm(resid) <= 1.0001e-9 * np.linalg.norm(b)
+    s.close()
