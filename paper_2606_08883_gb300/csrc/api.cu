@@ -126,6 +126,13 @@ CoarseDev coarse(mrcm_handle h) {
   c.ab = at<double>(h, h->lay.G);
   c.ipiv = at<int>(h, h->lay.ipiv);
   c.rdiag = at<double>(h, h->lay.rdiag);
+  c.nbk = P.NC > COARSE_DENSE_MAX ? (P.NC + GBB_NB - 1) / GBB_NB : 0;
+  c.ML = at<double>(h, h->lay.gbML);
+  c.MU = at<double>(h, h->lay.gbMU);
+  c.X = at<double>(h, h->lay.gbX);
+  c.Y = at<double>(h, h->lay.gbY);
+  c.F = at<double>(h, h->lay.gbF);
+  c.C = at<double>(h, h->lay.gbC);
   c.g = at<double>(h, h->lay.gc);
   c.iface = t.iface;
   c.home = t.home;
@@ -359,6 +366,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     if (pick >= 0) CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
     CK(h, launch_coarse_factor(c, flags, st, pick >= 0 ? vars[pick] : -1));
     if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
+    else CK(h, launch_coarse_blocks(c, st));
   }
   // smoothing: Dirichlet factors of the oversampled regions
   if (h->prm.smooth_steps > 0) {

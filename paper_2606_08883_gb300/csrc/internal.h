@@ -54,6 +54,7 @@ struct Layout {
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
   size_t rdiag;                           // reciprocals of the diagonal of U
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
+  size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
@@ -110,6 +111,7 @@ constexpr int ARNOLDI_MAX_BLOCKS = 1024;
 // then unsigned counters: [0] classic ticket, [1] barrier arrivals, [2] barrier generation
 constexpr size_t RED_DOUBLES = 8192;
 constexpr int COARSE_DENSE_MAX = 4096;   // 2E up to this size: explicit G^-1, one product per apply
+constexpr int GBB_NB = 512;              // above it: substitution steps per block of the blocked solve
 
 // flag word bits (device status)
 enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8 };
@@ -195,6 +197,12 @@ struct CoarseDev {
   double* ab;       // band LU storage, column-major, ldab x n
   int* ipiv;
   double* rdiag;    // 1 / U(j, j), written by the factorisation
+  // blocked substitution (2E nq > COARSE_DENSE_MAX): nbk blocks of GBB_NB steps; per block the dense
+  // transform of its L steps (window GBB_NB + kl) and of its U steps (window GBB_NB + kl + ku),
+  // column-major; padded vectors (kl + ku leading and kl trailing zeros); fresh-input products
+  // [nbk][GBB_NB + kl + ku]; carries entering each block [nbk][kl + ku]
+  int nbk;
+  double *ML, *MU, *X, *Y, *F, *C;
   double* g;        // rhs / solution (banded row order in, canonical unknowns out)
   const int* iface; // [E][3]
   const int* home;  // [2E] canonical row -> banded row
@@ -209,6 +217,8 @@ cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cud
 // per apply without an explicit inverse: right-hand side from mom0, then the band solve
 cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st);
+// set-up of the blocked substitution (2E nq > COARSE_DENSE_MAX), after the factorisation
+cudaError_t launch_coarse_blocks(const CoarseDev& c, cudaStream_t st);
 cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
                            double* sn, double* gv, double* out, double* wbuf, double* part, double* tot, double* Tm,

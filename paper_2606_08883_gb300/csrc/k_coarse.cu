@@ -738,6 +738,256 @@ __global__ void __launch_bounds__(GBS_THREADS) k_gbtrs_smem(CoarseDev c, const d
   for (int i = tid; i < n; i += NT) c.g[i] = b[i];
 }
 
+// ---- Blocked substitution (2E nq above the explicit-inverse limit) -----------------------------
+// The forward pass of the band solve (interchanges and L) and the backward pass (U) are each cut
+// into blocks of GBB_NB consecutive steps.  Block k's steps touch a window of W = GBB_NB + K rows
+// (K = kl for L, kl + ku for U) and act on it linearly, so at set-up each block's action is formed
+// as a dense W x W matrix by running its steps on the W unit vectors (one warp per column, the
+// same operations in the same order as a plain substitution).  Per apply, the part of every
+// block's output that comes from the rows no earlier block touches (its fresh rows) is a batch of
+// independent products; only the K rows that a block hands on to the next (its carry) form a
+// chain, one K x K product per block, run on one thread-block cluster.
+// Window positions: L block k covers rows k NB .. k NB + W - 1 with the carry in at [0, K), fresh
+// rows at [K, W), final rows at [0, NB) and the carry out at [NB, W); U block k covers rows
+// k NB - K .. k NB + NB - 1 with fresh rows at [0, NB), the carry in at [NB, W), the carry out at
+// [0, K) and final rows at [K, W).  Vectors hold kl + ku zero rows before row 0 (the rows below
+// the first U block) and kl after the last block.
+__global__ void __launch_bounds__(128) k_gbb_build(CoarseDev c, int upper) {
+  extern __shared__ double vsm[];  // [4 warps][W]
+  const int n = c.n, kl = c.kl, kv = c.kl + c.ku, ld = c.ldab;
+  const int K = upper ? kv : kl, W = GBB_NB + K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long gw = (long long)blockIdx.x * 4 + warp;
+  if (gw >= (long long)c.nbk * W) return;  // whole warps
+  const int k = (int)(gw / W), col = (int)(gw % W);
+  double* v = vsm + (size_t)warp * W;
+  for (int i = lane; i < W; i += 32) v[i] = i == col ? 1.0 : 0.0;
+  __syncwarp();
+  const double* __restrict__ ab = c.ab;
+  const int j0 = k * GBB_NB, j1 = min(j0 + GBB_NB, n);
+  if (!upper) {
+    for (int j = j0; j < j1; ++j) {
+      const int p = c.ipiv[j];
+      if (p != j) {
+        if (lane == 0) {
+          const double t = v[p - j0];
+          v[p - j0] = v[j - j0];
+          v[j - j0] = t;
+        }
+        __syncwarp();
+      }
+      const double bj = v[j - j0];
+      const int lm = min(kl, n - 1 - j);
+      if (bj != 0.0)
+        for (int i = 1 + lane; i <= lm; i += 32) v[j - j0 + i] -= ab[(size_t)(kv + i) + (size_t)j * ld] * bj;
+      __syncwarp();
+    }
+  } else {
+    const int base = j0 - kv;  // the row at window position 0
+    for (int j = j1 - 1; j >= j0; --j) {
+      if (lane == 0) v[j - base] *= c.rdiag[j];
+      __syncwarp();
+      const double bj = v[j - base];
+      if (bj != 0.0)
+        for (int i = max(0, j - kv) + lane; i < j; i += 32) v[i - base] -= ab[(size_t)(kv + i - j) + (size_t)j * ld] * bj;
+      __syncwarp();
+    }
+  }
+  double* M = (upper ? c.MU : c.ML) + (size_t)k * W * W + (size_t)col * W;
+  for (int i = lane; i < W; i += 32) M[i] = v[i];
+}
+
+// The right-hand side of the coupling rows into the padded forward-pass input.
+__global__ void k_gbb_rhs(CoarseDev c, const double* __restrict__ mom0, int E) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * c.nq) return;
+  int rf, rp;
+  double gf, gp;
+  coarse_rhs_rows(c, mom0, t / c.nq, t % c.nq, rf, gf, rp, gp);
+  const int pad = c.kl + c.ku;
+  c.X[pad + rf] = gf;
+  c.X[pad + rp] = gp;
+}
+
+// F_k = M_k[:, fresh] (fresh rows of `in`) for every block k: blockIdx.x = k, blockIdx.y = 128
+// window rows; the two halves of the CTA take alternate fresh columns.
+__global__ void __launch_bounds__(256) k_gbb_fresh(CoarseDev c, int upper, const double* __restrict__ in) {
+  __shared__ double fr[GBB_NB];
+  __shared__ double part[256];
+  const int kv = c.kl + c.ku, K = upper ? kv : c.kl, W = GBB_NB + K;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const int f0 = upper ? 0 : K;                              // window position of the first fresh row
+  const int row0 = upper ? k * GBB_NB - kv : k * GBB_NB;     // the row at window position 0
+  for (int t = tid; t < GBB_NB; t += 256) fr[t] = in[(size_t)kv + row0 + f0 + t];
+  __syncthreads();
+  const int r = blockIdx.y * 128 + (tid & 127), half = tid >> 7;
+  const double* __restrict__ M = (upper ? c.MU : c.ML) + (size_t)k * W * W;
+  double acc = 0.0;
+  if (r < W)
+    for (int t = half; t < GBB_NB; t += 2) acc += M[(size_t)(f0 + t) * W + r] * fr[t];
+  part[tid] = acc;
+  __syncthreads();
+  if (tid < 128 && r < W) c.F[(size_t)k * (GBB_NB + kv) + r] = part[tid] + part[tid + 128];
+}
+
+// The chain of carries: block after block (forward for L, backward for U), carry_out = M_k[carry
+// out, carry in] carry_in + F_k[carry out].  CTA q of the cluster forms rows [q K / CL, (q+1) K / CL)
+// (at most 64) and writes them into every CTA's copy of the next carry; one cluster barrier per
+// block.  The carry entering each block is kept in C for the final rows.
+__global__ void __launch_bounds__(256, 1) k_gbb_chain(CoarseDev c, int upper, const double* __restrict__ in) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double csm[];  // [2][K] carries, then [8][64] partial sums
+  const int kv = c.kl + c.ku, K = upper ? kv : c.kl, W = GBB_NB + K, nbk = c.nbk;
+  const int CL = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = (int)((long long)rank * K / CL), r1 = (int)((long long)(rank + 1) * K / CL), nr = r1 - r0;
+  double* cur = csm;
+  double* nxt = csm + K;
+  double* part = csm + 2 * K;
+  const int cin = upper ? GBB_NB : 0, cout = upper ? 0 : GBB_NB;
+  // the carry entering the first block holds rows that no block has touched
+  const int crow = upper ? (nbk - 1) * GBB_NB - kv + GBB_NB : 0;
+  for (int i = tid; i < K; i += 256) cur[i] = in[(size_t)kv + crow + i];
+  __syncthreads();
+  const int t0 = (int)((long long)warp * K / 8), t1 = (int)((long long)(warp + 1) * K / 8);
+  for (int h = 0; h < nbk; ++h) {
+    const int k = upper ? nbk - 1 - h : h;
+    for (int i = r0 + tid; i < r1; i += 256) c.C[(size_t)k * kv + i] = cur[i];
+    if (h + 1 < nbk) {
+      const double* __restrict__ M = (upper ? c.MU : c.ML) + (size_t)k * W * W + cout + r0;
+      double a0 = 0.0, a1 = 0.0;
+      for (int t = t0; t < t1; ++t) {
+        const double x = cur[t];
+        const double* Mc = M + (size_t)(cin + t) * W;
+        if (lane < nr) a0 += Mc[lane] * x;
+        if (lane + 32 < nr) a1 += Mc[lane + 32] * x;
+      }
+      part[warp * 64 + lane] = a0;
+      part[warp * 64 + lane + 32] = a1;
+      __syncthreads();
+      if (tid < nr) {
+        double sum = c.F[(size_t)k * (GBB_NB + kv) + cout + r0 + tid];
+        for (int w8 = 0; w8 < 8; ++w8) sum += part[w8 * 64 + tid];
+        for (int q = 0; q < CL; ++q) *cl.map_shared_rank(&nxt[r0 + tid], q) = sum;
+      }
+    }
+    cl.sync();  // the next carry is complete in every CTA, and nobody still reads this one
+    double* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+// Final rows of every block: M_k[final, carry in] C_k + F_k[final], written to `out` (padded
+// vector) or, for the last pass, to the solution.  blockIdx.x = k, blockIdx.y = 128 final rows.
+__global__ void __launch_bounds__(256) k_gbb_final(CoarseDev c, int upper, double* __restrict__ out) {
+  extern __shared__ double cr[];  // [K] carry entering block k
+  __shared__ double part[256];
+  const int n = c.n, kv = c.kl + c.ku, K = upper ? kv : c.kl, W = GBB_NB + K;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const int cin = upper ? GBB_NB : 0, fin = upper ? K : 0;
+  for (int j = tid; j < K; j += 256) cr[j] = c.C[(size_t)k * kv + j];
+  __syncthreads();
+  const int r = blockIdx.y * 128 + (tid & 127), half = tid >> 7;
+  const double* __restrict__ M = (upper ? c.MU : c.ML) + (size_t)k * W * W;
+  double acc = 0.0;
+  if (r < GBB_NB)
+    for (int j = half; j < K; j += 2) acc += M[(size_t)(cin + j) * W + fin + r] * cr[j];
+  part[tid] = acc;
+  __syncthreads();
+  if (tid < 128 && r < GBB_NB) {
+    const double v = part[tid] + part[tid + 128] + c.F[(size_t)k * (GBB_NB + kv) + fin + r];
+    const int row = k * GBB_NB + r;
+    if (upper) {
+      if (row < n) c.g[row] = v;
+    } else {
+      out[(size_t)kv + row] = v;
+    }
+  }
+}
+
+static bool gbb_chain_config(const CoarseDev& c, int K, int CL, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  if (K > 64 * CL) return false;
+  static const int max_cl = [] {
+    if (cudaFuncSetAttribute(k_gbb_chain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return 8;
+    }
+    return 16;
+  }();
+  if (CL > max_cl) return false;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(CL);
+  cfg->blockDim = dim3(256);
+  cfg->dynamicSmemBytes = sizeof(double) * (2 * (size_t)K + 8 * 64);
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int ncl = 0;
+  if (cudaOccupancyMaxActiveClusters(&ncl, k_gbb_chain, cfg) != cudaSuccess || ncl < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// Whether the blocked substitution can run for this band (a chain cluster that holds the carry).
+static bool gbb_usable(const CoarseDev& c) {
+  if (c.nbk <= 0) return false;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  const int kv = c.kl + c.ku;
+  return gbb_chain_config(c, kv, 16, &cfg, attr) || gbb_chain_config(c, kv, 8, &cfg, attr);
+}
+
+cudaError_t launch_coarse_blocks(const CoarseDev& c, cudaStream_t st) {
+  if (!gbb_usable(c)) return cudaSuccess;  // the per-apply band solve is used instead
+  const int kv = c.kl + c.ku;
+  const size_t nvec = (size_t)kv + (size_t)c.nbk * GBB_NB + c.kl;
+  cudaError_t e = raise_smem_limit<k_gbb_build>();
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.X, 0, sizeof(double) * nvec, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.Y, 0, sizeof(double) * nvec, st);
+  if (e != cudaSuccess) return e;
+  for (int upper = 0; upper < 2; ++upper) {
+    const int W = GBB_NB + (upper ? kv : c.kl);
+    const long long warps = (long long)c.nbk * W;
+    k_gbb_build<<<(unsigned)((warps + 3) / 4), 128, sizeof(double) * 4 * (size_t)W, st>>>(c, upper);
+    count_launch(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t launch_gbb_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st) {
+  const int kv = c.kl + c.ku;
+  k_gbb_rhs<<<(E * c.nq + 127) / 128, 128, 0, st>>>(c, mom0, E);
+  count_launch(1);
+  cudaError_t e = cudaGetLastError();
+  for (int upper = 0; upper < 2 && e == cudaSuccess; ++upper) {
+    const int K = upper ? kv : c.kl, W = GBB_NB + K;
+    const double* in = upper ? c.Y : c.X;
+    k_gbb_fresh<<<dim3(c.nbk, (W + 127) / 128), 256, 0, st>>>(c, upper, in);
+    count_launch(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (!gbb_chain_config(c, K, 16, &cfg, attr) && !gbb_chain_config(c, K, 8, &cfg, attr))
+      return cudaErrorInvalidConfiguration;
+    cfg.stream = st;
+    e = cudaLaunchKernelEx(&cfg, k_gbb_chain, c, upper, in);
+    count_launch(1);
+    if (e != cudaSuccess) break;
+    k_gbb_final<<<dim3(c.nbk, (GBB_NB + 127) / 128), 256, sizeof(double) * (size_t)K, st>>>(c, upper, c.Y);
+    count_launch(1);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
   const size_t sm4 = sizeof(double) * 4 * (size_t)c.n;
@@ -806,6 +1056,7 @@ cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cud
 
 cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
+  if (gbb_usable(c)) return launch_gbb_solve(c, mom0, E, st);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

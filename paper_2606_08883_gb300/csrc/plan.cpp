@@ -221,6 +221,17 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.gc = take(8 * NC);
   L.rdiag = take(8 * NC);
   L.Ginv = take(NC <= (size_t)COARSE_DENSE_MAX ? 8 * NC * NC : 0);
+  {
+    const bool blocked = NC > (size_t)COARSE_DENSE_MAX;
+    const size_t kv = (size_t)P.kl + P.ku, nbk = blocked ? (NC + GBB_NB - 1) / GBB_NB : 0;
+    const size_t WL = GBB_NB + P.kl, WU = GBB_NB + kv, nvec = kv + nbk * GBB_NB + P.kl;
+    L.gbML = take(8 * nbk * WL * WL);
+    L.gbMU = take(8 * nbk * WU * WU);
+    L.gbX = take(blocked ? 8 * nvec : 0);
+    L.gbY = take(blocked ? 8 * nvec : 0);
+    L.gbF = take(8 * nbk * WU);
+    L.gbC = take(8 * nbk * kv);
+  }
   L.rho = take(8 * n);
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);
