@@ -30,6 +30,18 @@ def _mix():
     prob, q = W.lognormal(96, seed=6, variance=1.0, corr=0.1, sub=16, oversample=2, smooth_steps=1, prec=W.PREC_FP64)
     q.restart = 120
     out.append((prob, q))
+    # the variants: a diagonal permeability tensor, piecewise-linear interface spaces, a grid the
+    # subdomain size does not divide, multiplicative smoothing
+    out.append((W.random_problem((96, 64, 1), seed=21, contrast=1e3, tensor=True),
+                W.Params(sub=(16, 16, 1), oversample=2, smooth_steps=2, restart=100)))
+    prob, q = W.channels(128, seed=7, sub=32, oversample=4, smooth_steps=2)
+    q.iface_degree = 1
+    out.append((prob, q))
+    out.append((W.random_problem((100, 70, 1), seed=22, contrast=1e3),
+                W.Params(sub=(32, 32, 1), oversample=2, smooth_steps=1, restart=100)))
+    prob, q = W.quarter_five_spot(64, seed=8)
+    q.smooth_kind = 1
+    out.append((prob, q))
     return out
 
 
