@@ -8,6 +8,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace mrcm;
@@ -25,13 +27,21 @@ void set_thread_error(const std::string& msg) { g_last_error = msg; }
 
 namespace {
 
-// Phase brackets: a (start, stop) event pair per kernel group while profiling is enabled.
+// NVTX range names of the phases (for profilers; without one attached a range is a no-op)
+const char* const kPhaseName[MRCM_PHASES] = {
+    "mrcm assemble", "mrcm factor ohat robin", "mrcm informed spaces", "mrcm factor omega", "mrcm basis",
+    "mrcm coupling factor", "mrcm factor ohat dirichlet", "mrcm particular", "mrcm coupling solve",
+    "mrcm reconstruct", "mrcm residual", "mrcm schwarz", "mrcm krylov"};
+
+// Phase brackets: an NVTX range always, and a (start, stop) event pair per kernel group while
+// profiling is enabled.
 struct Phase {
   mrcm_handle h;
   int ph;
   cudaStream_t st;
   long long l0;
   Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
+    nvtxRangePushA(kPhaseName[ph]);
     if (!h->prof) return;
     const size_t need = 2 * (h->ev_used + 1);
     while (h->ev_pool.size() < need) {
@@ -47,6 +57,7 @@ struct Phase {
     cudaEventRecord(h->ev_pool[2 * h->ev_used], st);
   }
   ~Phase() {
+    nvtxRangePop();
     if (!h->prof) return;
     cudaEventRecord(h->ev_pool[2 * h->ev_used + 1], st);
     h->ph_launch[ph] += g_launches.load() - l0;

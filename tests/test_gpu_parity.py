@@ -526,3 +526,35 @@ def test_high_contrast_matches_oracle_within_conditioning(mrcm, contrast):
     resid = b - grid.matvec(T, p.cpu().numpy().reshape(prob.K.shape), 2)
     assert info["status"] == 0 and np.linalg.norm(resid) <= 1.0001e-9 * np.linalg.norm(b)
     s.close()
+
+
+# the mixed form on the variants: FP32 local factors and solves, FP64 GMRES and true residual;
+# the criterion is the FP64 tolerance reached in at most one iteration more than the FP64 form
+@pytest.mark.parametrize("variant", ["uneven", "degree1", "tensor", "multiplicative", "alpha3"])
+def test_mixed_precision_variants_reach_fp64_tolerance(mrcm, variant):
+    if variant == "tensor":
+        prob, q = _tensor_case("tensor-ragged-60x36")
+    else:
+        prob, q = _case("uneven-61x45" if variant == "uneven" else "os-96x64-l4s2")
+        q.restart = 100
+    q.tol = 1e-8
+    if variant == "degree1":
+        q.iface_degree = 1
+    if variant == "multiplicative":
+        q.smooth_kind = 1
+    if variant == "alpha3":
+        q.alpha = 3.0
+    T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    its = {}
+    for prec in (W.PREC_FP64, W.PREC_FP32):
+        q.local_prec = prec
+        s = mrcm.Solver(prob, q)
+        s.factor()
+        p, info = s.solve()
+        assert info["status"] == 0, (variant, prec)
+        r = b - grid.matvec(T, p.cpu().numpy().reshape(grid.cell_shape(prob.K)), 2)
+        assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(b), (variant, prec)
+        its[prec] = info["iterations"]
+        s.close()
+    assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 1, (variant, its)
