@@ -284,6 +284,37 @@ def roofline(prof, prob, q, prec, peaks, iterations):
                                   "nominal GB300 dense FP64 1.25 TFLOP/s at 2070 MHz")}
 
 
+def phase_rooflines(prof, prob, q, prec, peaks, iterations):
+    """Every modelled phase against its bound, from the event-timed launch durations: the local
+    factorisations and FP64 solves and the Arnoldi step against the FP64 (or FP32) pipe, the FP32
+    solves, the residual, the reconstruction and the dense coupling product against HBM."""
+    model = phase_model(prob, q, prec)
+    model["krylov"] = krylov_model(prob.cells, iterations, q.restart)
+    nc = 2 * ((prob.n[0] // q.sub[0]) * (prob.n[1] // q.sub[1] - 1) + (prob.n[1] // q.sub[1]) * (prob.n[0] // q.sub[0] - 1))
+    nc *= 1 + getattr(q, "iface_degree", 0)
+    if nc <= 4096:  # one product with the explicit G^-1 per apply
+        model["coarse_solve"] = (2 * nc * nc, 8 * nc * nc)
+    out = {}
+    for name, (flops, nbytes) in model.items():
+        ms, launches = prof.get(name, (0.0, 0))
+        if launches <= 0 or ms <= 0.0:
+            continue
+        per = ms / 1e3 / launches
+        mem = name in ("residual", "reconstruct", "coarse_solve") or (
+            prec == "fp32" and name in ("schwarz", "particular", "informed", "basis"))
+        if mem:
+            peak = peaks.get("hbm_gbs", 6800.0)
+            ach = nbytes / per / 1e9
+            out[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 3), "launch_ms": round(per * 1e3, 4)}
+        else:
+            peak = NOMINAL_FP32_TFLOPS if (prec == "fp32" and name.startswith("factor")) else NOMINAL_FP64_TFLOPS
+            ach = flops / per / 1e12
+            out[name] = {"bound": "alu", "achieved": round(ach, 4), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(ach / peak, 3), "launch_ms": round(per * 1e3, 4)}
+    return out
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -417,6 +448,7 @@ def mrcm_arm(args):
         return
     peaks = load_peaks()
     dom, roof = roofline(prof, prob, q, args.prec, peaks, statistics.median(iters))
+    per_phase = phase_rooflines(prof, prob, q, args.prec, peaks, statistics.median(iters))
     lat = sorted(times)
     cpu_line = None
     if cpu is not None and "error" not in cpu:
@@ -435,7 +467,7 @@ def mrcm_arm(args):
         "setup_ms": setup_ms, "solve_ms": solve_ms,
         "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
         "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-        "autotuned": autotune_summary(),
+        "autotuned": autotune_summary(), "phase_rooflines": per_phase,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

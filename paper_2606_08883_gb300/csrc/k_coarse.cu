@@ -907,31 +907,41 @@ __global__ void __launch_bounds__(256) k_gbb_final(CoarseDev c, int upper, doubl
   }
 }
 
-static bool gbb_chain_config(const CoarseDev& c, int K, int CL, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+// Launch configuration of the carry chain on a cluster of CL CTAs; false when the carry does not fit
+// CL CTAs of at most 64 rows each, or when the device cannot schedule such a cluster (checked once
+// per cluster size, with the largest shared-memory request).
+static bool gbb_chain_config(int K, int CL, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
   if (K > 64 * CL) return false;
-  static const int max_cl = [] {
-    if (cudaFuncSetAttribute(k_gbb_chain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      return 8;
+  auto fill = [](int cl, size_t smem, cudaLaunchConfig_t* f, cudaLaunchAttribute* at) {
+    *f = cudaLaunchConfig_t{};
+    f->gridDim = dim3(cl);
+    f->blockDim = dim3(256);
+    f->dynamicSmemBytes = smem;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    f->attrs = at;
+    f->numAttrs = 1;
+  };
+  // bit CL / 8 - 1: clusters of CL (8 or 16) chain CTAs can be scheduled
+  static const int schedulable = [&fill] {
+    int bits = 0;
+    const bool big = cudaFuncSetAttribute(k_gbb_chain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    if (!big) cudaGetLastError();
+    for (int cl : {8, 16}) {
+      if (cl == 16 && !big) continue;
+      cudaLaunchConfig_t f;
+      cudaLaunchAttribute at[1];
+      fill(cl, sizeof(double) * (2 * 64 * (size_t)cl + 8 * 64), &f, at);
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_gbb_chain, &f) == cudaSuccess && ncl >= 1) bits |= 1 << (cl / 8 - 1);
+      else cudaGetLastError();
     }
-    return 16;
+    return bits;
   }();
-  if (CL > max_cl) return false;
-  *cfg = cudaLaunchConfig_t{};
-  cfg->gridDim = dim3(CL);
-  cfg->blockDim = dim3(256);
-  cfg->dynamicSmemBytes = sizeof(double) * (2 * (size_t)K + 8 * 64);
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg->attrs = attr;
-  cfg->numAttrs = 1;
-  int ncl = 0;
-  if (cudaOccupancyMaxActiveClusters(&ncl, k_gbb_chain, cfg) != cudaSuccess || ncl < 1) {
-    cudaGetLastError();
-    return false;
-  }
+  if (!(schedulable >> (CL / 8 - 1) & 1)) return false;
+  fill(CL, sizeof(double) * (2 * (size_t)K + 8 * 64), cfg, attr);
   return true;
 }
 
@@ -941,7 +951,7 @@ static bool gbb_usable(const CoarseDev& c) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   const int kv = c.kl + c.ku;
-  return gbb_chain_config(c, kv, 16, &cfg, attr) || gbb_chain_config(c, kv, 8, &cfg, attr);
+  return gbb_chain_config(kv, 16, &cfg, attr) || gbb_chain_config(kv, 8, &cfg, attr);
 }
 
 cudaError_t launch_coarse_blocks(const CoarseDev& c, cudaStream_t st) {
@@ -975,7 +985,7 @@ static cudaError_t launch_gbb_solve(const CoarseDev& c, const double* mom0, int 
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    if (!gbb_chain_config(c, K, 16, &cfg, attr) && !gbb_chain_config(c, K, 8, &cfg, attr))
+    if (!gbb_chain_config(K, 16, &cfg, attr) && !gbb_chain_config(K, 8, &cfg, attr))
       return cudaErrorInvalidConfiguration;
     cfg.stream = st;
     e = cudaLaunchKernelEx(&cfg, k_gbb_chain, c, upper, in);
