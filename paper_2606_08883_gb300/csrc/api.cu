@@ -40,6 +40,7 @@ struct Phase {
   int ph;
   cudaStream_t st;
   long long l0;
+  long long slot = -1;  // this phase's event pair (reserved at construction, so phases may nest)
   Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
     nvtxRangePushA(kPhaseName[ph]);
     if (!h->prof) return;
@@ -53,15 +54,15 @@ struct Phase {
       h->ev_pool.push_back(e);
     }
     if (h->ev_phase.size() < h->ev_used + 1) h->ev_phase.resize(h->ev_used + 1);
-    h->ev_phase[h->ev_used] = ph;
-    cudaEventRecord(h->ev_pool[2 * h->ev_used], st);
+    slot = (long long)h->ev_used++;
+    h->ev_phase[slot] = ph;
+    cudaEventRecord(h->ev_pool[2 * slot], st);
   }
   ~Phase() {
     nvtxRangePop();
-    if (!h->prof) return;
-    cudaEventRecord(h->ev_pool[2 * h->ev_used + 1], st);
+    if (slot < 0) return;
+    cudaEventRecord(h->ev_pool[2 * slot + 1], st);
     h->ph_launch[ph] += g_launches.load() - l0;
-    h->ev_used++;
   }
 };
 
@@ -360,6 +361,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   }
   // coupling system (Eq. 13-14)
   CoarseDev c = coarse(h);
+  bool forked = false;
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
@@ -375,14 +377,33 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     }, &terr);
     CK(h, terr);
     if (pick >= 0) CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
+    // The Dirichlet factors of the oversampled regions (smoothing, MRCM-OS step 4) depend only on
+    // A: they run on a second stream alongside the coupling factorisation (one cluster, most SMs
+    // free), forked just before it, and the caller's stream waits for them at the end.
+    if (h->prm.smooth_steps > 0) {
+      if (!h->side) {
+        CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+      }
+      CK(h, cudaEventRecord(h->fork_ev, st));
+      CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+      forked = true;
+    }
     CK(h, launch_coarse_factor(c, flags, st, pick >= 0 ? vars[pick] : -1));
+  }
+  if (forked) {
+    Phase ph(h, MRCM_PH_FACTOR_OHAT_DIRICHLET, h->side);
+    CK(h, launch_factor(g, BOX_OHAT_DIRICHLET, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_d), fp32, flags, h->side));
+  }
+  {
+    Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
     else CK(h, launch_coarse_blocks(c, st));
   }
-  // smoothing: Dirichlet factors of the oversampled regions
-  if (h->prm.smooth_steps > 0) {
-    Phase ph(h, MRCM_PH_FACTOR_OHAT_DIRICHLET, st);
-    CK(h, launch_factor(g, BOX_OHAT_DIRICHLET, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_d), fp32, flags, st));
+  if (forked) {
+    CK(h, cudaEventRecord(h->join_ev, h->side));
+    CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   }
   int hf = 0;
   CK(h, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));

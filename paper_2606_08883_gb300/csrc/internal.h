@@ -154,7 +154,13 @@ struct mrcm_ctx {
   };
   StepReadback* rb = nullptr;
   cudaEvent_t rb_ev[2] = {nullptr, nullptr};
+  // second stream for set-up work that overlaps (the Schwarz factors), with its fork / join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   ~mrcm_ctx() {
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : rb_ev)
       if (e) cudaEventDestroy(e);
