@@ -92,3 +92,28 @@ def test_piecewise_linear_sides_need_two_faces(lib):
     with pytest.raises(lib.MRCMError) as ei:
         lib.plan_export(prob, W.Params(sub=(16, 12, 1), oversample=0, iface_degree=1))
     assert ei.value.status == lib.MRCM_ERR_INVALID_ARG
+
+
+def test_plan_export_matches_oracle_on_random_partitions(lib):
+    # random grids, subdomain sizes (dividing or not) and oversampling widths: the host planner's
+    # integer tables equal the oracle's bit for bit, and both reject the same invalid inputs
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(nx=st.integers(1, 40), ny=st.integers(1, 40), sx=st.integers(1, 16), sy=st.integers(1, 16),
+               l=st.integers(0, 6))
+    def check(nx, ny, sx, sy, l):
+        prob = W.random_problem((nx, ny, 1), seed=0)
+        q = W.Params(sub=(sx, sy, 1), oversample=l)
+        try:
+            want = Partition(2, (nx, ny, 1), (sx, sy, 1), l).export()
+        except ValueError:
+            with pytest.raises(lib.MRCMError) as ei:
+                lib.plan_export(prob, q)
+            assert ei.value.status == lib.MRCM_ERR_INVALID_ARG
+            return
+        got = lib.plan_export(prob, q)
+        assert got.dtype == want.dtype and np.array_equal(got, want)
+
+    check()
