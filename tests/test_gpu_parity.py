@@ -558,3 +558,21 @@ def test_mixed_precision_variants_reach_fp64_tolerance(mrcm, variant):
         its[prec] = info["iterations"]
         s.close()
     assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 1, (variant, its)
+
+
+def test_banded_coupling_solve_degree1_above_the_dense_limit(mrcm):
+    # piecewise-linear spaces on the 44 x 44 partition: 15,136 coupling unknowns with twice the band
+    # width, so the blocked substitution carries about 700 rows from block to block
+    prob = W.random_problem((264, 264, 1), seed=13, contrast=1e3)
+    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=100, max_iter=300, iface_degree=1)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+    pre = _oracle(prob, q)
+    assert pre.n_coarse == 15136
+    r = np.random.default_rng(17).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    parts = pre.apply_parts(r)
+    assert _rel(s.debug(mrcm.MRCM_DBG_COARSE), parts["c"]) < 1e-9
+    assert _rel(z, parts["z"]) < 1e-10
+    s.close()
