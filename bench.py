@@ -48,6 +48,9 @@ def parse():
                     help="Schwarz sweeps: restricted additive (default) or multiplicative multicolour")
     ap.add_argument("--degree", type=int, default=0, choices=[0, 1],
                     help="interface-space degree: 0 piecewise constant (default), 1 piecewise linear")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="off: the library's built-in launch variants (for profiler runs, whose per-launch "
+                         "overhead would mislead the autotuner's timings)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=8, help="GMRES iterations per reference-arm sample")
@@ -89,7 +92,7 @@ def config_dict(args, prob, q):
             "subdomains": f"{prob.n[0] // q.sub[0]}x{prob.n[1] // q.sub[1]} of {q.sub[0]}x{q.sub[1]}",
             "oversample": q.oversample, "smooth_steps": q.smooth_steps, "alpha": q.alpha, "restart": q.restart,
             "tol_relative": q.tol, "local_prec": args.prec, "smoothing": getattr(args, "smooth", "additive"),
-            "iface_degree": int(getattr(args, "degree", 0)), "l2": "flushed between timed steps (256 MiB write)",
+            "iface_degree": int(getattr(args, "degree", 0)), "autotune": getattr(args, "autotune", "on"), "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single-gpu"}
 
 
@@ -374,6 +377,8 @@ def mrcm_arm(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     from paper_2606_08883_gb300 import mrcm
+    if getattr(args, "autotune", "on") == "off":
+        mrcm.autotune(0)
     prob, q = workload(args, rank)
     solver = mrcm.Solver(prob, q, device=dev)
     stream = torch.cuda.current_stream(dev)
