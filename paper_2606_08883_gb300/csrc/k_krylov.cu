@@ -310,11 +310,11 @@ __device__ __forceinline__ double givens_scan(const double* c_, const double* s_
 template <int NE>
 __device__ __forceinline__ void update_ring(const double* __restrict__ V, size_t n, int j, const double* sh_h,
                                             size_t base, int tid, double* ring, double* w, double& nrm,
-                                            double (&keep)[UPD_EL]) {
+                                            double (&keep)[UPD_EL], int nvalid = NE) {
   constexpr int NT = ARN_THREADS;
   double acc[NE];
 #pragma unroll
-  for (int e = 0; e < NE; ++e) acc[e] = w[base + (size_t)e * NT];
+  for (int e = 0; e < NE; ++e) acc[e] = e < nvalid ? w[base + (size_t)e * NT] : 0.0;
   double* tr = ring + tid;
   const int S = (j + UPD_UU) / UPD_UU;
   auto issue = [&](int s) {
@@ -325,7 +325,8 @@ __device__ __forceinline__ void update_ring(const double* __restrict__ V, size_t
         if (i <= j)
 #pragma unroll
           for (int e = 0; e < NE; ++e)
-            cp_async8(tr + ((size_t)((s % UPD_DS) * UPD_UU + u) * NE + e) * NT, V + (size_t)i * n + base + (size_t)e * NT);
+            if (e < nvalid)
+              cp_async8(tr + ((size_t)((s % UPD_DS) * UPD_UU + u) * NE + e) * NT, V + (size_t)i * n + base + (size_t)e * NT);
       }
     }
     cp_async_commit();
@@ -348,9 +349,11 @@ __device__ __forceinline__ void update_ring(const double* __restrict__ V, size_t
   cp_async_wait<0>();
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
-    w[base + (size_t)e * NT] = acc[e];
-    nrm += acc[e] * acc[e];
-    keep[e] = acc[e];
+    if (e < nvalid) {
+      w[base + (size_t)e * NT] = acc[e];
+      nrm += acc[e] * acc[e];
+      keep[e] = acc[e];
+    }
   }
 }
 
@@ -401,7 +404,10 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi_ls(Geo g, LsArgs a) 
   //    one read of v_k; task j gives a_j = (w, v_j) and ||w||^2.  Slots: a_t at t, r_k at j+1+k,
   //    ||w||^2 at 2j+1.
   const int nd = 2 * j + 2;
-  for (int t = warp; t <= j; t += nw) {
+  // tasks in descending order: the sweep starts on the vectors the previous update read last and
+  // ends on v_0, v_1, ..., which the update below reads first (both while still in L2)
+  for (int u = warp; u <= j; u += nw) {
+    const int t = j - u;
     double s0 = 0.0, s1 = 0.0;
     size_t c = lo + lane;
     if (t < j) {
@@ -534,8 +540,11 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi_ls(Geo g, LsArgs a) 
   const bool one_group = hi - lo <= (size_t)UPD_EL * nt;
   for (size_t base = lo + tid; base < hi; base += (size_t)UPD_EL * nt) {
     const size_t left = (hi - base + nt - 1) / nt;
-    if (left >= (size_t)UPD_EL)
-      update_ring<UPD_EL>(a.V, n, j, shh, base, tid, ring, w, nrm, keep);
+    // the warp that holds the slice end runs the wide path on all its lanes (the missing elements
+    // masked) instead of both paths one after the other
+    const int nv = left >= (size_t)UPD_EL ? UPD_EL : (int)left;
+    if (__any_sync(__activemask(), nv == UPD_EL))
+      update_ring<UPD_EL>(a.V, n, j, shh, base, tid, ring, w, nrm, keep, nv);
     else
       update_ring<1>(a.V, n, j, shh, base, tid, ring, w, nrm, keep);
   }
