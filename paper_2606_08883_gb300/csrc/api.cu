@@ -43,7 +43,7 @@ struct Phase {
   long long slot = -1;  // this phase's event pair (reserved at construction, so phases may nest)
   Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
     nvtxRangePushA(kPhaseName[ph]);
-    if (!h->prof) return;
+    if (!h->prof || !((h->prof_mask >> ph) & 1u)) return;
     const size_t need = 2 * (h->ev_used + 1);
     while (h->ev_pool.size() < need) {
       cudaEvent_t e;
@@ -337,22 +337,36 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     CK(h, launch_assemble(g, h->bc_kind, bcp, h->has_f ? at<double>(h, L.f) : nullptr, at<double>(h, L.Tx),
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
   }
-  // MRCM-OS step 2: informed multiplier spaces from the oversampled Robin problems (Eq. 15)
+  // The factorisations depend only on A and are latency-bound (a barrier per column), so
+  // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 run on a second
+  // stream beside the oversampled Robin factors and the informed spaces of step 2, and the basis
+  // solves wait for them.
+  if (!h->side) {
+    CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    CK(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+  }
+  CK(h, cudaEventRecord(h->fork_ev, st));
+  CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+  // MRCM-OS step 2: informed multiplier spaces from the oversampled Robin problems (Eq. 15); the
+  // oversampled factors are submitted first, since the informed spaces wait for them
   CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * P.nq * L.smax, st));
   if (P.l > 0) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
     CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
   }
   {
+    Phase ph(h, MRCM_PH_FACTOR_OMEGA, h->side);
+    CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, h->side));
+  }
+  CK(h, cudaEventRecord(h->join_ev, h->side));
+  {
     Phase ph(h, MRCM_PH_INFORMED, st);
     for (int q = 0; q < P.nq; ++q)
       CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st));
   }
-  // MRCM-OS step 3: local Robin factors and multiscale basis functions
-  {
-    Phase ph(h, MRCM_PH_FACTOR_OMEGA, st);
-    CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, st));
-  }
+  // MRCM-OS step 3: multiscale basis functions from the local Robin factors
+  CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   {
     Phase ph(h, MRCM_PH_BASIS, st);
     for (int q = 0; q < P.nq; ++q)
@@ -381,11 +395,6 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     // A: they run on a second stream alongside the coupling factorisation (one cluster, most SMs
     // free), forked just before it, and the caller's stream waits for them at the end.
     if (h->prm.smooth_steps > 0) {
-      if (!h->side) {
-        CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
-        CK(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
-      }
       CK(h, cudaEventRecord(h->fork_ev, st));
       CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
       forked = true;
@@ -678,6 +687,12 @@ int64_t mrcm_launch_count(void) { return g_launches.load(); }
 mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable) {
   if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
   h->prof = enable != 0;
+  return MRCM_OK;
+}
+
+mrcm_status mrcm_profile_select(mrcm_handle h, uint32_t phase_mask) {
+  if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
+  h->prof_mask = phase_mask;
   return MRCM_OK;
 }
 

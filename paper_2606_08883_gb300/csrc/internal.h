@@ -140,6 +140,7 @@ struct mrcm_ctx {
   const volatile int* cancel = nullptr;  // set by the request server; checked once per GMRES step
   // phase profiler
   bool prof = false;
+  uint32_t prof_mask = ~0u;     // phases recorded while prof is set
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_phase;   // phase of each recorded (start, stop) pair, in pool order
   size_t ev_used = 0;          // pairs recorded since the last read

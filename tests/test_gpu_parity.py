@@ -285,6 +285,30 @@ def test_workspace_too_small_and_deterministic(mrcm):
     assert torch.equal(a, b)
 
 
+def test_profile_records_only_the_selected_phases(mrcm):
+    """Per-phase event timing restricted to one phase: that phase alone carries launches and time,
+    and the solution is the unprofiled one."""
+    prob, q = _case("os-48x40")
+    q.restart = 100
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    ref, _ = s.solve()
+    s.profile(True, phases=["schwarz"])
+    s.factor()
+    got, _ = s.solve()
+    prof = s.profile_read(reset=True)
+    assert torch.equal(got, ref)
+    assert prof["schwarz"][1] > 0 and prof["schwarz"][0] > 0.0
+    assert all(v == (0.0, 0) for k, v in prof.items() if k != "schwarz"), prof
+    s.profile(True)
+    s.factor()
+    s.solve()
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    for k in ("factor_ohat_robin", "factor_omega", "informed", "basis", "particular", "schwarz", "krylov"):
+        assert prof[k][1] > 0, k
+
+
 def test_full_size_channels_512_matches_oracle(mrcm):
     """The 512 x 512 channelised workload (contrast 1e6) in the configuration the benchmark times."""
     prob, q = W.channels(512, seed=1)
