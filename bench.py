@@ -33,6 +33,7 @@ METRIC = "GMRES solves/s at rel. residual 1e-8"
 UNIT = "solves/s"
 NOMINAL_FP64_TFLOPS = 1.25      # GB300 dense FP64, recipe table (all SMs at 2070 MHz)
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
+PROFILE_EVERY = 8   # timed steps: events around every 8th occurrence of the dominant phase
 
 
 def parse():
@@ -404,12 +405,13 @@ def mrcm_arm(args):
         solver.factor()
         p, info = solver.solve()
     torch.cuda.synchronize(dev)
-    # the timed region records events only around the dominant phase (the one the roofline reports,
-    # picked from the fully profiled last warm-up step); the per-phase breakdown comes from one fully
-    # profiled step after it, so the timed steps carry no other instrumentation
+    # the timed region records events only around every PROFILE_EVERY-th occurrence of the dominant
+    # phase (the one the roofline reports, picked from the fully profiled last warm-up step); the
+    # per-phase breakdown comes from one fully profiled step after it, so the timed steps carry no
+    # other instrumentation
     warm = solver.profile_read(reset=True) if args.warmup > 0 else {}
     dom_phase = dominant_phase(warm, prob, q, args.prec, info["iterations"] if info else 1)
-    solver.profile(True, phases=[dom_phase] if dom_phase else None)
+    solver.profile(True, phases=[dom_phase] if dom_phase else None, every=PROFILE_EVERY if dom_phase else 1)
     solver.profile_read(reset=True)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = getattr(props, "uuid", None)

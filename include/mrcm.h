@@ -221,10 +221,12 @@ enum { MRCM_PH_ASSEMBLE = 0, MRCM_PH_FACTOR_OHAT_ROBIN = 1, MRCM_PH_INFORMED = 2
        MRCM_PH_PARTICULAR = 7, MRCM_PH_COARSE_SOLVE = 8, MRCM_PH_RECONSTRUCT = 9, MRCM_PH_RESIDUAL = 10,
        MRCM_PH_SCHWARZ = 11, MRCM_PH_KRYLOV = 12, MRCM_PHASES = 13 };
 mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable);
-/* Restricts the recording to the phases whose bit (1 << MRCM_PH_*) is set in phase_mask (all
- * phases after mrcm_setup), so that a timed run can carry events around the phases it reports and
- * no others; the other phases then add neither events nor launch counts to the totals. */
-mrcm_status mrcm_profile_select(mrcm_handle h, uint32_t phase_mask);
+/* Restricts the recording to the phases whose bit (1 << MRCM_PH_*) is set in phase_mask, and to
+ * every `every`-th occurrence of each (counted per phase from this call; every >= 1).  After
+ * mrcm_setup all phases and every occurrence are recorded.  A timed run can so carry events around
+ * a sample of the launches it reports and no others: phases and occurrences left out add neither
+ * events nor launch counts to the totals, so totals / launches stays the mean launch duration. */
+mrcm_status mrcm_profile_select(mrcm_handle h, uint32_t phase_mask, int32_t every);
 mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int32_t cap, int32_t reset,
                               void* stream);
 

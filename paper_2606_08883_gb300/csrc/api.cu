@@ -44,6 +44,7 @@ struct Phase {
   Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
     nvtxRangePushA(kPhaseName[ph]);
     if (!h->prof || !((h->prof_mask >> ph) & 1u)) return;
+    if (h->ph_seen[ph]++ % h->prof_every != 0) return;
     const size_t need = 2 * (h->ev_used + 1);
     while (h->ev_pool.size() < need) {
       cudaEvent_t e;
@@ -690,9 +691,12 @@ mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable) {
   return MRCM_OK;
 }
 
-mrcm_status mrcm_profile_select(mrcm_handle h, uint32_t phase_mask) {
+mrcm_status mrcm_profile_select(mrcm_handle h, uint32_t phase_mask, int32_t every) {
   if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");
+  if (every < 1) return fail(h, MRCM_ERR_INVALID_ARG, "every must be >= 1");
   h->prof_mask = phase_mask;
+  h->prof_every = every;
+  for (long long& c : h->ph_seen) c = 0;
   return MRCM_OK;
 }
 

@@ -141,6 +141,8 @@ struct mrcm_ctx {
   // phase profiler
   bool prof = false;
   uint32_t prof_mask = ~0u;     // phases recorded while prof is set
+  int prof_every = 1;           // record every prof_every-th occurrence of a phase
+  long long ph_seen[MRCM_PHASES] = {0};   // occurrences of each phase since the last selection
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_phase;   // phase of each recorded (start, stop) pair, in pool order
   size_t ev_used = 0;          // pairs recorded since the last read

@@ -66,7 +66,7 @@ _SIGS = {
     "mrcm_plan_export": ([_P, _Q, C.POINTER(C.c_int32), C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
     "mrcm_debug_get": ([_H, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t), C.c_void_p], C.c_int),
     "mrcm_profile_enable": ([_H, C.c_int32], C.c_int),
-    "mrcm_profile_select": ([_H, C.c_uint32], C.c_int),
+    "mrcm_profile_select": ([_H, C.c_uint32, C.c_int32], C.c_int),
     "mrcm_profile_read": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "mrcm_launch_count": ([], C.c_int64),
     "mrcm_residual_norm_noalloc": ([_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -280,11 +280,11 @@ class Solver:
                               _stream_ptr(self.stream)), self.handle)
         return out
 
-    def profile(self, enable=True, phases=None):
+    def profile(self, enable=True, phases=None, every=1):
         """Per-phase event timing on or off; ``phases`` (names from PHASES) restricts the recording
-        to those phases, None records all."""
+        to those phases (None: all), ``every`` to every every-th occurrence of each."""
         mask = 0xFFFFFFFF if phases is None else sum(1 << PHASES.index(p) for p in phases)
-        _check(mrcm_profile_select(self.handle, mask), self.handle)
+        _check(mrcm_profile_select(self.handle, mask, int(every)), self.handle)
         _check(mrcm_profile_enable(self.handle, 1 if enable else 0), self.handle)
 
     def profile_read(self, reset=True):

@@ -300,6 +300,12 @@ def test_profile_records_only_the_selected_phases(mrcm):
     assert torch.equal(got, ref)
     assert prof["schwarz"][1] > 0 and prof["schwarz"][0] > 0.0
     assert all(v == (0.0, 0) for k, v in prof.items() if k != "schwarz"), prof
+    n_all = prof["schwarz"][1]
+    s.profile(True, phases=["schwarz"], every=4)   # occurrences 0, 4, 8, ... of the phase
+    s.factor()
+    s.solve()
+    prof = s.profile_read(reset=True)
+    assert prof["schwarz"][1] == (n_all + 3) // 4   # one launch per additive sweep
     s.profile(True)
     s.factor()
     s.solve()
