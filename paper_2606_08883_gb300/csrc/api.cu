@@ -124,6 +124,7 @@ Geo geo(mrcm_handle h) {
   g.Ky = at<double>(h, h->lay.Ky);
   g.Tx = at<double>(h, h->lay.Tx);
   g.Ty = at<double>(h, h->lay.Ty);
+  g.gtr = at<double>(h, h->lay.gtr);
   return g;
 }
 

@@ -54,6 +54,7 @@ struct Layout {
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
   size_t rdiag;                           // reciprocals of the diagonal of U
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
+  size_t gtr;                             // Robin coefficients of the Gamma faces, k_local.cu
   size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
@@ -99,6 +100,8 @@ struct Geo {
   const double* Ky;        // the y component (equal to K for a scalar field)
   const double* Tx;        // ny x (nx+1)
   const double* Ty;        // (ny+1) x nx
+  double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta) of the Gamma faces: written by the basis
+                           // solves at set-up, read by the particular solves' moments
 };
 
 // ------------------------------------------------------------------------------------------

@@ -770,10 +770,11 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       if (robin_side(g, s, kside)) {
         const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
-          int gx, gy, ox2, oy2;
-          double Tf, beta;
-          gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
-          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
+          // the face's inside cell, and its t_R and beta as the basis solves formed them
+          const int gx = (s % g.mx) * g.sx + (kside < 2 ? (kside == 0 ? 0 : g.sx - 1) : t);
+          const int gy = (s / g.mx) * g.sy + (kside < 2 ? t : (kside == 2 ? 0 : g.sy - 1));
+          const double tr = g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2];
+          const double beta = g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2 + 1];
           const double fl = tr * (double)Y[(gy - b.oy) * w + (gx - b.ox)];
 #pragma unroll
           for (int qt = 0; qt < 2; ++qt)
@@ -819,6 +820,10 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
           double Tf, beta;
           gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
           const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
+          if (a.q == 0 && r == 0) {  // kept for the particular solves' moments
+            g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2] = tr;
+            g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2 + 1] = beta;
+          }
           const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + kside) * g.smax + t];
           const double fl = tr * ((double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r] - ph);
           const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
