@@ -383,7 +383,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
     // the factorisation variants give identical factors; the autotuner times each once per band
     // shape (re-assembling G before every run, since the factorisation works in place)
-    int vars[4];
+    int vars[COARSE_FACTOR_MAX_VARIANTS];
     const int nv = coarse_factor_variants(c, vars);
     const int key[6] = {c.n, c.kl, c.ku, 0, 0, 0};
     cudaError_t terr = cudaSuccess;

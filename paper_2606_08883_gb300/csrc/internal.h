@@ -224,7 +224,8 @@ struct CoarseDev {
 cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st);
 // variant: see k_coarse.cu (-1: the first that runs); coarse_factor_variants lists those that run
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st, int variant = -1);
-int coarse_factor_variants(const CoarseDev& c, int* v);
+constexpr int COARSE_FACTOR_MAX_VARIANTS = 8;
+int coarse_factor_variants(const CoarseDev& c, int* v);   // v: COARSE_FACTOR_MAX_VARIANTS entries
 cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 // per apply without an explicit inverse: right-hand side from mom0, then the band solve
 cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);

@@ -269,38 +269,40 @@ __device__ __forceinline__ void gb_wait() {
 __device__ __forceinline__ void gb_pivot(const double* cj, int j, int km, int n, int ku, int ju_prev, int lane,
                                          double* sl, int* s_jp, int* s_ju, int* s_ok, int* ipiv, double* rdiag,
                                          int* flags) {
-  double best = -1.0;
-  int bi = 0x7fffffff;
+  // |x| compared through its bit pattern with the sign cleared, which orders like |x| for every
+  // non-NaN double (+0 and -0 equal); key = pattern + 1, and 0 for NaN, which is never chosen.
+  // Each lane keeps its first index of the largest key; the warp takes the largest key, then the
+  // lowest index holding it, with integer reductions instead of a compare-and-shuffle chain.
+  unsigned long long best = 0ull;
+  unsigned bi = 0xffffffffu;
   for (int i = lane; i <= km; i += 32) {
-    const double v = fabs(cj[i]);
-    if (v > best || (v == best && i < bi)) {
-      best = v;
-      bi = i;
+    const double x = cj[i];
+    const unsigned long long k = isnan(x) ? 0ull : ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) + 1ull;
+    if (k > best) {
+      best = k;
+      bi = (unsigned)i;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov > best || (ov == best && oi < bi)) {
-      best = ov;
-      bi = oi;
-    }
-  }
-  if (bi > km) bi = 0;  // no comparable entry (NaN column): pivot in place, reported as singular below
-  const double piv = cj[bi];
+  const unsigned khi = __reduce_max_sync(0xffffffffu, (unsigned)(best >> 32));
+  const unsigned klo = __reduce_max_sync(0xffffffffu, (unsigned)(best >> 32) == khi ? (unsigned)best : 0u);
+  const bool mine = best != 0ull && (unsigned)(best >> 32) == khi && (unsigned)best == klo;
+  unsigned bsel = __reduce_min_sync(0xffffffffu, mine ? bi : 0xffffffffu);
+  if (bsel > (unsigned)km) bsel = 0;  // no comparable entry (NaN column): pivot in place, reported as singular below
+  const int bi_sel = (int)bsel;
+  const double piv = cj[bi_sel];
   const bool ok = piv != 0.0 && isfinite(piv);
   if (ok) {
     const double rp = 1.0 / piv;
     if (lane == 0) rdiag[j] = rp;
     const double old0 = cj[0];
-    for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi ? old0 : cj[i]) * rp;
+    for (int i = 1 + lane; i <= km; i += 32) sl[i] = (i == bi_sel ? old0 : cj[i]) * rp;
   }
   if (lane == 0) {
     *s_ok = ok ? 1 : 0;
     if (!ok) atomicOr(flags, FLAG_SINGULAR_COARSE);
-    *s_jp = bi;
-    ipiv[j] = j + bi;
-    *s_ju = ok ? max(ju_prev, min(j + ku + bi, n - 1)) : ju_prev;
+    *s_jp = bi_sel;
+    ipiv[j] = j + bi_sel;
+    *s_ju = ok ? max(ju_prev, min(j + ku + bi_sel, n - 1)) : ju_prev;
   }
 }
 
@@ -1032,7 +1034,7 @@ cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E,
 cudaError_t launch_coarse_factor(const CoarseDev& c, int* flags, cudaStream_t st, int variant) {
   if (c.n == 0) return cudaSuccess;
   if (variant < 0) {
-    int v[4];
+    int v[COARSE_FACTOR_MAX_VARIANTS];
     coarse_factor_variants(c, v);
     variant = v[0];
   }
