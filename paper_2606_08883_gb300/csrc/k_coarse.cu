@@ -530,43 +530,58 @@ int coarse_factor_variants(const CoarseDev& c, int* v) {
   return nv;
 }
 
-// Columns of G^-1, one warp per column and no block barriers: the band entries of the next step
-// are loaded while the current step runs (at most four rows per lane, i.e. kl + ku <= 128).
+// Columns of G^-1, one warp per column and no block barriers (at most four band rows per lane,
+// i.e. kl + ku <= 128).  Each lane streams its band entries of the next GBC_DEPTH - 1 steps through
+// its own slots of a cp.async ring (it reads back only what it copied, so no warp barrier is needed
+// for them); the pivot indices and the reciprocal diagonals are staged once per CTA.  The forward
+// sweep of column col starts at step col - kl: before it, every interchange swaps two zero rows and
+// every update is skipped (b[j] = 0), so the result is the one of the full sweep.
 constexpr int GBC_ROWS = 4;
+constexpr int GBC_DEPTH = 6;
 __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __restrict__ Ginv) {
-  extern __shared__ double sbuf[];
+  extern __shared__ __align__(16) double sbuf[];
   const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
   const double* __restrict__ ab = c.ab;
-  const int* __restrict__ ipiv = c.ipiv;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* rd = sbuf;                                            // [n] 1 / U(j, j)
+  int* piv = reinterpret_cast<int*>(rd + n);                    // [n] (padded to an even count)
+  double* ring = rd + n + (n + 1) / 2;                          // [4 warps][GBC_DEPTH][GBC_ROWS][32]
+  double* b = ring + 4 * GBC_DEPTH * GBC_ROWS * 32 + (size_t)warp * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    rd[i] = c.rdiag[i];
+    piv[i] = c.ipiv[i];
+  }
+  __syncthreads();
   const int col = blockIdx.x * 4 + warp;
-  if (col >= n) return;  // whole warps
-  double* b = sbuf + (size_t)warp * n;
+  if (col >= n) return;  // whole warps; no block barrier follows
+  double* myr = ring + (size_t)warp * GBC_DEPTH * GBC_ROWS * 32 + lane;
+  auto slot = [&](int t, int q) -> double* { return myr + ((size_t)(t % GBC_DEPTH) * GBC_ROWS + q) * 32; };
   for (int i = lane; i < n; i += 32) b[i] = (i == col) ? 1.0 : 0.0;
   __syncwarp();
   // forward: b[j + i] -= L(j + i, j) b[j], after the interchange of step j
-  double cur[GBC_ROWS], nxt[GBC_ROWS];
-  auto loadL = [&](int j, double (&v)[GBC_ROWS]) {
-    const int lm = min(kl, n - 1 - j);
+  const int j0 = max(0, col - kl);
+  auto issueL = [&](int t) {  // step j0 + t
+    const int j = j0 + t;
+    if (j < n) {
+      const int lm = min(kl, n - 1 - j);
 #pragma unroll
-    for (int q = 0; q < GBC_ROWS; ++q) {
-      const int i = 1 + lane + 32 * q;
-      v[q] = i <= lm ? ab[(size_t)(kv + i) + (size_t)j * ld] : 0.0;
+      for (int q = 0; q < GBC_ROWS; ++q) {
+        const int i = 1 + lane + 32 * q;
+        if (i <= lm) gb_cp_async8(slot(t, q), ab + (size_t)(kv + i) + (size_t)j * ld);
+      }
     }
+    gb_commit();
   };
-  loadL(0, cur);
-  int lcur = ipiv[0];
-  for (int j = 0; j < n; ++j) {
-    int lnxt = 0;
-    if (j + 1 < n) {
-      loadL(j + 1, nxt);
-      lnxt = ipiv[j + 1];
-    }
-    if (lcur != j) {
+  for (int t = 0; t < GBC_DEPTH - 1; ++t) issueL(t);
+  for (int j = j0, t = 0; j < n; ++j, ++t) {
+    issueL(t + GBC_DEPTH - 1);
+    gb_wait<GBC_DEPTH - 1>();
+    const int lp = piv[j];
+    if (lp != j) {
       if (lane == 0) {
-        const double t = b[lcur];
-        b[lcur] = b[j];
-        b[j] = t;
+        const double tt = b[lp];
+        b[lp] = b[j];
+        b[j] = tt;
       }
       __syncwarp();
     }
@@ -576,32 +591,30 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __
 #pragma unroll
       for (int q = 0; q < GBC_ROWS; ++q) {
         const int i = 1 + lane + 32 * q;
-        if (i <= lm) b[j + i] -= cur[q] * bj;
+        if (i <= lm) b[j + i] -= *slot(t, q) * bj;
       }
     }
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < GBC_ROWS; ++q) cur[q] = nxt[q];
-    lcur = lnxt;
   }
+  gb_wait<0>();
   // backward: b[j] *= 1 / U(j, j), then b[i] -= U(i, j) b[j] for i = j - kv .. j - 1
-  double dcur, dnxt = 0.0;
-  auto loadU = [&](int j, double (&v)[GBC_ROWS]) {
-    const int i0 = max(0, j - kv);
+  auto issueU = [&](int t) {  // step n - 1 - t
+    const int j = n - 1 - t;
+    if (j >= 0) {
+      const int i0 = max(0, j - kv);
 #pragma unroll
-    for (int q = 0; q < GBC_ROWS; ++q) {
-      const int i = i0 + lane + 32 * q;
-      v[q] = i < j ? ab[(size_t)(kv + i - j) + (size_t)j * ld] : 0.0;
+      for (int q = 0; q < GBC_ROWS; ++q) {
+        const int i = i0 + lane + 32 * q;
+        if (i < j) gb_cp_async8(slot(t, q), ab + (size_t)(kv + i - j) + (size_t)j * ld);
+      }
     }
+    gb_commit();
   };
-  loadU(n - 1, cur);
-  dcur = 1.0 / ab[(size_t)kv + (size_t)(n - 1) * ld];
-  for (int j = n - 1; j >= 0; --j) {
-    if (j > 0) {
-      loadU(j - 1, nxt);
-      dnxt = 1.0 / ab[(size_t)kv + (size_t)(j - 1) * ld];  // reciprocal of the next diagonal, off the critical path
-    }
-    if (lane == 0) b[j] = b[j] * dcur;
+  for (int t = 0; t < GBC_DEPTH - 1; ++t) issueU(t);
+  for (int j = n - 1, t = 0; j >= 0; --j, ++t) {
+    issueU(t + GBC_DEPTH - 1);
+    gb_wait<GBC_DEPTH - 1>();
+    if (lane == 0) b[j] = b[j] * rd[j];
     __syncwarp();
     const double bj = b[j];
     const int i0 = max(0, j - kv);
@@ -609,14 +622,12 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols_warp(CoarseDev c, double* __
 #pragma unroll
       for (int q = 0; q < GBC_ROWS; ++q) {
         const int i = i0 + lane + 32 * q;
-        if (i < j) b[i] -= cur[q] * bj;
+        if (i < j) b[i] -= *slot(t, q) * bj;
       }
     }
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < GBC_ROWS; ++q) cur[q] = nxt[q];
-    dcur = dnxt;
   }
+  gb_wait<0>();
   for (int i = lane; i < n; i += 32) Ginv[(size_t)i * n + col] = b[i];
 }
 
@@ -1002,8 +1013,16 @@ static cudaError_t launch_gbb_solve(const CoarseDev& c, const double* mom0, int 
 
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st) {
   if (c.n == 0) return cudaSuccess;
-  const size_t sm4 = sizeof(double) * 4 * (size_t)c.n;
-  if (c.kl <= 32 * GBC_ROWS && c.kl + c.ku <= 32 * GBC_ROWS && sm4 <= 96 * 1024) {
+  const size_t sm4 = sizeof(double) * (5 * (size_t)c.n + ((size_t)c.n + 1) / 2 + 4 * GBC_DEPTH * GBC_ROWS * 32);
+  static const int optin = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+  }();
+  if (c.kl <= 32 * GBC_ROWS && c.kl + c.ku <= 32 * GBC_ROWS && sm4 <= (size_t)optin) {
+    const cudaError_t e = raise_smem_limit<k_gbtrs_cols_warp>();
+    if (e != cudaSuccess) return e;
     k_gbtrs_cols_warp<<<(c.n + 3) / 4, 128, sm4, st>>>(c, Ginv);
   } else {
     k_gbtrs_cols<<<c.n, 128, sizeof(double) * c.n, st>>>(c, Ginv);
