@@ -1,0 +1,61 @@
+"""Host bookkeeping of bench.py on CPU: the dominant phase comes from a fully profiled step, and the
+roofline's mean launch duration is a phase's event time over its recorded launches, so sampling
+every n-th launch of the phase leaves it unchanged."""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2606_08883_gb300 import workloads as W  # noqa: E402
+
+PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
+          "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
+
+
+def _case():
+    prob, q = W.channels(64, seed=1, sub=16, oversample=2, smooth_steps=2)
+    return prob, q
+
+
+def _prof(**entries):
+    out = {name: (0.0, 0) for name in PHASES}
+    out.update(entries)
+    return out
+
+
+def test_dominant_phase_is_the_largest_modelled_share():
+    prob, q = _case()
+    prof = _prof(schwarz=(3.0, 30), krylov=(2.0, 15), particular=(1.0, 15), coarse_factor=(5.0, 2))
+    # coarse_factor has no work model, so it is never the roofline's kernel
+    assert bench.dominant_phase(prof, prob, q, "fp64", 15) == "schwarz"
+    assert bench.dominant_phase(_prof(), prob, q, "fp64", 15) is None
+
+
+def test_roofline_mean_launch_from_sampled_events():
+    prob, q = _case()
+    peaks = {"hbm_gbs": 6680.0}
+    flops = bench.phase_model(prob, q, "fp64")["schwarz"][0]
+    # every launch recorded: 40 launches in 4 ms; every 8th recorded: 5 launches in 0.5 ms
+    full = bench.roofline(_prof(schwarz=(4.0, 40)), prob, q, "fp64", peaks, 15)
+    sampled = bench.roofline(_prof(schwarz=(0.5, 5)), prob, q, "fp64", peaks, 15)
+    for name, roof in (full, sampled):
+        assert name == "schwarz"
+        assert roof["launch_ms"] == pytest.approx(0.1)
+        assert roof["achieved"] == pytest.approx(flops / 1e-4 / 1e12)
+        assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+        assert roof["unit"] == "TFLOP/s" and roof["bound"] == "alu"
+    assert bench.PROFILE_EVERY >= 1
+
+
+def test_phase_rooflines_cover_every_profiled_modelled_phase():
+    prob, q = _case()
+    prof = _prof(schwarz=(1.0, 10), particular=(0.5, 5), reconstruct=(0.1, 5), factor_omega=(1.5, 1))
+    out = bench.phase_rooflines(prof, prob, q, "fp64", {"hbm_gbs": 6680.0}, 15)
+    assert set(out) == {"schwarz", "particular", "reconstruct", "factor_omega"}
+    assert out["reconstruct"]["bound"] == "hbm" and out["schwarz"]["bound"] == "alu"
+    assert out["factor_omega"]["launch_ms"] == pytest.approx(1.5)
