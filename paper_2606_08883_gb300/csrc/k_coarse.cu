@@ -222,7 +222,16 @@ __global__ void __launch_bounds__(128) k_gbtrs_cols(CoarseDev c, double* __restr
 __global__ void __launch_bounds__(256) k_coarse_apply(CoarseDev c, const double* __restrict__ Ginv,
                                                       const double* __restrict__ mom0, int E, double* __restrict__ out) {
   extern __shared__ double gs[];
+  constexpr int CH = 32;  // row entries per lane in flight
   const int n = c.n;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const double* gr = Ginv + (size_t)(row < n ? row : 0) * n;
+  // the first CH entries per lane of this warp's row of G^-1 are loaded while the block forms the
+  // right-hand side; the sum runs over k = lane, lane + 32, ... in order, as a plain loop would
+  double gv[CH];
+#pragma unroll
+  for (int q = 0; q < CH; ++q) gv[q] = (row < n && lane + 32 * q < n) ? gr[lane + 32 * q] : 0.0;
   for (int t = threadIdx.x; t < E * c.nq; t += blockDim.x) {
     int rf, rp;
     double gf, gp;
@@ -231,12 +240,22 @@ __global__ void __launch_bounds__(256) k_coarse_apply(CoarseDev c, const double*
     gs[rp] = gp;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
-  const double* gr = Ginv + (size_t)row * n;
   double acc = 0.0;
-  for (int k = lane; k < n; k += 32) acc += gr[k] * gs[k];
+  for (int base = 0; base < n; base += 32 * CH) {
+    if (base > 0) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int k = base + lane + 32 * q;
+        gv[q] = k < n ? gr[k] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int k = base + lane + 32 * q;
+      if (k < n) acc += gv[q] * gs[k];
+    }
+  }
   acc = warp_sum(acc);
   if (lane == 0) out[row] = acc;
 }
