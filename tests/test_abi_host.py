@@ -117,3 +117,28 @@ def test_plan_export_matches_oracle_on_random_partitions(lib):
         assert got.dtype == want.dtype and np.array_equal(got, want)
 
     check()
+
+
+def test_plan_export_matches_oracle_on_random_3d_partitions(lib):
+    # the same comparison on random 3-D grids: boxes, oversampled boxes, Robin sides, interface
+    # tables and banded coupling rows for six sides per subdomain
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=100, deadline=None)
+    @hyp.given(nx=st.integers(1, 12), ny=st.integers(1, 12), nz=st.integers(2, 10), sx=st.integers(1, 6),
+               sy=st.integers(1, 6), sz=st.integers(1, 6), l=st.integers(0, 3))
+    def check(nx, ny, nz, sx, sy, sz, l):
+        prob = W.random_problem((nx, ny, nz), dim=3, seed=0)
+        q = W.Params(sub=(sx, sy, sz), oversample=l)
+        try:
+            want = Partition(3, (nx, ny, nz), (sx, sy, sz), l).export()
+        except ValueError:
+            with pytest.raises(lib.MRCMError) as ei:
+                lib.plan_export(prob, q)
+            assert ei.value.status == lib.MRCM_ERR_INVALID_ARG
+            return
+        got = lib.plan_export(prob, q)
+        assert got.dtype == want.dtype and np.array_equal(got, want)
+
+    check()
