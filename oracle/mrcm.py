@@ -7,8 +7,9 @@ Set-up (MRCM-OS steps 1-3, with the preconditioner's homogeneous boundary condit
    with Robin data lambda^k = 1 on the faces of side k and 0 elsewhere.  On each face f of Gamma_s
    (inside cell c in Omega_s, outside cell c' in hat-Omega_s) take the discrete normal flux
    F = T_f (q_c - q_c'), the velocity u = F/|f|, the face pressure pi = q_c - F/tau_c and
-   phi_s^k(f) = -beta_f u + pi.  With l = 0 the faces of Gamma_s lie on the Robin boundary, the
-   Robin trace identity gives phi_s^k = lambda^k exactly, and that value is used.
+   phi_s^k(f) = -beta_f u + pi (the informed trace of q).  With l = 0 the faces of Gamma_s lie on
+   the Robin boundary, the Robin trace identity gives phi_s^k = lambda^k exactly, and that value is
+   used.
 2. Multiscale basis functions (MBF): psi_sk = (A^R_{Omega_s})^-1 (t_R phi_s^k on Gamma_s), with
    Robin traces F_sk(f) = t_R (psi_sk,c - phi_s^k(f)) and |f| P_sk(f) = |f| phi_s^k(f) + beta F_sk(f).
 3. Coupling system (Eq. 13-14) with piecewise-constant M_H, V_H on each interface Gamma_{s,s'}
@@ -19,8 +20,15 @@ Set-up (MRCM-OS steps 1-3, with the preconditioner's homogeneous boundary condit
    factored by LU with partial pivoting (dense LAPACK getrf; SuperLU beyond 4096 unknowns).
 4. Dirichlet restrictions A[hat-Omega_s, hat-Omega_s] for the smoothing sweeps.
 
-Apply z = T r (the modified MRCM-O of Sec. 3: homogeneous conditions, source r):
-  psi_s0 = (A^R_{Omega_s})^-1 r|Omega_s with traces F_s0 = t_R psi_s0,c, |f| P_s0 = beta F_s0;
+Apply z = T r (the modified MRCM-O of Sec. 3: homogeneous conditions, source r).  The source
+term's basis function is built on the extended region like the others (Sec. 1: oversampling lets
+each MBF be constructed in an extended region while the coupling stays on the non-overlapping
+partition):
+  q_s0 = (A^R_{hat-Omega_s})^-1 r|hat-Omega_s (zero Robin data on the boundary of hat-Omega_s),
+  phi_s0 = informed trace of q_s0 on Gamma_s (the formula of step 1; phi_s0 = 0 when l = 0),
+  psi_s0 = (A^R_{Omega_s})^-1 (r|Omega_s + t_R phi_s0) with traces F_s0 = t_R (psi_s0,c - phi_s0),
+  |f| P_s0 = |f| phi_s0 + beta F_s0, so that the Robin data of subdomain s is
+  lambda_s = phi_s0 + sum_k c_sk phi_s^k;
   G c = -g0 where g0 collects the particular traces row by row;
   z|Omega_s = psi_s0 + sum_k c_sk psi_sk;
   then ``smooth_steps`` restricted Schwarz sweeps (the smoothing of MRCM-OS step 4, Sec. 2.1):
@@ -30,12 +38,16 @@ Apply z = T r (the modified MRCM-O of Sec. 3: homogeneous conditions, source r):
   additive step is taken one colour after the other, each colour with the residual left by the
   colours before it.
 
-Pinned by (tests/test_oracle_mrcm.py): one subdomain gives T = A^-1; l = 0 gives indicator phi;
-a monolithic dense solve of the whole coupled MRCM system equals the superposition; per-cell mass
-balance and weak flux / pressure continuity of the MRCM reconstruction; exactness of P0 Robin
-coupling on a field that is constant along the interfaces; linearity of T; the smoothing sweep
+Pinned by (tests/test_oracle_mrcm.py): one subdomain gives T = A^-1; l = 0 gives indicator phi and
+phi_s0 = 0 (the MRCM of Eq. 11-14); a monolithic dense solve of the whole coupled system equals
+the superposition; basis and particular solutions equal the restrictions of the oversampled
+solutions; per-cell mass balance and weak flux / pressure continuity of the reconstruction;
+exactness on a field that is constant along the interfaces; linearity of T; the smoothing sweep
 leaves A^-1 r unchanged; the additive sweep equals a dense restricted additive Schwarz step; with
-l = 0 the multiplicative sweep equals block Gauss-Seidel over the colour-ordered subdomain blocks.
+l = 0 the multiplicative sweep equals block Gauss-Seidel over the colour-ordered subdomain blocks;
+oversampling alone cuts the GMRES iterations of the Sec. 4.1 problems well below plain MRCM, as
+Sec. 4.1 and Tables 2-3 state; with one sweep the preconditioned operator satisfies Appendix A's
+energy-norm contraction on a heterogeneous field.
 """
 
 import numpy as np
@@ -97,6 +109,14 @@ class MRCMOS:
         b = [x for x in range(3) if x != a][q - 1]
         return 2.0 * (pos[b] + 0.5 - lo[b]) / (hi[b] - lo[b]) - 1.0
 
+    def informed_trace(self, d, q):
+        """phi(f) = -beta_f u + pi on every Gamma_s face for oversampled solutions q (columns):
+        F = T_f (q_c - q_c'), u = F/|f|, pi = q_c - F/tau_c (the definition of phi_i^k, Sec. 2.1)."""
+        qc = q[d.g_in]
+        F = (d.g_tf * (qc - q[d.g_out]).T).T
+        pi = qc - (F.T / d.tau).T
+        return (-(d.beta / d.area) * F.T).T + pi
+
     # ---------------------------------------------------------------- set-up, per subdomain
     def _setup_subdomain(self, s):
         P, K, T, h, dim, nq = self.part, self.K, self.T, self.h, self.dim, self.nq
@@ -123,6 +143,21 @@ class MRCMOS:
         # test-function values of M_H, V_H on every Gamma_s face: (nq, ng)
         d.test = np.array([[self.side_poly(q, gpos[i], int(d.gamma_side[i]), blo, bhi)
                             for i in range(ng)] for q in range(nq)]).reshape(nq, ng)
+        # the oversampled Robin operator and, for every Gamma_s face, its inside / outside cells
+        # in hat-Omega_s (used by the informed traces of step 1 and of the particular solve)
+        d.oop = None
+        if self.l > 0 and N > 0:
+            olo, ohi = P.obox[s, 0], P.obox[s, 1]
+            d.oop = BoxOperator(K, T, h, dim, self.n, olo, ohi, True, self.alpha, self.sub)
+            g_in, g_out, g_tf = [], [], []
+            for k in sides:
+                for (pos, inside, outside) in P.gamma_faces(s, k):
+                    g_in.append(d.oop.local_index(inside))
+                    g_out.append(d.oop.local_index(outside))
+                    g_tf.append(self.T[k // 2][pos[2], pos[1], pos[0]])
+            d.g_in = np.array(g_in, dtype=np.int64)
+            d.g_out = np.array(g_out, dtype=np.int64)
+            d.g_tf = np.array(g_tf)
         # step 1: informed multiplier space
         phi = np.zeros((N, ng))
         if N > 0:
@@ -132,28 +167,14 @@ class MRCMOS:
                     phi[j, m] = d.test[q, m]
             else:
                 olo, ohi = P.obox[s, 0], P.obox[s, 1]
-                oop = BoxOperator(K, T, h, dim, self.n, olo, ohi, True, self.alpha, self.sub)
-                ofaces = {k: oop_f for k, oop_f in ((k, P.side_faces(olo, ohi, k)) for k in sides)}
-                rhs = np.zeros((oop.n_loc, N))
+                ofaces = {k: P.side_faces(olo, ohi, k) for k in sides}
+                rhs = np.zeros((d.oop.n_loc, N))
                 for j, (k, q) in enumerate(funcs):
                     for (pos, inside, outside) in ofaces[k]:
                         a = k // 2
                         _tau, _beta, t_r, _area = robin_face(K, h, a, inside, outside, self.alpha, self.sub)
-                        rhs[oop.local_index(inside), j] += t_r * self.side_poly(q, pos, k, olo, ohi)
-                q_sol = oop.solve(rhs)
-                fi = 0  # Gamma_s faces come in the same side / in-plane order as d.gamma
-                for k in sides:
-                    for (pos, inside, outside) in P.gamma_faces(s, k):
-                        a = k // 2
-                        t_f = self.T[a][pos[2], pos[1], pos[0]]
-                        tau, beta, _tr, area = robin_face(K, h, a, inside, outside, self.alpha, self.sub)
-                        qc = q_sol[oop.local_index(inside)]
-                        qo = q_sol[oop.local_index(outside)]
-                        F = t_f * (qc - qo)
-                        pi = qc - F / tau
-                        phi[:, fi] = -beta * F / area + pi
-                        fi += 1
-                assert fi == ng
+                        rhs[d.oop.local_index(inside), j] += t_r * self.side_poly(q, pos, k, olo, ohi)
+                phi = self.informed_trace(d, d.oop.solve(rhs)).T
         d.phi = phi
         # step 2: multiscale basis functions and their side moments
         rhs = np.zeros((d.op.n_loc, N))
@@ -217,16 +238,24 @@ class MRCMOS:
 
     # ---------------------------------------------------------------- apply
     def particular(self, r):
-        """psi_s0 for every subdomain and the coarse right-hand side g0."""
+        """psi_s0 for every subdomain, the informed particular traces phi_s0 and the coarse
+        right-hand side g0."""
         P, nq = self.part, self.nq
-        psi0 = []
+        psi0, phi0 = [], []
         F0 = np.zeros((P.S, 6, nq))
         P0 = np.zeros((P.S, 6, nq))
         for d in self.subs:
-            x = d.op.solve(d.op.restrict(r))
+            rs = d.op.restrict(r).copy()
+            ph = np.zeros(len(d.gamma))
+            if d.oop is not None:
+                # the source problem on the extended region, zero Robin data on its boundary
+                ph = self.informed_trace(d, d.oop.solve(d.oop.restrict(r)))
+                np.add.at(rs, d.gamma_li, d.t_r * ph)
+            x = d.op.solve(rs)
             psi0.append(x)
-            F = d.t_r * x[d.gamma_li]
-            Pw = d.beta * F
+            phi0.append(ph)
+            F = d.t_r * (x[d.gamma_li] - ph)
+            Pw = d.area * ph + d.beta * F
             for k in d.sides:
                 m = d.gamma_side == k
                 F0[d.s, k] = d.test[:, m] @ F[m]
@@ -236,6 +265,7 @@ class MRCMOS:
             for q in range(nq):
                 g0[2 * nq * e + q] = F0[s, 2 * a + 1, q] + F0[s2, 2 * a, q]
                 g0[2 * nq * e + nq + q] = P0[s, 2 * a + 1, q] - P0[s2, 2 * a, q]
+        self._phi0 = phi0
         return psi0, g0
 
     def reconstruct(self, psi0, c):
@@ -273,7 +303,7 @@ class MRCMOS:
         psi0, g0 = self.particular(r)
         c = self.coarse_solve(-g0)
         z = self.reconstruct(psi0, c)
-        out = {"psi0": psi0, "g0": g0, "c": c, "z_mrcm": z.copy()}
+        out = {"psi0": psi0, "phi0": self._phi0, "g0": g0, "c": c, "z_mrcm": z.copy()}
         for _ in range(self.smooth_steps):
             z = self.sweep(r, z)
         out["z"] = z

@@ -435,8 +435,11 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   // particular solutions and their side moments
   {
     Phase ph(h, MRCM_PH_PARTICULAR, st);
-    CK(h, launch_particular(g, at<void>(h, L.Linv_loc), L.LSl, fp32, r, at<double>(h, L.psi0), at<double>(h, L.mom0),
-                              at<int>(h, L.flags), st));
+    // on the extended regions' Robin factors when l > 0 (the source term's basis function is built
+    // there), on the subdomains' own Robin factors when l = 0
+    const bool ext = P.l > 0;
+    CK(h, launch_particular(g, at<void>(h, ext ? L.Linv_ohat_r : L.Linv_loc), ext ? L.LSo : L.LSl, fp32, r,
+                            at<double>(h, L.psi0), at<double>(h, L.mom0), at<int>(h, L.flags), st));
   }
   // coupling system
   CoarseDev c = coarse(h);

@@ -100,7 +100,7 @@ struct Geo {
   const double* Ky;        // the y component (equal to K for a scalar field)
   const double* Tx;        // ny x (nx+1)
   const double* Ty;        // (ny+1) x nx
-  double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta) of the Gamma faces: written by the basis
+  double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta, T_f, |f| / tau) of the Gamma faces: written by the basis
                            // solves at set-up, read by the particular solves' moments
 };
 

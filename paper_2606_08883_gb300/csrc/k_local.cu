@@ -502,7 +502,9 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool RES = NBUF == 0;
   const int s = (MODE == MODE_SCHWARZ && a.colour >= 0) ? colour_box(g, a.colour, blockIdx.x) : (int)blockIdx.x;
-  const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ);
+  // the particular solve runs on the extended region when there is one (the source term's basis
+  // function is built there like the others; its restriction to Omega_s is psi_s0)
+  const bool ohat = (MODE == MODE_INFORMED || MODE == MODE_SCHWARZ || (MODE == MODE_PARTICULAR && g.l > 0));
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
   T* Lb = reinterpret_cast<T*>(smem_raw);    // [NBUF][2][LS] line blocks, or [hgt][LS] (resident)
@@ -525,9 +527,10 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   tw.h = hgt;
   tw.m = hgt / 2;
   tw.nf = tw.m > hgt - 1 - tw.m ? tw.m : hgt - 1 - tw.m;
-  // a restricted Schwarz solve keeps only the lines of its subdomain
-  tw.lo_keep = MODE == MODE_SCHWARZ ? g.l : 0;
-  tw.hi_keep = MODE == MODE_SCHWARZ ? hgt - 1 - g.l : hgt - 1;
+  // a restricted Schwarz solve keeps only the lines of its subdomain; an extended particular solve
+  // also keeps the line beyond each y side, which holds the outside cells of that side's faces
+  tw.lo_keep = MODE == MODE_SCHWARZ ? g.l : (ohat ? g.l - 1 : 0);
+  tw.hi_keep = MODE == MODE_SCHWARZ ? hgt - 1 - g.l : (ohat ? hgt - g.l : hgt - 1);
   {
     const int nt_ = tw.m - tw.lo_keep, nb_ = tw.hi_keep - tw.m;
     tw.nb = nt_ > nb_ ? nt_ : nb_;
@@ -761,27 +764,43 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   // ---------------- outputs
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (MODE == MODE_PARTICULAR) {
-    for (int k = tid; k < hgt * w; k += nt) {
-      const int J = k / w, x = k % w;
-      if (active(g, b.ox + x, b.oy + J)) a.out[(size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+    // psi_s0 on Omega_s, and its side moments against the test functions of degree 0, 1.  The
+    // Gamma-face coefficients [t_R, beta, T_f, |f| / tau] were stored by the basis solves.
+    //   l = 0: the Robin traces with zero data, F = t_R x_c, |f| P = beta F;
+    //   l > 0: the traces of the extended solution q, F = T_f (q_c - q_c'), |f| P = |f| q_c - (|f| / tau) F
+    //          (equal to the Robin traces of the local solve with the informed particular data).
+    const int lo = ohat ? g.l : 0;
+    const int ws = sub_w(g, s), hs = sub_h(g, s);
+    for (int k = tid; k < ws * hs; k += nt) {
+      const int y = k / ws, x = k % ws;
+      a.out[(size_t)(b.oy + lo + y) * g.nx + b.ox + lo + x] = (double)Y[(lo + y) * w + lo + x];
     }
     for (int kside = wid; kside < 4; kside += nw) {
       double F[2] = {0.0, 0.0}, Pw[2] = {0.0, 0.0};  // against the test functions of degree 0, 1
       if (robin_side(g, s, kside)) {
         const int len = side_len(g, s, kside);
+        const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
+        // inside cell of face t in box coordinates, and the step to its outside cell
+        const int dx = kside == 0 ? -1 : (kside == 1 ? 1 : 0), dy = kside == 2 ? -1 : (kside == 3 ? 1 : 0);
         for (int t = lane; t < len; t += 32) {
-          // the face's inside cell, and its t_R and beta as the basis solves formed them
-          const int gx = (s % g.mx) * g.sx + (kside < 2 ? (kside == 0 ? 0 : g.sx - 1) : t);
-          const int gy = (s / g.mx) * g.sy + (kside < 2 ? t : (kside == 2 ? 0 : g.sy - 1));
-          const double tr = g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2];
-          const double beta = g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2 + 1];
-          const double fl = tr * (double)Y[(gy - b.oy) * w + (gx - b.ox)];
+          const int x = lo + (kside < 2 ? (kside == 0 ? 0 : g.sx - 1) : t);
+          const int y = lo + (kside < 2 ? t : (kside == 2 ? 0 : g.sy - 1));
+          const double* cf = g.gtr + (((size_t)s * 4 + kside) * g.smax + t) * 4;
+          const double qc = (double)Y[y * w + x];
+          double fl, pw;
+          if (ohat) {
+            fl = cf[2] * (qc - (double)Y[(y + dy) * w + x + dx]);
+            pw = area * qc - cf[3] * fl;
+          } else {
+            fl = cf[0] * qc;
+            pw = cf[1] * fl;
+          }
 #pragma unroll
           for (int qt = 0; qt < 2; ++qt)
             if (qt < g.nq) {
               const double wt = side_fn(qt, t, len);
               F[qt] += wt * fl;
-              Pw[qt] += wt * (beta * fl);
+              Pw[qt] += wt * pw;
             }
         }
       }
@@ -817,16 +836,19 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
         const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
           int gx, gy, ox2, oy2;
-          double Tf, beta;
+          double Tf, beta, tau;
           gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
-          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, nullptr);
+          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, &tau);
+          const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
           if (a.q == 0 && r == 0) {  // kept for the particular solves' moments
-            g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2] = tr;
-            g.gtr[(((size_t)s * 4 + kside) * g.smax + t) * 2 + 1] = beta;
+            double* cf = g.gtr + (((size_t)s * 4 + kside) * g.smax + t) * 4;
+            cf[0] = tr;
+            cf[1] = beta;
+            cf[2] = Tf;
+            cf[3] = area / tau;
           }
           const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + kside) * g.smax + t];
           const double fl = tr * ((double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r] - ph);
-          const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
           const double pw = area * ph + beta * fl;
 #pragma unroll
           for (int qt = 0; qt < 2; ++qt)
@@ -985,7 +1007,7 @@ cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, cons
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, int* flags, cudaStream_t st) {
   SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags, -1};
-  return launch_solve<MODE_PARTICULAR, 1>(g, a, false, fp32, st);
+  return launch_solve<MODE_PARTICULAR, 1>(g, a, g.l > 0, fp32, st);
 }
 
 // colour -1: every box (additive sweep, zin and zout distinct); colour c: the boxes of colour c only,

@@ -216,7 +216,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.psi0 = take(8 * n);
   L.z0 = take(8 * n);
   L.mom0 = take(8 * S * 8 * nq);
-  L.gtr = take(8 * S * 4 * L.smax * 2);
+  L.gtr = take(8 * S * 4 * L.smax * 4);
   L.G = take(8 * (size_t)L.ldab * NC);
   L.ipiv = take(4 * NC);
   L.gc = take(8 * NC);

@@ -88,10 +88,27 @@ def test_restart_reuses_iterate():
     assert np.allclose(p_res, p_full, rtol=1e-10, atol=1e-12)
 
 
-def test_appendix_a_energy_norm_bound():
+def _energy_eps(A, Tm):
+    w, U = np.linalg.eigh(A)
+    Ah = (U * np.sqrt(w)) @ U.T
+    Aih = (U / np.sqrt(w)) @ U.T
+    return np.linalg.norm(np.eye(A.shape[0]) - Ah @ (A @ Tm) @ Aih, 2)
+
+
+def test_oversampling_brings_the_energy_contraction_below_one():
+    # Appendix A's assumption ||I - A T||_A < 1 holds for MRCM-OS with one sweep on this field,
+    # and it is the oversampling that gives it: the same sweep after the non-overlapping MRCM
+    # (l = 0), or the oversampled MRCM without a sweep, leave ||I - A T||_A above one
+    assert _energy_eps(*_tiny(seed=9, l=2, smooth=1, contrast=10.0)[2:4]) < 0.6
+    assert _energy_eps(*_tiny(seed=9, l=0, smooth=1, contrast=10.0)[2:4]) > 1.0
+    assert _energy_eps(*_tiny(seed=9, l=2, smooth=0, contrast=10.0)[2:4]) > 1.0
+
+
+@pytest.mark.parametrize("smooth", [1, 2])
+def test_appendix_a_energy_norm_bound(smooth):
     # Appendix A: if ||I - A T||_A = eps < 1, GMRES on the transformed system reduces its residual
     # at least by eps per step.  Checked with a textbook GMRES on B = A^1/2 (A T) A^-1/2.
-    prob, pre, A, Tm, b = _tiny(seed=9, l=2, smooth=2, contrast=10.0)
+    prob, pre, A, Tm, b = _tiny(seed=9, l=2, smooth=smooth, contrast=10.0)
     w, U = np.linalg.eigh(A)
     Ah = (U * np.sqrt(w)) @ U.T
     Aih = (U / np.sqrt(w)) @ U.T

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import grid
+from oracle.local import BoxOperator, robin_face
 from oracle.mrcm import MRCMOS
 from paper_2606_08883_gb300 import workloads as W
 
@@ -91,6 +92,69 @@ def _monolithic(pre, r):
     return z, x[nz:]
 
 
+def _monolithic_oversampled(pre, r):
+    """The same coupled system written on the extended regions (l > 0): unknowns are the
+    pressures of every hat-Omega_s (source r on hat-Omega_s, Robin data sum_k c_sk lambda^k on the
+    boundary of hat-Omega_s, Eq. 15) and the coefficients c; the flux and pressure continuity rows
+    (Eq. 13-14) take the discrete flux F = T_f (q_c - q_c') and the face pressure q_c - F / tau_c of
+    the extended solutions on the Gamma faces.  No informed trace and no Omega_s problem appear:
+    their agreement with this system is what the test checks."""
+    P = pre.part
+    K, T, h = pre.K, pre.T, pre.h
+    ops = [BoxOperator(K, T, h, pre.dim, pre.n, P.obox[d.s, 0], P.obox[d.s, 1], True, pre.alpha, pre.sub)
+           for d in pre.subs]
+    offs = np.concatenate([[0], np.cumsum([o.n_loc for o in ops])])
+    nz = offs[-1]
+    nc = pre.n_coarse
+    M = np.zeros((nz + nc, nz + nc))
+    rhs = np.zeros(nz + nc)
+    for d, op in zip(pre.subs, ops):
+        o = offs[d.s]
+        M[o:o + op.n_loc, o:o + op.n_loc] = op.dense()
+        rhs[o:o + op.n_loc] = op.restrict(r)
+        olo, ohi = P.obox[d.s, 0], P.obox[d.s, 1]
+        for j, (k, q) in enumerate(d.funcs):
+            col = nz + pre.coff[d.s] + j
+            for (pos, inside, outside) in P.side_faces(olo, ohi, k):
+                _tau, _beta, t_r, _area = robin_face(K, h, k // 2, inside, outside, pre.alpha, pre.sub)
+                M[o + op.local_index(inside), col] -= t_r * pre.side_poly(q, pos, k, olo, ohi)
+    nq = pre.nq
+
+    def face_terms(d, side):
+        op, o = ops[d.s], offs[d.s]
+        faces = P.gamma_faces(d.s, side)
+        Fz = np.zeros((len(faces), nz + nc))
+        Pw = np.zeros((len(faces), nz + nc))
+        test = np.zeros((nq, len(faces)))
+        for t, (pos, inside, outside) in enumerate(faces):
+            a = side // 2
+            tau, _beta, _tr, area = robin_face(K, h, a, inside, outside, pre.alpha, pre.sub)
+            tf = T[a][pos[2], pos[1], pos[0]]
+            ci, co = o + op.local_index(inside), o + op.local_index(outside)
+            Fz[t, ci] += tf
+            Fz[t, co] -= tf
+            Pw[t, ci] += area
+            Pw[t] -= area / tau * Fz[t]
+            for q in range(nq):
+                test[q, t] = pre.side_poly(q, pos, side, P.box[d.s, 0], P.box[d.s, 1])
+        return Fz, Pw, test
+
+    for e, (a, s, s2) in enumerate(P.interfaces):
+        F1, P1, t1 = face_terms(pre.subs[s], 2 * a + 1)
+        F2, P2, t2 = face_terms(pre.subs[s2], 2 * a)
+        for q in range(nq):
+            M[nz + 2 * nq * e + q] = t1[q] @ F1 + t2[q] @ F2
+            M[nz + 2 * nq * e + nq + q] = t1[q] @ P1 - t2[q] @ P2
+    x = np.linalg.solve(M, rhs)
+    z = np.zeros(pre.shape)
+    for d, op in zip(pre.subs, ops):
+        zz = x[offs[d.s]:offs[d.s] + op.n_loc].reshape(op.w[2], op.w[1], op.w[0])
+        inner = tuple(slice(int(P.box[d.s, 0, a] - P.obox[d.s, 0, a]), int(P.box[d.s, 1, a] - P.obox[d.s, 0, a]))
+                      for a in (2, 1, 0))
+        z[d.op.sl] = zz[inner]
+    return z, x[nz:]
+
+
 # n2: the 2-D grid; (14, 11) is not divisible by the 4 x 4 subdomains (last sizes 2 and 3)
 @pytest.mark.parametrize("l,degree,dim,n2", [(0, 0, 2, (12, 12)), (1, 0, 2, (12, 12)), (2, 0, 2, (12, 12)),
                                              (2, 1, 2, (12, 12)), (1, 0, 3, None), (0, 0, 2, (14, 11)),
@@ -107,7 +171,7 @@ def test_superposition_equals_monolithic_dense_solve(l, degree, dim, n2):
         assert tuple(pre.part.m[:2]) == tuple(-(-v // 4) for v in n2)
     r = np.random.default_rng(3).standard_normal(prob.K.shape)
     parts = pre.apply_parts(r)
-    z_ref, c_ref = _monolithic(pre, r)
+    z_ref, c_ref = (_monolithic if l == 0 else _monolithic_oversampled)(pre, r)
     assert np.linalg.norm(parts["z_mrcm"] - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
     assert np.linalg.norm(parts["c"] - c_ref) <= 1e-9 * np.linalg.norm(c_ref)
 
@@ -120,7 +184,7 @@ def test_diagonal_tensor_superposition_and_single_subdomain(l):
     pre = _pre(prob, (4, 4, 1), l, 0)
     r = np.random.default_rng(32).standard_normal(pre.shape)
     parts = pre.apply_parts(r)
-    z_ref, c_ref = _monolithic(pre, r)
+    z_ref, c_ref = (_monolithic if l == 0 else _monolithic_oversampled)(pre, r)
     assert np.linalg.norm(parts["z_mrcm"] - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
     one = _pre(prob, (12, 12, 1), 0, 1)
     ref = np.linalg.solve(_dense_A(one), r.ravel()).reshape(r.shape)
@@ -138,7 +202,7 @@ def test_mass_balance_and_weak_continuity(tensor, n):
     Fside, Pside = {}, {}
     for d in pre.subs:
         zs = d.op.restrict(z)
-        lam = d.phi.T @ c[pre.coff[d.s]:pre.coff[d.s] + len(d.funcs)]
+        lam = parts["phi0"][d.s] + d.phi.T @ c[pre.coff[d.s]:pre.coff[d.s] + len(d.funcs)]
         # per-cell mass balance inside the subdomain: A^R z_s - t_R lambda = r
         res = d.op.dense() @ zs
         np.add.at(res, d.gamma_li, -d.t_r * lam)
@@ -301,6 +365,56 @@ def test_basis_equals_restricted_oversampled_solution(l, degree, dim, n2):
             inner = tuple(slice(int(P.box[d.s, 0, a] - olo[a]), int(P.box[d.s, 1, a] - olo[a])) for a in (2, 1, 0))
             ref = qk[inner].ravel()
             assert np.allclose(d.psi[:, j], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("l,dim,n2", [(1, 2, (16, 12)), (3, 2, (16, 12)), (1, 3, None), (2, 2, (19, 15))])
+def test_particular_equals_restricted_oversampled_solution(l, dim, n2):
+    # the source term's basis function is built on the extended region: psi_s0, the local Robin
+    # solve on Omega_s with source r and the informed particular trace phi_s0 as data, equals the
+    # dense solve of the hat-Omega_s Robin problem with source r (zero data) restricted to Omega_s
+    if dim == 2:
+        prob = W.random_problem(n2 + (1,), seed=41, contrast=1e4)
+        sub = (4, 4, 1)
+    else:
+        prob = W.random_problem((6, 6, 4), dim=3, seed=41, contrast=1e3, bc_kind=[0, 0, 1, 1, 1, 1])
+        sub = (3, 3, 2)
+    pre = _pre(prob, sub, l, 0)
+    r = np.random.default_rng(42).standard_normal(pre.shape)
+    psi0 = pre.apply_parts(r)["psi0"]
+    P = pre.part
+    for d in pre.subs:
+        olo, ohi = P.obox[d.s, 0], P.obox[d.s, 1]
+        oop = BoxOperator(prob.K, pre.T, prob.h, dim, pre.n, olo, ohi, True, 10.0, sub)
+        q0 = np.linalg.solve(oop.dense(), oop.restrict(r)).reshape(oop.w[2], oop.w[1], oop.w[0])
+        inner = tuple(slice(int(P.box[d.s, 0, a] - olo[a]), int(P.box[d.s, 1, a] - olo[a])) for a in (2, 1, 0))
+        ref = q0[inner].ravel()
+        assert np.allclose(psi0[d.s], ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_zero_oversampling_has_no_particular_trace():
+    # l = 0: hat-Omega = Omega, the source problem has zero Robin data on Gamma, so phi_s0 = 0 and T
+    # is the plain MRCM of Eq. 11-14 (the monolithic l = 0 pin above covers its value)
+    prob = W.random_problem((12, 12, 1), seed=43, contrast=1e3)
+    pre = _pre(prob, (4, 4, 1), 0, 0)
+    parts = pre.apply_parts(np.random.default_rng(44).standard_normal(pre.shape))
+    assert all(np.array_equal(ph, np.zeros_like(ph)) for ph in parts["phi0"])
+
+
+@pytest.mark.parametrize("variable", [False, True])
+def test_oversampling_alone_cuts_iterations(variable):
+    # Sec. 4.1 and Tables 2-3: with oversampling and no smoothing (MRCM-O) GMRES(10) needs far fewer
+    # iterations than with the non-overlapping MRCM, and more oversampling needs fewer still.  The
+    # Sec. 4.1 problems on a 64 x 64 grid, 4 x 4 and 8 x 8 subdomains, absolute tolerance 1e-8.
+    from oracle.solve import solve
+    prob, _exact = W.analytic(64, variable)
+    for m in (4, 8):
+        it = []
+        for l in (0, 2, 4):
+            _p, info, _pre_ = solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=(64 // m, 64 // m, 1), l=l,
+                                    smooth_steps=0, alpha=10.0, tol=1e-8, tol_relative=False, restart=10, max_iter=400)
+            assert info["status"] == 0
+            it.append(info["iterations"])
+        assert it[1] <= 0.6 * it[0] and it[2] <= 0.45 * it[0] and it[2] < it[1], it
 
 
 def test_piecewise_linear_sides_need_two_faces():
