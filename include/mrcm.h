@@ -233,6 +233,13 @@ mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int3
 /* Total kernels this library has launched in the process (all handles), for launch accounting. */
 int64_t mrcm_launch_count(void);
 
+/* Measured FP64 FMA throughput of the current device (not in the paper: the denominator of the
+ * FP64 kernels' rooflines).  Runs a register-operand FMA loop on every SM (four 256-thread blocks
+ * per SM, eight independent chains per thread) four times on `stream`, synchronising it, and
+ * writes the best of the last three as TFLOP/s (2 flops per FMA) to the host double *tflops_out.
+ * Launches one kernel per repetition; allocates no device memory. */
+mrcm_status mrcm_measure_fp64_peak(double* tflops_out, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Request server with continuous batching (not in the paper: a serving layer around Algorithm 1).
  *
@@ -287,7 +294,8 @@ void mrcm_server_destroy(mrcm_server_handle s);
  * are rejected with MRCM_ERR_INVALID_ARG.  b, p: device arrays of n cells; norm_out: device
  * pointer to one double, written when `stream` reaches the launch.  All calls share the one
  * array, so calls that overlap on the GPU (other streams, other threads) race: serialise them.
- * Requires a factored handle (for the transmissibilities). */
+ * Requires a factored handle (for the transmissibilities) and, as the current device, the device
+ * the handle was set up on (else MRCM_ERR_INVALID_ARG). */
 mrcm_status mrcm_residual_norm_noalloc(mrcm_handle h, const double* b, const double* p, double* norm_out,
                                        void* stream);
 

@@ -281,6 +281,7 @@ mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, v
   h->ws = static_cast<char*>(workspace);
   h->ws_bytes = workspace_bytes;
   h->coarse_n = P.E2;
+  if (cudaGetDevice(&h->device) != cudaSuccess) h->device = -1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   mrcm_status rc = copy_problem(h, problem, st);
   if (rc != MRCM_OK) {
@@ -688,6 +689,35 @@ mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host,
 void mrcm_destroy(mrcm_handle h) { delete h; }
 
 int64_t mrcm_launch_count(void) { return g_launches.load(); }
+
+mrcm_status mrcm_measure_fp64_peak(double* tflops_out, void* stream) {
+  if (!tflops_out) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(nullptr, MRCM_ERR_CUDA, "no CUDA device");
+  const int blocks = 4 * sms, threads = 256, iters = 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 0.0f;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  // the sink is never written for these operands; a null pointer is never dereferenced
+  for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+    err = cudaEventRecord(e0, st);
+    if (err == cudaSuccess) err = mrcm::launch_dfma_probe(nullptr, blocks, threads, iters, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(nullptr, MRCM_ERR_CUDA, cudaGetErrorString(err));
+  const double fma = (double)blocks * threads * iters * 32.0;
+  *tflops_out = 2.0 * fma / (best * 1e-3) / 1e12;
+  return MRCM_OK;
+}
 
 mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable) {
   if (!h) return fail(h, MRCM_ERR_INVALID_ARG, "null handle");

@@ -133,6 +133,7 @@ struct mrcm_ctx {
   int has_bc[6];
   int has_f;
   bool iso = true;    // K is a scalar field (Ky mirrors it)
+  int device = -1;    // the device current at mrcm_setup (the workspace's device)
   char* ws;           // workspace base (device)
   size_t ws_bytes;
   bool factored = false;
@@ -183,6 +184,8 @@ cudaError_t launch_assemble(const Geo& g, const int* bc_kind, const double* cons
                             double* Tx, double* Ty, double* b, cudaStream_t st);
 cudaError_t launch_matvec(const Geo& g, const double* v, double* w, cudaStream_t st);
 cudaError_t launch_residual(const Geo& g, const double* r, const double* z, double* rho, cudaStream_t st);
+// FP64 FMA throughput probe (k_grid.cu): blocks x threads x iters x 32 FMA
+cudaError_t launch_dfma_probe(double* sink, int blocks, int threads, int iters, cudaStream_t st);
 cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const* bcv, const double* p,
                           double* ux, double* uy, cudaStream_t st);
 

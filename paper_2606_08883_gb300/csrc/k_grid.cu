@@ -181,4 +181,30 @@ cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const*
   return cudaGetLastError();
 }
 
+// FP64 FMA throughput probe: eight independent register-operand FMA chains per thread, enough
+// chains per SM to cover the FMA latency, so the FP64 pipes run at their issue limit.  The result
+// is kept live by a store that never happens for these operands.
+__global__ void k_dfma_probe(double* sink, int iters) {
+  double a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = 1.0 + 1e-9 * (threadIdx.x + 37 * i);
+  const double b = 0.9999999, c = 1e-9;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t += a[i];
+  if (t == -1.0) sink[blockIdx.x] = t;
+}
+
+cudaError_t launch_dfma_probe(double* sink, int blocks, int threads, int iters, cudaStream_t st) {
+  k_dfma_probe<<<blocks, threads, 0, st>>>(sink, iters);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 }  // namespace mrcm

@@ -79,6 +79,13 @@ extern "C" mrcm_status mrcm_residual_norm_noalloc(mrcm_handle h, const double* b
     h->err = std::string("mrcm_residual_norm_noalloc: no usable current device: ") + cudaGetErrorString(e);
     return MRCM_ERR_CUDA;
   }
+  if (dev != h->device) {
+    // the scratch copy is picked by the current device, the transmissibilities come from the
+    // handle's workspace: both must be on the same GPU
+    h->err = "mrcm_residual_norm_noalloc: the current device (" + std::to_string(dev) +
+             ") is not the one the handle was set up on (" + std::to_string(h->device) + ")";
+    return MRCM_ERR_INVALID_ARG;
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);

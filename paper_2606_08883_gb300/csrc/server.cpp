@@ -117,6 +117,12 @@ struct mrcm_server {
 namespace {
 
 void run_request(mrcm_server* S, Request* r, cudaStream_t st) {
+  // every exit waits for the request's stream, so that no copy or kernel still touches its arena
+  // block when the worker releases it (another request may be admitted to the same bytes)
+  struct StreamIdleOnExit {
+    cudaStream_t st;
+    ~StreamIdleOnExit() { cudaStreamSynchronize(st); }
+  } idle_on_exit{st};
   char* base = S->arena_base + r->off;
   const size_t n = r->n;
   const int nx = r->prob.n[0], ny = r->prob.n[1];

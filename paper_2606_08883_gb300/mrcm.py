@@ -69,6 +69,7 @@ _SIGS = {
     "mrcm_profile_select": ([_H, C.c_uint32, C.c_int32], C.c_int),
     "mrcm_profile_read": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "mrcm_launch_count": ([], C.c_int64),
+    "mrcm_measure_fp64_peak": ([C.POINTER(C.c_double), C.c_void_p], C.c_int32),
     "mrcm_residual_norm_noalloc": ([_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "mrcm_server_create": ([C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
     "mrcm_submit": ([C.c_void_p, _P, _Q, C.POINTER(C.c_uint64)], C.c_int),
@@ -108,6 +109,13 @@ def autotune_table():
         out.append({"kind": int(e[0]), "key": tuple(int(v) for v in e[1:7]), "choice": int(e[7]),
                     "ncand": int(e[8]), "best_us": float(e[9])})
     return out
+
+
+def measure_fp64_peak(stream=None):
+    """Measured FP64 FMA throughput of the current device, TFLOP/s (mrcm_measure_fp64_peak)."""
+    v = C.c_double(0.0)
+    _check(mrcm_measure_fp64_peak(C.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 class MRCMError(RuntimeError):

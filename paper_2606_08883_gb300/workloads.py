@@ -144,6 +144,16 @@ def _flow_problem(dim, n, h, K, name):
                    [left, right, None, None, None, None], None, name=name)
 
 
+def flow_window(K, h, name="window"):
+    """The flow problem of ``_flow_problem`` (p = 1 / 0 on the first / last x face, no flow across
+    the others, no source) on a block of cells cut from a larger field: K (nz, ny, nx) is the block,
+    h the cell size of the field it came from."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    n = (K.shape[2], K.shape[1], K.shape[0])
+    dim = 2 if K.shape[0] == 1 else 3
+    return _flow_problem(dim, n, tuple(h), K, name)
+
+
 # ---------------------------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------------------------

@@ -59,3 +59,48 @@ def test_phase_rooflines_cover_every_profiled_modelled_phase():
     assert set(out) == {"schwarz", "particular", "reconstruct", "factor_omega"}
     assert out["reconstruct"]["bound"] == "hbm" and out["schwarz"]["bound"] == "alu"
     assert out["factor_omega"]["launch_ms"] == pytest.approx(1.5)
+
+
+def test_default_line_is_the_2048_mixed_workload():
+    args = bench.parse([])
+    assert (args.workload, args.prec, args.restart) == ("lognormal-2048", "fp32", 30)
+    prob, q = bench.workload(args)
+    assert prob.n[:2] == (2048, 2048) and tuple(q.sub[:2]) == (32, 32)
+    assert (q.oversample, q.smooth_steps, q.local_prec) == (2, 1, W.PREC_FP32)
+    assert bench.config_dict(args, prob, q)["subdomains"] == "64x64 of 32x32"
+    prob64, q64 = bench.workload(args, prec="fp64")
+    assert q64.local_prec == W.PREC_FP64 and prob64.name == prob.name
+    assert bench.parse(["--workload", "channels-512"]).prec == "fp64"
+
+
+def test_block_sample_converted_by_cells_and_oracle_iterations():
+    # t = (n / n_block) (t_setup + t_gmres it / it_block)
+    args = bench.parse([])
+    s = bench.OracleSampler(args)
+    s.full_cells = 2048 * 2048
+    s.rec = {"iterations": 10}
+    r = {"setup_s": 0.5, "iter_s": 1.3, "iters": 13, "cells": 256 * 256}
+    assert s.full_time(r) == pytest.approx(64 * (0.5 + 1.3 * 10 / 13))
+    full = bench.OracleSampler(bench.parse(["--workload", "channels-512"]))
+    assert full.full_time(r) == pytest.approx(1.8)   # a full-size sample is not scaled
+
+
+def test_error_against_the_stored_oracle_samples():
+    import numpy as np
+    rec = {"sample_cells": [0, 5, 9], "p_sample": [1.0, 2.0, 2.0]}
+    p = np.zeros(10)
+    p[[0, 5, 9]] = [1.0, 2.0, 2.0 + 3e-9]
+    assert bench.err_vs_oracle(p, rec) == pytest.approx(1e-9)
+    args = bench.parse([])
+    rec = bench.golden(args)
+    assert rec is not None and rec["iterations"] > 0 and len(rec["sample_cells"]) == len(rec["p_sample"]) == 1024
+    assert bench.golden(bench.parse(["--restart", "20"])) is None   # another configuration: no stored value
+
+
+def test_particular_solve_modelled_on_the_extended_box():
+    prob, q = _case()   # oversampling 2: 20 x 20 extended boxes, Omega plus one line per side kept
+    m = bench.phase_model(prob, q, "fp64")
+    w = q.sub[0] + 2 * q.oversample
+    S = (prob.n[0] // q.sub[0]) * (prob.n[1] // q.sub[1])
+    products = (w - 1) + 1 + (w // 2 - (q.oversample - 1)) + (w - 1 - (q.oversample - 1) - w // 2)
+    assert m["particular"][0] == S * products * 2 * w * w

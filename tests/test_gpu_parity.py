@@ -180,7 +180,7 @@ def test_multiplicative_smoothing_matches_oracle(mrcm, name):
 
 def test_multiplicative_smoothing_gmres_matches_oracle(mrcm):
     prob, q = _case("os-96x64-l4s2")
-    q.smooth_kind, q.tol, q.restart = 1, 1e-9, 100
+    q.smooth_kind, q.tol, q.restart = 1, 1e-9, 30
     s = mrcm.Solver(prob, q)
     s.factor()
     p, info = s.solve()
@@ -188,14 +188,16 @@ def test_multiplicative_smoothing_gmres_matches_oracle(mrcm):
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter, smooth_kind=1)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
     s.close()
 
 
-# GMRES(8) where restarted GMRES converges for this operator (covers the restart path); a long
-# restart where it stagnates (A T has eigenvalues with negative real part once smoothing is on)
-@pytest.mark.parametrize("name,restart", [("os-96x64-l4s2", 8), ("mrcm-48x40", 8), ("dirichlet-all", 8),
-                                          ("os-48x40", 100), ("ragged-60x36", 100), ("uneven-61x45", 100),
+# Short restarts (4, 8) cover the restart path; GMRES(30) is the workloads' setting.  The last case
+# is the non-overlapping MRCM followed by a sweep: without oversampling the sweep does not make
+# I - A T a contraction (Appendix A), GMRES(30) stagnates there, and it takes a Krylov dimension
+# it never reaches.
+@pytest.mark.parametrize("name,restart", [("os-96x64-l4s2", 4), ("mrcm-48x40", 8), ("dirichlet-all", 4),
+                                          ("os-48x40", 30), ("ragged-60x36", 30), ("uneven-61x45", 30),
                                           ("uneven-50x37-l0", 100)])
 def test_gmres_matches_oracle(mrcm, name, restart):
     prob, q = _case(name)
@@ -210,19 +212,21 @@ def test_gmres_matches_oracle(mrcm, name, restart):
     assert info["status"] == 0 and info["rel_res"] <= q.tol
     assert info["iterations"] == info_ref["iterations"]
     assert info["restarts"] == info_ref["restarts"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-9
+    if restart < 30:
+        assert info["restarts"] > 0
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
     hist_ref = np.array(info_ref["history"])
     assert len(info["history"]) == len(hist_ref)
     assert np.allclose(info["history"], hist_ref, rtol=1e-6, atol=1e-12 * hist_ref[0])
     ux, uy = info["u"]
-    assert _rel(ux.cpu().numpy(), info_ref["u"][0]) < 1e-9
-    assert _rel(uy.cpu().numpy(), info_ref["u"][1]) < 1e-9
+    assert _rel(ux.cpu().numpy(), info_ref["u"][0]) < 1e-10
+    assert _rel(uy.cpu().numpy(), info_ref["u"][1]) < 1e-10
 
 
 def test_fp32_local_solves_reach_fp64_tolerance(mrcm):
     prob, q = _case("os-96x64-l4s2")
     q.tol = 1e-8
-    q.restart = 100
+    q.restart = 30
     p_ref, info_ref, _ = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       restart=q.restart)
@@ -269,7 +273,6 @@ def test_edge_cases(mrcm):
 def test_workspace_too_small_and_deterministic(mrcm):
     import ctypes as C
     prob, q = _case("os-48x40")
-    q.restart = 100  # GMRES(30) stagnates on this case (see test_gmres_matches_oracle)
     need = mrcm.footprint(prob, q)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     K = torch.as_tensor(prob.K.ravel(), device="cuda")
@@ -289,7 +292,6 @@ def test_profile_records_only_the_selected_phases(mrcm):
     """Per-phase event timing restricted to one phase: that phase alone carries launches and time,
     and the solution is the unprofiled one."""
     prob, q = _case("os-48x40")
-    q.restart = 100
     s = mrcm.Solver(prob, q)
     s.factor()
     ref, _ = s.solve()
@@ -316,22 +318,28 @@ def test_profile_records_only_the_selected_phases(mrcm):
 
 
 def test_full_size_channels_512_matches_oracle(mrcm):
-    """The 512 x 512 channelised workload (contrast 1e6) in the configuration the benchmark times."""
+    """The 512 x 512 channelised workload (contrast 1e6, 16 x 16 subdomains of 32 x 32, l = 4, two
+    sweeps, FP64, GMRES(30)) in the configuration the benchmark times, against a full oracle solve:
+    iterations equal, p and the face velocities to 1e-10, and one application of T."""
     prob, q = W.channels(512, seed=1)
     s = mrcm.Solver(prob, q)
     s.factor()
-    pre = _oracle(prob, q)
+    p, info = s.solve(fluxes=True)
+    p_ref, info_ref, pre = oracle_solve(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f, sub=q.sub,
+                                        l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
+                                        tol_relative=True, restart=q.restart, max_iter=q.max_iter)
+    assert info["status"] == 0 and info["rel_res"] <= 1e-8
+    assert info["iterations"] == info_ref["iterations"]
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
+    assert _rel(info["u"][0].cpu().numpy(), info_ref["u"][0]) < 1e-10
+    assert _rel(info["u"][1].cpu().numpy(), info_ref["u"][1]) < 1e-10
+    # T on a random vector: the local Robin and Dirichlet problems of a contrast-1e6 field have
+    # condition numbers near 1e9, so two backward-stable elimination orders agree to about
+    # eps * 1e9 ~ 1e-7 at worst; measured about 2e-11
     r = np.random.default_rng(5).standard_normal(prob.K.shape)
     z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
-    zr = pre.apply(r)
-    # contrast 1e6: local condition numbers reach ~1e9, so two backward-stable elimination orders
-    # agree to about eps * cond
-    assert _rel(z, zr) < 1e-6
-    p, info = s.solve()
-    assert info["status"] == 0 and info["rel_res"] <= 1e-8
-    A_p = grid.matvec(pre.T, p.cpu().numpy().reshape(prob.K.shape), 2)
-    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
-    assert np.linalg.norm(b - A_p) <= 1.0001e-8 * np.linalg.norm(b)
+    assert _rel(z, pre.apply(r)) < 1e-9
+    s.close()
 
 
 # a diagonal permeability tensor, components drawn independently: every face takes the component
@@ -349,7 +357,7 @@ def _tensor_case(name):
     pk, qk = TENSOR_CASES[name]
     prob = W.random_problem(pk["n"], seed=pk["seed"], contrast=1e3, bc_kind=pk.get("bc_kind"), tensor=True)
     q = W.Params(**qk)
-    q.tol, q.restart = 1e-10, 100
+    q.tol, q.restart = 1e-10, 30
     return prob, q
 
 
@@ -380,7 +388,7 @@ def test_diagonal_tensor_matches_oracle(mrcm, name):
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=1e-10,
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
     s.close()
 
 
@@ -400,7 +408,7 @@ def test_banded_coupling_solve_above_the_dense_limit(mrcm):
     # 44 x 44 subdomains: 2E = 7,568 coupling unknowns, above the explicit-inverse limit, so every
     # apply runs the band LU solve (the path of the 2048 x 2048 workload's 16,128 unknowns)
     prob = W.random_problem((264, 264, 1), seed=13, contrast=1e3)
-    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=100, max_iter=300)
+    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=30, max_iter=300)
     s = mrcm.Solver(prob, q)
     s.factor()
     s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
@@ -416,7 +424,7 @@ def test_banded_coupling_solve_above_the_dense_limit(mrcm):
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
     s.close()
 
 
@@ -444,7 +452,7 @@ def test_piecewise_linear_interface_spaces_match_oracle(mrcm, name):
 @pytest.mark.parametrize("name", ["os-96x64-l4s2", "uneven-61x45"])
 def test_piecewise_linear_gmres_matches_oracle(mrcm, name):
     prob, q = _case(name)
-    q.iface_degree, q.tol, q.restart = 1, 1e-9, 100
+    q.iface_degree, q.tol, q.restart = 1, 1e-9, 30
     s = mrcm.Solver(prob, q)
     s.factor()
     p, info = s.solve()
@@ -452,7 +460,7 @@ def test_piecewise_linear_gmres_matches_oracle(mrcm, name):
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter, iface_degree=1)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-8
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
     s.close()
 
 
@@ -474,7 +482,6 @@ def test_autotuned_launch_shapes_give_identical_results(mrcm):
     # the tuned variants (line-block ring depth of the local solves, cluster size of the coupling
     # factorisation) change how data is staged, never the arithmetic
     prob, q = _case("os-96x64-l4s2")
-    q.restart = 100
     r = torch.as_tensor(np.random.default_rng(71).standard_normal(prob.cells), device="cuda")
     out = {}
     try:
@@ -498,7 +505,7 @@ def test_autotuned_launch_shapes_give_identical_results(mrcm):
 
 def test_full_size_quarter_five_spot_64_matches_oracle(mrcm):
     """The 64 x 64 quarter-five-spot workload (log-normal field, 4 x 4 subdomains of 16 x 16, l = 2,
-    one sweep, FP64) at its full size against the oracle: iterations equal, p and u to 1e-9."""
+    one sweep, FP64, GMRES(30)) at its full size against the oracle: iterations equal, p and u to 1e-10."""
     prob, q = W.quarter_five_spot(64, seed=1)
     s = mrcm.Solver(prob, q)
     s.factor()
@@ -507,21 +514,30 @@ def test_full_size_quarter_five_spot_64_matches_oracle(mrcm):
                                       l=q.oversample, smooth_steps=q.smooth_steps, alpha=q.alpha, tol=q.tol,
                                       tol_relative=True, restart=q.restart, max_iter=q.max_iter)
     assert info["status"] == 0 and info["iterations"] == info_ref["iterations"]
-    assert _rel(p.cpu().numpy(), p_ref) < 1e-9
-    assert _rel(info["u"][0].cpu().numpy(), info_ref["u"][0]) < 1e-9
-    assert _rel(info["u"][1].cpu().numpy(), info_ref["u"][1]) < 1e-9
+    assert _rel(p.cpu().numpy(), p_ref) < 1e-10
+    assert _rel(info["u"][0].cpu().numpy(), info_ref["u"][0]) < 1e-10
+    assert _rel(info["u"][1].cpu().numpy(), info_ref["u"][1]) < 1e-10
     s.close()
 
 
-def test_full_size_lognormal_2048_mixed_precision(mrcm):
-    """The 2048 x 2048 log-normal workload (variance 4, correlation length 0.05, 64 x 64 subdomains of
-    32 x 32, l = 2; two sweeps, as one leaves GMRES stagnating on these fields) at full size, with
-    16,128 coupling unknowns on the band path.  Properties that hold at any size: the true FP64
-    residual of the returned p meets 1e-8 for FP64 and for FP32 local solves, and the mixed form
-    needs at most one iteration more than the FP64 one (whose counts equal the oracle's on every
-    case small enough to run it)."""
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "workloads_oracle.json")
+    return json.load(open(path))["results"][name]
+
+
+def test_full_size_lognormal_2048_matches_oracle(mrcm):
+    """The 2048 x 2048 log-normal workload (variance 4, correlation length 0.05, 64 x 64 subdomains
+    of 32 x 32, l = 2, one sweep, GMRES(30); 16,128 coupling unknowns on the blocked band path) at
+    full size.  FP64: iterations equal to the oracle's stored count and p equal to its stored
+    pressure at 1024 sampled cells to 1e-10; one application of T against the oracle's.  Mixed
+    (FP32 local factors and solves, FP64 GMRES): the true FP64 residual meets 1e-8 and p is within
+    1e-6 of the oracle's (the FP32 solves make T a different operator; the outer residual bounds
+    the error through the conditioning of A)."""
+    gold = _golden("lognormal-2048")
+    idx, ps = np.asarray(gold["sample_cells"]), np.asarray(gold["p_sample"])
     prob, q = W.lognormal(2048, seed=1)
-    q.smooth_steps, q.restart, q.max_iter = 2, 100, 300
     T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
     b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
     its = {}
@@ -531,11 +547,23 @@ def test_full_size_lognormal_2048_mixed_precision(mrcm):
         s.factor()
         p, info = s.solve()
         assert info["status"] == 0, (prec, info)
-        r = b - grid.matvec(T, p.cpu().numpy().reshape(prob.K.shape), 2)
+        pn = p.cpu().numpy()
+        r = b - grid.matvec(T, pn.reshape(prob.K.shape), 2)
         assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(b), prec
+        err = np.linalg.norm(pn[idx] - ps) / np.linalg.norm(ps)
         its[prec] = info["iterations"]
+        if prec == W.PREC_FP64:
+            assert info["iterations"] == gold["iterations"]
+            assert err < 1e-10, err
+            pre = MRCMOS(prob.K, prob.h, 2, prob.bc_kind, q.sub, q.oversample, q.smooth_steps, q.alpha)
+            rv = np.random.default_rng(7).standard_normal(prob.K.shape)
+            z = s.apply_precond(torch.as_tensor(rv.ravel(), device="cuda")).cpu().numpy()
+            assert _rel(z, pre.apply(rv)) < 1e-10
+            del pre
+        else:
+            assert err < 1e-6, err
         s.close()
-    assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 1, its
+    assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 2, its
 
 
 @pytest.mark.parametrize("contrast", [1e6, 1e9])
@@ -543,7 +571,7 @@ def test_high_contrast_matches_oracle_within_conditioning(mrcm, contrast):
     # K spread over 6 and 9 decades: local condition numbers reach about contrast * (box size)^2,
     # so the two elimination orders agree to eps times that, not to 1e-10
     prob = W.random_problem((48, 40, 1), seed=17, contrast=contrast)
-    q = W.Params(sub=(8, 8, 1), oversample=2, smooth_steps=1, tol=1e-9, restart=100)
+    q = W.Params(sub=(8, 8, 1), oversample=2, smooth_steps=1, tol=1e-9, restart=30)
     s = mrcm.Solver(prob, q)
     s.factor()
     pre = _oracle(prob, q)
@@ -566,7 +594,6 @@ def test_mixed_precision_variants_reach_fp64_tolerance(mrcm, variant):
         prob, q = _tensor_case("tensor-ragged-60x36")
     else:
         prob, q = _case("uneven-61x45" if variant == "uneven" else "os-96x64-l4s2")
-        q.restart = 100
     q.tol = 1e-8
     if variant == "degree1":
         q.iface_degree = 1
@@ -594,7 +621,7 @@ def test_banded_coupling_solve_degree1_above_the_dense_limit(mrcm):
     # piecewise-linear spaces on the 44 x 44 partition: 15,136 coupling unknowns with twice the band
     # width, so the blocked substitution carries about 700 rows from block to block
     prob = W.random_problem((264, 264, 1), seed=13, contrast=1e3)
-    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=100, max_iter=300, iface_degree=1)
+    q = W.Params(sub=(6, 6, 1), oversample=2, smooth_steps=2, tol=1e-9, restart=30, max_iter=300, iface_degree=1)
     s = mrcm.Solver(prob, q)
     s.factor()
     s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)

@@ -23,22 +23,20 @@ def _mix():
         out.append(W.quarter_five_spot(64, seed=seed))
     for seed, prec in ((3, W.PREC_FP64), (4, W.PREC_FP32)):
         prob, q = W.lognormal(128, seed=seed, variance=2.0, corr=0.1, sub=32, oversample=2, smooth_steps=1, prec=prec)
-        q.restart = 120
         out.append((prob, q))
     prob, q = W.channels(128, seed=5, sub=32, oversample=4, smooth_steps=2)
     out.append((prob, q))
     prob, q = W.lognormal(96, seed=6, variance=1.0, corr=0.1, sub=16, oversample=2, smooth_steps=1, prec=W.PREC_FP64)
-    q.restart = 120
     out.append((prob, q))
     # the variants: a diagonal permeability tensor, piecewise-linear interface spaces, a grid the
     # subdomain size does not divide, multiplicative smoothing
     out.append((W.random_problem((96, 64, 1), seed=21, contrast=1e3, tensor=True),
-                W.Params(sub=(16, 16, 1), oversample=2, smooth_steps=2, restart=100)))
+                W.Params(sub=(16, 16, 1), oversample=2, smooth_steps=2, restart=30)))
     prob, q = W.channels(128, seed=7, sub=32, oversample=4, smooth_steps=2)
     q.iface_degree = 1
     out.append((prob, q))
     out.append((W.random_problem((100, 70, 1), seed=22, contrast=1e3),
-                W.Params(sub=(32, 32, 1), oversample=2, smooth_steps=1, restart=100)))
+                W.Params(sub=(32, 32, 1), oversample=2, smooth_steps=1, restart=30)))
     prob, q = W.quarter_five_spot(64, seed=8)
     q.smooth_kind = 1
     out.append((prob, q))
@@ -106,4 +104,32 @@ def test_admission_by_footprint_and_cancel(mrcm):
     res = _wait(srv, [a, b])
     assert res[a][0] == mrcm.MRCM_OK
     assert res[b][0] == mrcm.MRCM_ERR_CANCELLED
+    srv.close()
+
+
+def test_cancel_a_running_request(mrcm):
+    # a solve whose tolerance is out of reach runs until it is cancelled; the cancel is seen at the
+    # next GMRES step, the request finishes as cancelled with the steps it ran, its arena block is
+    # released (the stream idle first) and the server goes on serving
+    prob, q = W.lognormal(512, seed=9, variance=2.0, corr=0.1, sub=32, oversample=2, smooth_steps=1, prec=W.PREC_FP64)
+    q.tol, q.max_iter = 1e-15, 20000
+    srv = mrcm.Server(2 << 30, max_inflight=2)
+    t = srv.submit(prob, q)
+    t0 = time.time()
+    while srv.stats()["running"] == 0:
+        assert time.time() - t0 < 60.0
+        time.sleep(0.002)
+    time.sleep(0.5)   # past the set-up, inside GMRES
+    assert srv.poll(t) is None
+    srv.cancel(t)
+    res = _wait(srv, [t], timeout=60.0)
+    rc, _p, info = res[t]
+    assert rc == mrcm.MRCM_ERR_CANCELLED
+    assert 0 < info["iterations"] < q.max_iter
+    small, sq = W.quarter_five_spot(64, seed=3)
+    t2 = srv.submit(small, sq)
+    r2 = _wait(srv, [t2])
+    assert r2[t2][0] == mrcm.MRCM_OK
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 1 and st["running"] == 0
     srv.close()
