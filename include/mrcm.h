@@ -98,6 +98,10 @@ typedef struct mrcm_params {
                                scaled to [-1, 1] over the side); each Robin side then carries
                                1 + iface_degree coupling unknowns and each interface 2 (1 + iface_degree)
                                rows of Eq. 13-14 */
+  int32_t coarse_pivoting;  /* the band LU of the coupling matrix G: 0 (the default) factors it without
+                               row interchanges over the whole GPU and falls back to partial pivoting
+                               when a pivot is zero or an entry grows past 1e6 times the largest entry
+                               of G; 1 always uses partial pivoting (slower: one column at a time) */
 } mrcm_params;
 
 enum { MRCM_SMOOTH_ADDITIVE = 0, MRCM_SMOOTH_MULTIPLICATIVE = 1 };

@@ -341,13 +341,17 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
   }
   // The factorisations depend only on A and are latency-bound (a barrier per column), so
-  // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 run on a second
-  // stream beside the oversampled Robin factors and the informed spaces of step 2, and the basis
-  // solves wait for them.
+  // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 and then the
+  // Dirichlet factors of the oversampled regions (the smoothing of step 4) run on a second stream
+  // beside the oversampled Robin factors and the informed spaces of step 2; the basis solves wait
+  // for the first, the end of the set-up for the second.  The two chains take about the same time,
+  // so the second stream is done by the time the coupling factorisation (a cooperative launch
+  // holding one CTA on every SM) starts.
   if (!h->side) {
     CK(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     CK(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+    CK(h, cudaEventCreateWithFlags(&h->omega_ev, cudaEventDisableTiming));
   }
   CK(h, cudaEventRecord(h->fork_ev, st));
   CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
@@ -358,9 +362,15 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
     CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
   }
+  const bool smooth = h->prm.smooth_steps > 0;
   {
     Phase ph(h, MRCM_PH_FACTOR_OMEGA, h->side);
     CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, h->side));
+  }
+  CK(h, cudaEventRecord(h->omega_ev, h->side));
+  if (smooth) {
+    Phase ph(h, MRCM_PH_FACTOR_OHAT_DIRICHLET, h->side);
+    CK(h, launch_factor(g, BOX_OHAT_DIRICHLET, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_d), fp32, flags, h->side));
   }
   CK(h, cudaEventRecord(h->join_ev, h->side));
   {
@@ -369,21 +379,21 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
       CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st));
   }
   // MRCM-OS step 3: multiscale basis functions from the local Robin factors
-  CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
+  CK(h, cudaStreamWaitEvent(st, h->omega_ev, 0));
   {
     Phase ph(h, MRCM_PH_BASIS, st);
     for (int q = 0; q < P.nq; ++q)
       CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), q, at<double>(h, L.psi),
                          at<double>(h, L.mom), at<int>(h, L.flags), st));
   }
-  // coupling system (Eq. 13-14)
+  // coupling system (Eq. 13-14): band LU without row interchanges over the whole GPU first; the
+  // pivoted factorisation only if that one reports a zero pivot or element growth (or if the
+  // caller asks for pivoting)
   CoarseDev c = coarse(h);
-  bool forked = false;
-  {
-    Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
-    CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
-    // the factorisation variants give identical factors; the autotuner times each once per band
-    // shape (re-assembling G before every run, since the factorisation works in place)
+  unsigned* np_scratch = reinterpret_cast<unsigned*>(flags + 16);
+  // partial pivoting: the variants give identical factors, and the autotuner times each once per
+  // band shape (re-assembling G before every run, since the factorisation works in place)
+  auto pivoted = [&]() -> mrcm_status {
     int vars[COARSE_FACTOR_MAX_VARIANTS];
     const int nv = coarse_factor_variants(c, vars);
     const int key[6] = {c.n, c.kl, c.ku, 0, 0, 0};
@@ -393,33 +403,41 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
       return e != cudaSuccess ? e : launch_coarse_factor(c, flags, st, vars[i]);
     }, &terr);
     CK(h, terr);
-    if (pick >= 0) CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
-    // The Dirichlet factors of the oversampled regions (smoothing, MRCM-OS step 4) depend only on
-    // A: they run on a second stream alongside the coupling factorisation (one cluster, most SMs
-    // free), forked just before it, and the caller's stream waits for them at the end.
-    if (h->prm.smooth_steps > 0) {
-      CK(h, cudaEventRecord(h->fork_ev, st));
-      CK(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
-      forked = true;
-    }
+    CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
     CK(h, launch_coarse_factor(c, flags, st, pick >= 0 ? vars[pick] : -1));
-  }
-  if (forked) {
-    Phase ph(h, MRCM_PH_FACTOR_OHAT_DIRICHLET, h->side);
-    CK(h, launch_factor(g, BOX_OHAT_DIRICHLET, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_d), fp32, flags, h->side));
+    return MRCM_OK;
+  };
+  h->coarse_pivoted = h->prm.coarse_pivoting != 0;
+  {
+    Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
+    if (h->coarse_pivoted) {
+      const mrcm_status rc = pivoted();
+      if (rc != MRCM_OK) return rc;
+    } else {
+      CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
+      CK(h, launch_coarse_factor_nopiv(c, flags, np_scratch, st));
+    }
   }
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
     else CK(h, launch_coarse_blocks(c, st));
   }
-  if (forked) {
-    CK(h, cudaEventRecord(h->join_ev, h->side));
-    CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
-  }
+  CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   int hf = 0;
   CK(h, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
+  if ((hf & FLAG_NOPIV_REJECTED) && !(hf & (FLAG_NONFINITE | FLAG_SINGULAR_LOCAL | FLAG_TIMEOUT))) {
+    Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
+    CK(h, cudaMemsetAsync(flags, 0, sizeof(int), st));
+    const mrcm_status rc = pivoted();
+    if (rc != MRCM_OK) return rc;
+    if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
+    else CK(h, launch_coarse_blocks(c, st));
+    CK(h, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    h->coarse_pivoted = true;
+  }
   if (hf & FLAG_NONFINITE) return fail(h, MRCM_ERR_INVALID_ARG, "K must be positive and finite");
   if (hf & FLAG_SINGULAR_LOCAL) return fail(h, MRCM_ERR_SINGULAR, "non-positive pivot in a local factorisation");
   if (hf & FLAG_SINGULAR_COARSE) return fail(h, MRCM_ERR_SINGULAR, "zero pivot in the coupling system");

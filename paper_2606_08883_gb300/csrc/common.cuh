@@ -91,4 +91,39 @@ __device__ __forceinline__ double robin_tr(double k_in, double k_out, double are
   return 1.0 / (1.0 / tau + beta / area);
 }
 
+// Grid-wide barrier for cooperative launches (every block co-resident).  bar[0] counts arrivals
+// (zero between barriers), bar[1] is the generation.  A block that polls more than
+// BARRIER_SPIN_LIMIT times sets FLAG_TIMEOUT in *flags and returns false instead of waiting on.
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;   // ~1-2 s of polling, then give up
+
+// Returns false if the wait gave up (the flag is set; the caller returns).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned my = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    s_ok = 1;
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == my) {
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicOr(flags, FLAG_TIMEOUT);
+          s_ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 }  // namespace mrcm

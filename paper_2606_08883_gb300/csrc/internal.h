@@ -117,7 +117,8 @@ constexpr int COARSE_DENSE_MAX = 4096;   // 2E up to this size: explicit G^-1, o
 constexpr int GBB_NB = 512;              // above it: substitution steps per block of the blocked solve
 
 // flag word bits (device status)
-enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8 };
+enum : int { FLAG_SINGULAR_LOCAL = 1, FLAG_SINGULAR_COARSE = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8,
+             FLAG_NOPIV_REJECTED = 16 };   // the no-pivot coupling LU met a zero pivot or large growth
 
 }  // namespace mrcm
 
@@ -137,6 +138,7 @@ struct mrcm_ctx {
   char* ws;           // workspace base (device)
   size_t ws_bytes;
   bool factored = false;
+  bool coarse_pivoted = false;   // the last factorisation of G fell back to partial pivoting
   std::string err;
   int coarse_n;       // 2E
   std::vector<int> tab_host;  // plan tables uploaded to the device
@@ -163,11 +165,12 @@ struct mrcm_ctx {
   cudaEvent_t rb_ev[2] = {nullptr, nullptr};
   // second stream for set-up work that overlaps (the Schwarz factors), with its fork / join events
   cudaStream_t side = nullptr;
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr, omega_ev = nullptr;
   ~mrcm_ctx() {
     if (side) cudaStreamDestroy(side);
     if (fork_ev) cudaEventDestroy(fork_ev);
     if (join_ev) cudaEventDestroy(join_ev);
+    if (omega_ev) cudaEventDestroy(omega_ev);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : rb_ev)
       if (e) cudaEventDestroy(e);
@@ -233,6 +236,12 @@ cudaError_t launch_coarse_rhs(const CoarseDev& c, const double* mom0, int E, cud
 // per apply without an explicit inverse: right-hand side from mom0, then the band solve
 cudaError_t launch_coarse_solve(const CoarseDev& c, const double* mom0, int E, cudaStream_t st);
 cudaError_t launch_coarse_invert(const CoarseDev& c, double* Ginv, cudaStream_t st);
+// Band LU of G without row interchanges (identity ipiv), blocked over the whole GPU in one
+// cooperative launch; sets FLAG_NOPIV_REJECTED when a pivot is zero or not finite or an element
+// grows past NOPIV_MAX_GROWTH times the largest entry of G (the caller then factors with pivoting).
+// scratch: 8 words of device memory (barrier and statistics), zeroed by the launcher.
+constexpr double NOPIV_MAX_GROWTH = 1e6;
+cudaError_t launch_coarse_factor_nopiv(const CoarseDev& c, int* flags, unsigned* scratch, cudaStream_t st);
 // set-up of the blocked substitution (2E nq > COARSE_DENSE_MAX), after the factorisation
 cudaError_t launch_coarse_blocks(const CoarseDev& c, cudaStream_t st);
 cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);

@@ -1057,6 +1057,293 @@ cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const do
   return cudaGetLastError();
 }
 
+// ============================================================================================
+// Band LU without row interchanges, blocked over the whole GPU (one cooperative launch, one CTA
+// per SM).  In the banded home order the coupling matrix factors stably without pivoting (its
+// element growth stays near one on the workloads), so no column waits for a pivot search: for each
+// panel of NP_NB columns,
+//   1. every warp solves one row of L21 = A21 U11^-1 or one column of U12 = L11^-1 A12;
+//   2. the band part of A22 -= L21 U12 is updated in 16 x 16 tiles spread over the CTAs: CTAs 1-4
+//      update the tiles of the next diagonal block first and hand it to CTA 0, which factors it
+//      (unblocked, in shared memory) while the others update the rest (look-ahead),
+// with a grid barrier after each step.  GB300's FP64 pipe retires about two lanes per clock per SM
+// with a 64-cycle latency, so the kernel keeps dependent chains short (four partial sums per tile
+// entry, one FMA per entry in the diagonal factorisation) and issues few predicated-off FP64
+// instructions.  The factors land in the LAPACK band layout with ipiv[j] = j and
+// rdiag[j] = 1 / U(j, j), so every solve kernel takes them unchanged.  A zero or non-finite pivot,
+// or an entry larger than NOPIV_MAX_GROWTH times the largest entry of G, sets FLAG_NOPIV_REJECTED;
+// the caller then factors again with partial pivoting.
+constexpr int NP_NB = 32;
+constexpr int NP_THREADS = 256;
+constexpr int NP_TILE = 16;
+
+__device__ __forceinline__ void np_max_abs(unsigned long long* p, double v) {
+  // non-negative doubles (and NaN with the sign cleared, above +inf) order like their bit patterns
+  atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
+}
+
+// 1 / v by Newton's method x <- x (2 - v x) from a single-precision estimate: two steps take the
+// 24 correct bits of the estimate past double precision.  Values outside the single-precision range
+// take the division.
+__device__ __forceinline__ double np_recip(double v) {
+  const float vf = (float)v;
+  double x = (double)__frcp_rn(vf);
+  if (!(fabs(x) > 0.0 && fabs(x) < 1e37)) return 1.0 / v;
+  double e = fma(-v, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-v, x, 1.0);
+  return fma(x, e, x);
+}
+
+// Factors the kb x kb diagonal block at (k0, k0) held in A (already updated), writes it back with
+// rdiag and ipiv; called by every thread of one CTA.  One block barrier per column: the update of
+// step j reads column j unscaled (times the pivot's reciprocal) and writes the multipliers to Lm,
+// and the thread that forms the next pivot takes its reciprocal at once.
+__device__ void np_factor_diag(const CoarseDev& c, int k0, int kb, double (*A)[NP_NB + 1], double (*Lm)[NP_NB + 1],
+                               double& gmax, int* flags) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  static_assert(NP_THREADS == 256 && NP_NB == 32, "the diagonal factor maps 8 warps of 4 rows x 32 columns");
+  __shared__ double rps[NP_NB];
+  __shared__ int s_bad;
+  if (tid == 0) {
+    s_bad = !(A[0][0] != 0.0 && isfinite(A[0][0]));
+    rps[0] = np_recip(A[0][0]);
+  }
+  __syncthreads();
+  // warp w owns rows 4w .. 4w + 3, lane tx column tx.  Step j updates the trailing block with row j
+  // scaled by the pivot's reciprocal (one FMA per entry); column j keeps its unscaled values, which
+  // no later step touches, and the multipliers are formed from them at the end.  Warps whose rows all
+  // lie above the pivot skip the step.
+  const int tx = tid & 31, w = tid >> 5;
+  for (int j = 0; j < kb; ++j) {
+    if (4 * w + 3 > j) {
+      const double u = tx > j && tx < kb ? A[j][tx] * rps[j] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = 4 * w + k;
+        if (i > j && i < kb && tx > j && tx < kb) {
+          const double v = fma(-A[i][j], u, A[i][tx]);
+          A[i][tx] = v;
+          if (i == j + 1 && tx == j + 1) {
+            if (!(v != 0.0 && isfinite(v))) s_bad = 1;
+            rps[j + 1] = np_recip(v);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < NP_NB * NP_NB; t += nt) {
+    const int i = t >> 5, j = t & 31;
+    if (i > j && i < kb) Lm[i][j] = A[i][j] * rps[j];
+  }
+  __syncthreads();
+  const int kv = c.kl + c.ku;
+  for (int t = tid; t < kb * kb; t += nt) {
+    const int i = t / kb, j = t % kb;
+    if (i - j <= c.kl && j - i <= c.ku) {
+      const double v = i > j ? Lm[i][j] : A[i][j];
+      c.ab[(size_t)(kv + i - j) + (size_t)(k0 + j) * c.ldab] = v;
+      gmax = fmax(gmax, fabs(v));
+    }
+  }
+  for (int j = tid; j < kb; j += nt) {
+    c.rdiag[k0 + j] = rps[j];
+    c.ipiv[k0 + j] = k0 + j;
+  }
+  if (tid == 0 && s_bad) atomicOr(flags, FLAG_NOPIV_REJECTED);
+}
+
+// Loads the kb x kb diagonal block at (k0, k0) from the band (zeros outside it) into A.
+__device__ __forceinline__ void np_load_diag(const CoarseDev& c, int k0, int kb, double (*A)[NP_NB + 1]) {
+  const int kv = c.kl + c.ku;
+  for (int t = threadIdx.x; t < NP_NB * NP_NB; t += blockDim.x) {
+    const int i = t / NP_NB, j = t % NP_NB;
+    double v = 0.0;
+    if (i < kb && j < kb && i - j <= c.kl && j - i <= c.ku)
+      v = c.ab[(size_t)(kv + i - j) + (size_t)(k0 + j) * c.ldab];
+    A[i][j] = v;
+  }
+}
+
+// One 16 x 16 tile of A22 -= L21 U12 (band entries only), four partial sums per entry.
+__device__ __forceinline__ void np_tile(const CoarseDev& c, int k0, int kb, int i0, int j0, double (*sL)[NP_NB + 1],
+                                        double (*sU)[NP_TILE + 1], double& gmax) {
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku, tid = threadIdx.x;
+  double* ab = c.ab;
+  __syncthreads();
+  for (int e = tid; e < NP_TILE * NP_NB; e += NP_THREADS) {
+    const int r = e / NP_NB, q = e % NP_NB, i = i0 + r, col = k0 + q;
+    sL[r][q] = (q < kb && i < n && i - col <= kl) ? ab[(size_t)(kv + i - col) + (size_t)col * ld] : 0.0;
+    const int rr = e / NP_TILE, cc = e % NP_TILE, j = j0 + cc, row = k0 + rr;
+    sU[rr][cc] = (rr < kb && j < n && j - row <= ku) ? ab[(size_t)(kv + row - j) + (size_t)j * ld] : 0.0;
+  }
+  __syncthreads();
+  const int r = tid / NP_TILE, cc = tid % NP_TILE, i = i0 + r, j = j0 + cc;
+  if (i < n && j < n && i - j <= kl && j - i <= ku) {
+    double* a = ab + (size_t)(kv + i - j) + (size_t)j * ld;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP_NB; q += 4) {
+      s0 += sL[r][q] * sU[q][cc];
+      s1 += sL[r][q + 1] * sU[q + 1][cc];
+      s2 += sL[r][q + 2] * sU[q + 2][cc];
+      s3 += sL[r][q + 3] * sU[q + 3][cc];
+    }
+    const double v = *a - ((s0 + s1) + (s2 + s3));
+    *a = v;
+    gmax = fmax(gmax, fabs(v));
+  }
+}
+
+__global__ void __launch_bounds__(NP_THREADS) k_gbtrf_np(CoarseDev c, int* flags, unsigned* bar,
+                                                         unsigned long long* stats) {
+  __shared__ double A[NP_NB][NP_NB + 1];       // diagonal block (L11 and U11)
+  __shared__ double Lm[NP_NB][NP_NB + 1];      // multipliers of the diagonal block being factored
+  __shared__ double rd[NP_NB];                 // 1 / U11(j, j)
+  __shared__ double sL[NP_TILE][NP_NB + 1];    // tile rows of L21
+  __shared__ double sU[NP_NB][NP_TILE + 1];    // tile columns of U12
+  const int n = c.n, kl = c.kl, ku = c.ku, ld = c.ldab, kv = kl + ku;
+  double* ab = c.ab;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NP_THREADS / 32;
+  const int G = gridDim.x, b = blockIdx.x;
+  unsigned* dcount = bar + 6;                  // diagonal-block tiles updated so far (monotonic)
+  // with enough CTAs the next diagonal block's tiles go to CTAs 1..4, CTA 0 factors it, the other
+  // tiles go to the remaining CTAs
+  const bool split = G >= 8;
+  const int first_other = split ? 5 : (G > 1 ? 1 : 0), n_other = G - first_other;
+  unsigned dtarget = 0;
+  double gmax = 0.0;
+  {
+    double m = 0.0;
+    for (size_t t = (size_t)b * NP_THREADS + tid; t < (size_t)n * (kl + ku + 1); t += (size_t)G * NP_THREADS) {
+      const int j = (int)(t / (kl + ku + 1)), r = (int)(t % (kl + ku + 1));
+      const int i = j - ku + r;
+      if (i >= 0 && i < n) m = fmax(m, fabs(ab[(size_t)(kv + i - j) + (size_t)j * ld]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) np_max_abs(&stats[0], m);
+  }
+  if (b == 0) {
+    const int kb = min(NP_NB, n);
+    np_load_diag(c, 0, kb, A);
+    __syncthreads();
+    np_factor_diag(c, 0, kb, A, Lm, gmax, flags);
+  }
+  if (!grid_barrier(bar, flags)) return;
+  for (int k0 = 0; k0 < n; k0 += NP_NB) {
+    const int kb = min(NP_NB, n - k0), r0 = k0 + kb;
+    const int nr = min(kl, n - r0), nc = min(ku, n - r0);
+    if (nr <= 0 && nc <= 0) break;
+    np_load_diag(c, k0, kb, A);
+    for (int j = tid; j < NP_NB; j += NP_THREADS) rd[j] = j < kb ? c.rdiag[k0 + j] : 0.0;
+    __syncthreads();
+    for (int task = b * nw + warp; task < nr + nc; task += G * nw) {
+      if (task < nr) {
+        const int i = r0 + task, col = k0 + lane;
+        double acc = (lane < kb && i - col <= kl) ? ab[(size_t)(kv + i - col) + (size_t)col * ld] : 0.0;
+        double x = 0.0;
+        for (int m = 0; m < kb; ++m) {
+          const double xm = __shfl_sync(0xffffffffu, acc, m) * rd[m];
+          if (lane == m) x = xm;
+          if (lane > m) acc -= xm * A[m][lane];
+        }
+        if (lane < kb && i - col <= kl) {
+          ab[(size_t)(kv + i - col) + (size_t)col * ld] = x;
+          gmax = fmax(gmax, fabs(x));
+        }
+      } else {
+        const int j = r0 + task - nr, row = k0 + lane;
+        double acc = (lane < kb && j - row <= ku) ? ab[(size_t)(kv + row - j) + (size_t)j * ld] : 0.0;
+        for (int m = 0; m < kb; ++m) {
+          const double ym = __shfl_sync(0xffffffffu, acc, m);
+          if (lane > m) acc -= A[lane][m] * ym;
+        }
+        if (lane < kb && j - row <= ku) {
+          ab[(size_t)(kv + row - j) + (size_t)j * ld] = acc;
+          gmax = fmax(gmax, fabs(acc));
+        }
+      }
+    }
+    if (!grid_barrier(bar, flags)) return;
+    const int ntr = (nr + NP_TILE - 1) / NP_TILE, ntc = (nc + NP_TILE - 1) / NP_TILE;
+    const int kb2 = min(NP_NB, n - r0);
+    const int dt = kb2 > 0 ? (kb2 + NP_TILE - 1) / NP_TILE : 0;
+    // diagonal-block tiles: CTAs 1..dt^2 (split) or CTA 0
+    if (split ? (b >= 1 && b <= dt * dt) : b == 0) {
+      for (int d = split ? b - 1 : 0; d < (split ? b : dt * dt); ++d) {
+        const int ti = d / dt, tj = d % dt;
+        np_tile(c, k0, kb, r0 + ti * NP_TILE, r0 + tj * NP_TILE, sL, sU, gmax);
+      }
+      if (split) {
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          atomicAdd(dcount, 1u);
+        }
+      }
+    }
+    if (split) dtarget += dt * dt;
+    // the other tiles of the band, round robin over the remaining CTAs
+    if (b >= first_other || n_other == 0) {
+      for (int t = (n_other > 0 ? b - first_other : 0); t < ntr * ntc; t += (n_other > 0 ? n_other : 1)) {
+        const int ti = t / ntc, tj = t % ntc;
+        if (ti < dt && tj < dt) continue;
+        const int i0 = r0 + ti * NP_TILE, j0 = r0 + tj * NP_TILE;
+        if (i0 - (j0 + NP_TILE - 1) > kl || j0 - (i0 + NP_TILE - 1) > ku) continue;
+        np_tile(c, k0, kb, i0, j0, sL, sU, gmax);
+      }
+    }
+    if (b == 0 && kb2 > 0) {
+      if (split && tid == 0) {
+        volatile unsigned* dc = dcount;
+        long long spins = 0;
+        while (*dc < dtarget) {
+          if (++spins > BARRIER_SPIN_LIMIT) {
+            atomicOr(flags, FLAG_TIMEOUT);
+            break;
+          }
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      np_load_diag(c, r0, kb2, A);
+      __syncthreads();
+      np_factor_diag(c, r0, kb2, A, Lm, gmax, flags);
+    }
+    if (!grid_barrier(bar, flags)) return;
+  }
+  for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) np_max_abs(&stats[1], gmax);
+  if (!grid_barrier(bar, flags)) return;
+  if (b == 0 && tid == 0) {
+    const double g0 = __longlong_as_double((long long)stats[0]), g1 = __longlong_as_double((long long)stats[1]);
+    if (!(g1 <= NOPIV_MAX_GROWTH * g0)) atomicOr(flags, FLAG_NOPIV_REJECTED);
+  }
+}
+
+
+cudaError_t launch_coarse_factor_nopiv(const CoarseDev& c, int* flags, unsigned* scratch, cudaStream_t st) {
+  if (c.n == 0) return cudaSuccess;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gbtrf_np, NP_THREADS, 0);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  // barrier words [0, 2), the two statistics (8-byte aligned at word 2) and the diagonal-tile
+  // counter (word 6) start at zero
+  e = cudaMemsetAsync(scratch, 0, 8 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  CoarseDev cc = c;
+  unsigned* bar = scratch;
+  unsigned long long* stats = reinterpret_cast<unsigned long long*>(scratch + 2);
+  void* args[] = {(void*)&cc, (void*)&flags, (void*)&bar, (void*)&stats};
+  e = cudaLaunchCooperativeKernel((const void*)k_gbtrf_np, dim3(sms), dim3(NP_THREADS), args, 0, st);
+  count_launch(1);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_coarse_assemble(const CoarseDev& c, const double* mom, int E, cudaStream_t st) {
   if (E == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(c.ab, 0, sizeof(double) * (size_t)c.ldab * c.n, st);

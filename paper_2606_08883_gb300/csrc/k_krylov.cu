@@ -159,38 +159,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual_norm(Geo g, const doub
 // an arrival counter plus a generation word, polled with a bounded spin that sets FLAG_TIMEOUT and
 // returns instead of waiting forever.
 // ============================================================================================
-constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;   // ~1-2 s of polling, then give up
-
-// Returns false if the wait gave up (the flag is set; the caller returns).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* flags) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned my = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    s_ok = 1;
-    if (arrived == gridDim.x - 1) {
-      bar[0] = 0u;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == my) {
-        if (++spins > BARRIER_SPIN_LIMIT) {
-          atomicOr(flags, 8);
-          s_ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // One Arnoldi step (inner step j) in a single cooperative launch, with the modified
 // Gram-Schmidt coefficients obtained from one global reduction.  MGS computes
 //   h_i = (w - sum_{k<i} h_k v_k, v_i) = a_i - sum_{k<i} (v_k, v_i) h_k,   a_i = (w, v_i),

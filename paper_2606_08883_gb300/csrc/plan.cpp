@@ -37,6 +37,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   if (q.smooth_kind != MRCM_SMOOTH_ADDITIVE && q.smooth_kind != MRCM_SMOOTH_MULTIPLICATIVE)
     return "smooth_kind must be MRCM_SMOOTH_ADDITIVE or MRCM_SMOOTH_MULTIPLICATIVE";
   if (q.iface_degree != 0 && q.iface_degree != 1) return "iface_degree must be 0 or 1";
+  if (q.coarse_pivoting != 0 && q.coarse_pivoting != 1) return "coarse_pivoting must be 0 or 1";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
     if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";

@@ -50,6 +50,7 @@ class Params:
     local_prec: int = PREC_FP64
     smooth_kind: int = 0          # 0 additive, 1 multiplicative multicolour Schwarz sweeps
     iface_degree: int = 0         # 0 piecewise-constant, 1 piecewise-linear side functions
+    coarse_pivoting: int = 0      # 0 no-pivot coupling LU with a pivoted fallback, 1 always pivoted
 
 
 # ---------------------------------------------------------------------------------------------

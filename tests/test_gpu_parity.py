@@ -482,6 +482,7 @@ def test_autotuned_launch_shapes_give_identical_results(mrcm):
     # the tuned variants (line-block ring depth of the local solves, cluster size of the coupling
     # factorisation) change how data is staged, never the arithmetic
     prob, q = _case("os-96x64-l4s2")
+    q.coarse_pivoting = 1   # the pivoted coupling LU is the autotuned one (its variants give identical factors)
     r = torch.as_tensor(np.random.default_rng(71).standard_normal(prob.cells), device="cuda")
     out = {}
     try:
@@ -633,3 +634,28 @@ def test_banded_coupling_solve_degree1_above_the_dense_limit(mrcm):
     assert _rel(s.debug(mrcm.MRCM_DBG_COARSE), parts["c"]) < 1e-9
     assert _rel(z, parts["z"]) < 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("name,degree", [("os-96x64-l4s2", 0), ("uneven-61x45", 0), ("mrcm-48x40", 1),
+                                         ("dirichlet-all", 1)])
+def test_coupling_lu_without_pivoting_matches_the_pivoted_one(mrcm, name, degree):
+    # the coupling matrix is factored without row interchanges over the whole GPU unless a pivot is
+    # zero or an entry grows; the coefficients c and T agree with the partially pivoted factors and
+    # with the oracle's (LAPACK getrf) to rounding
+    prob, q = _case(name)
+    q.iface_degree = degree
+    pre = _oracle(prob, q)
+    r = np.random.default_rng(81).standard_normal(prob.K.shape)
+    parts = pre.apply_parts(r)
+    out = {}
+    for piv in (0, 1):
+        q.coarse_pivoting = piv
+        s = mrcm.Solver(prob, q)
+        s.factor()
+        s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+        z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+        out[piv] = (s.debug(mrcm.MRCM_DBG_COARSE), z)
+        assert _rel(out[piv][0], parts["c"]) < 1e-9
+        assert _rel(z, parts["z"]) < 1e-10
+        s.close()
+    assert _rel(out[0][0], out[1][0]) < 1e-11
