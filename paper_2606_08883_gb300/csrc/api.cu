@@ -714,7 +714,7 @@ mrcm_status mrcm_measure_fp64_peak(double* tflops_out, void* stream) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(nullptr, MRCM_ERR_CUDA, "no CUDA device");
-  const int blocks = 4 * sms, threads = 256, iters = 4096;
+  const int blocks = 4 * sms, threads = 256, iters = 1024;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float best = 0.0f;
   cudaError_t err = cudaEventCreate(&e0);
