@@ -124,6 +124,7 @@ def config_dict(args, prob, q):
             "subdomains": f"{-(-prob.n[0] // q.sub[0])}x{-(-prob.n[1] // q.sub[1])} of {q.sub[0]}x{q.sub[1]}",
             "oversample": q.oversample, "smooth_steps": q.smooth_steps, "alpha": q.alpha, "restart": q.restart,
             "tol_relative": q.tol, "local_prec": args.prec, "krylov_prec": "fp64",
+            "refine_setup": int(getattr(q, "refine_setup", 0)),
             "smoothing": getattr(args, "smooth", "additive"), "iface_degree": int(getattr(args, "degree", 0)),
             "autotune": getattr(args, "autotune", "on"), "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single-gpu"}
@@ -639,7 +640,21 @@ def mrcm_arm(args):
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.cells,
                "d2h_bytes_per_step": 8 * prob.cells}
     solver.close()
-    # the plain FP64 form of the same problem (mixed workloads): same timing, fewer steps
+    # the mixed form without the refinement of its set-up solves, and the plain FP64 form of the
+    # same problem (mixed workloads): same timing, fewer steps
+    unrefined_form = None
+    if args.prec == "fp32" and not args.no_fp64_form and q.refine_setup:
+        probr, qr = workload(args, rank)
+        qr.refine_setup = 0
+        sr = mrcm.Solver(probr, qr, device=dev)
+        kr = max(1, min(args.steps, 5))
+        tr, itr, pr, infor = timed_solves(sr, kr, max(1, min(args.warmup, 2)), stream, dev, flush, barrier)
+        vr, totr = aggregate(sum(tr), kr, world, dist, dev)
+        unrefined_form = {"value": vr, "unit": UNIT, "steps": kr, "ms_per_step": totr / kr,
+                          "iterations": int(statistics.median(itr)), "rel_res": infor["rel_res"],
+                          "err_vs_oracle": err_vs_oracle(pr, rec) if rec else None,
+                          "what": "FP32 set-up solves not refined (refine_setup = 0)"}
+        sr.close()
     fp64_form = None
     if args.prec == "fp32" and not args.no_fp64_form:
         prob64, q64 = workload(args, rank, "fp64")
@@ -667,7 +682,7 @@ def mrcm_arm(args):
         "rel_res": info["rel_res"],
         "oracle": ({"iterations": rec["iterations"], "err_vs_oracle": err, "sample_cells": len(rec["sample_cells"]),
                     "source": "tests/golden/workloads_oracle.json (FP64 oracle, seed 1)"} if rec else None),
-        "fp64_form": fp64_form,
+        "fp64_form": fp64_form, "unrefined_form": unrefined_form,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "setup_ms": setup_ms, "solve_ms": solve_ms,
         "phases_ms_per_step": {k: round(v[0], 4) for k, v in prof_all.items()},

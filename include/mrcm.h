@@ -102,6 +102,10 @@ typedef struct mrcm_params {
                                row interchanges over the whole GPU and falls back to partial pivoting
                                when a pivot is zero or an entry grows past 1e6 times the largest entry
                                of G; 1 always uses partial pivoting (slower: one column at a time) */
+  int32_t refine_setup;     /* with local_prec = MRCM_PREC_FP32: 1 refines the set-up solves (informed
+                               spaces and basis functions) once against the FP64 box operators, which
+                               brings the GMRES count to the FP64 one at the cost of a longer set-up;
+                               0 (the default) does not.  Ignored for FP64 local solves. */
 } mrcm_params;
 
 enum { MRCM_SMOOTH_ADDITIVE = 0, MRCM_SMOOTH_MULTIPLICATIVE = 1 };

@@ -358,6 +358,9 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   // MRCM-OS step 2: informed multiplier spaces from the oversampled Robin problems (Eq. 15); the
   // oversampled factors are submitted first, since the informed spaces wait for them
   CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * P.nq * L.smax, st));
+  // FP32 set-up solves refined once against the FP64 box operators (refine_setup)
+  const bool refine = fp32 && h->prm.refine_setup != 0;
+  if (refine && P.l > 0) CK(h, launch_line_coef(g, BOX_OHAT_ROBIN, at<double>(h, L.coef_o), st));
   if (P.l > 0) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
     CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
@@ -366,6 +369,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   {
     Phase ph(h, MRCM_PH_FACTOR_OMEGA, h->side);
     CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, h->side));
+    if (refine) CK(h, launch_line_coef(g, BOX_OMEGA_ROBIN, at<double>(h, L.coef_l), h->side));
   }
   CK(h, cudaEventRecord(h->omega_ev, h->side));
   if (smooth) {
@@ -376,7 +380,8 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   {
     Phase ph(h, MRCM_PH_INFORMED, st);
     for (int q = 0; q < P.nq; ++q)
-      CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st));
+      CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st,
+                            refine ? at<double>(h, L.coef_o) : nullptr));
   }
   // MRCM-OS step 3: multiscale basis functions from the local Robin factors
   CK(h, cudaStreamWaitEvent(st, h->omega_ev, 0));
@@ -384,7 +389,8 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_BASIS, st);
     for (int q = 0; q < P.nq; ++q)
       CK(h, launch_basis(g, at<void>(h, L.Linv_loc), L.LSl, fp32, at<double>(h, L.phi), q, at<double>(h, L.psi),
-                         at<double>(h, L.mom), at<int>(h, L.flags), st));
+                         at<double>(h, L.mom), at<int>(h, L.flags), st,
+                         refine ? at<double>(h, L.coef_l) : nullptr));
   }
   // coupling system (Eq. 13-14): band LU without row interchanges over the whole GPU first; the
   // pivoted factorisation only if that one reports a zero pivot or element growth (or if the

@@ -51,6 +51,7 @@ struct Layout {
   size_t K, Ky, Tx, Ty, b, f, bcv;        // problem data (Ky: y component of K; bcv: 4 side arrays)
   size_t Linv_loc, Linv_ohat_r, Linv_ohat_d;   // line-block inverse factors
   size_t phi, psi, mom, psi0, z0, mom0;   // informed spaces, basis, side moments, apply scratch
+  size_t coef_o, coef_l;                  // FP64 line coefficients of the Robin boxes (FP32 local solves)
   size_t G, ipiv, gc;                     // coupling band LU, pivots, rhs / solution
   size_t rdiag;                           // reciprocals of the diagonal of U
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
@@ -196,9 +197,13 @@ cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const*
 enum BoxKind : int { BOX_OMEGA_ROBIN = 0, BOX_OHAT_ROBIN = 1, BOX_OHAT_DIRICHLET = 2 };
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
                           cudaStream_t st);
-cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st);
+// each cell's FP64 line coefficients [S][h][w][diagonal, x coupling, y coupling] of the boxes of
+// one kind; given to the FP32 informed and basis solves (coef), they refine once against them
+cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st);
+cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st,
+                            const double* coef = nullptr);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
-                         double* mom, int* flags, cudaStream_t st);
+                         double* mom, int* flags, cudaStream_t st, const double* coef = nullptr);
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
                               double* mom0, int* flags, cudaStream_t st);
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,

@@ -302,6 +302,30 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   if (tid == 0 && bad) atomicOr(flags, FLAG_SINGULAR_LOCAL);
 }
 
+// FP64 line coefficients [diagonal, x coupling to the right, y coupling to the line above] of every
+// cell of every box of one kind, for the refinement step of the FP32 set-up solves
+__global__ void k_line_coef(Geo g, int kind, double* __restrict__ coef) {
+  const int s = blockIdx.x;
+  const bool ohat = kind != BOX_OMEGA_ROBIN;
+  const bool robin = kind != BOX_OHAT_DIRICHLET;
+  const Box b = box_of(g, s, ohat);
+  for (int c = threadIdx.x; c < b.w * b.h; c += blockDim.x) {
+    const int J = c / b.w, x = c - J * b.w;
+    double d, o, e;
+    line_coeffs(g, b, robin, J, x, d, o, e);
+    double* cf = coef + ((size_t)s * b.w * b.h + c) * 3;
+    cf[0] = d;
+    cf[1] = o;
+    cf[2] = e;
+  }
+}
+
+cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st) {
+  k_line_coef<<<g.mx * g.my, 256, 0, st>>>(g, kind, coef);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 size_t factor_smem_bytes(int w, bool fp32, int nch) {
   const size_t e = fp32 ? 4 : 8;
   return e * nch * (4 * (size_t)w * w + 4 * (size_t)w) + 16;
@@ -378,6 +402,7 @@ struct SolveArgs {
   int* flags;          // device status word (FLAG_TIMEOUT if a bounded wait gives up)
   int colour;          // schwarz: -1 all boxes, else only the boxes of this colour (see colour_box)
   int q;               // informed, basis: the degree of the side functions this launch handles
+  const double* coef;  // FP32 informed, basis: the box's FP64 line coefficients [S][h][w][d, o, e]
 };
 
 // Degree-q function of a box side at its face t of len: 1, or the linear function of the position
@@ -517,6 +542,12 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   const int ecn = (hgt * w + 3) & ~3;
   unsigned long long* bars =                 // [hgt] line-block barriers (resident)
       reinterpret_cast<unsigned long long*>(smem_raw + ((reinterpret_cast<unsigned char*>(Ec + ecn) - smem_raw + 7) & ~(size_t)7));
+  // FP32 set-up solves (informed spaces, basis) may take one step of iterative refinement (when
+  // given the box's FP64 line coefficients): the first solution x0 is kept in X0, the residual
+  // b - A x0 is formed in FP64 and solved again, and the outputs use x0 + delta in FP64
+  const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
+  T* X0 = reinterpret_cast<T*>(                // [hgt][w][NR] first solution (REF only)
+      smem_raw + ((reinterpret_cast<unsigned char*>(bars + hgt) - smem_raw + 15) & ~(size_t)15));
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * box_stride(w, hgt, LS);
   // the couplings join the first copy group (ring) or their own group (resident)
@@ -677,6 +708,60 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   T* tA1 = tv + w * NR;
   T* tB0 = tv + 2 * w * NR;      // bottom back inputs (ping-pong)
   T* tB1 = tv + 3 * w * NR;
+  for (int pass = 0; pass < (REF ? 2 : 1); ++pass) {
+  if (REF && pass == 1) {
+    // x0 aside; r = b - A x0 in FP64 per cell (A from the box's FP64 line coefficients: diagonal d,
+    // x coupling o to the right, y coupling e to the line above), rounded into Y for the second solve
+    for (int k = tid; k < hgt * w * NR; k += nt) X0[k] = Y[k];
+    for (int k = tid; k < w * NR; k += nt) cb[k] = (T)0;
+    __syncthreads();
+    for (int c = tid; c < hgt * w; c += nt) {
+      const int J = c / w, x = c - J * w;
+      const double* cf = a.coef + (((size_t)s * hgt + J) * w + x) * 3;
+      const double d = cf[0], o = cf[1], e = cf[2];
+      const double oL = x > 0 ? cf[-3 + 1] : 0.0, eD = J + 1 < hgt ? cf[3 * (size_t)w + 2] : 0.0;
+      const int gx = b.ox + x, gy = b.oy + J;
+      const bool on = active(g, gx, gy);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        double ax = d * (double)X0[c * NR + r];
+        if (x + 1 < w) ax -= o * (double)X0[(c + 1) * NR + r];
+        if (x > 0) ax -= oL * (double)X0[(c - 1) * NR + r];
+        if (J > 0) ax -= e * (double)X0[(c - w) * NR + r];
+        if (J + 1 < hgt) ax -= eD * (double)X0[(c + w) * NR + r];
+        double bv = 0.0;
+        if (on && MODE == MODE_INFORMED && robin_side(g, s, r)) {
+          // lambda^r on the faces of side r of the oversampled box
+          const bool edge = r == 0 ? x == 0 : (r == 1 ? x == w - 1 : (r == 2 ? J == 0 : J == hgt - 1));
+          if (edge) {
+            const int ax_ = r < 2 ? 0 : 1, dir = (r & 1) ? 1 : -1;
+            double lam = 1.0;
+            if (a.q) {
+              const int lo = ax_ == 0 ? max(b.oy, 0) : max(b.ox, 0);
+              const int hi = ax_ == 0 ? min(b.oy + hgt, g.ny) : min(b.ox + w, g.nx);
+              lam = side_fn(a.q, (ax_ == 0 ? gy : gx) - lo, hi - lo);
+            }
+            bv = face_tr(g, gx, gy, ax_, dir, nullptr, nullptr) * lam;
+          }
+        } else if (on && MODE == MODE_BASIS) {
+          // t_R phi^r on the Gamma faces of the subdomain's Robin sides that touch this cell
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const bool edge = k == 0 ? x == 0 : (k == 1 ? x == w - 1 : (k == 2 ? J == 0 : J == hgt - 1));
+            if (!edge || !robin_side(g, s, k)) continue;
+            const int t = k < 2 ? J : x;
+            if (t >= side_len(g, s, k)) continue;
+            const double tr = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, nullptr, nullptr);
+            bv += tr * a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + t];
+          }
+        }
+        Y[c * NR + r] = (T)(bv - ax);
+      }
+    }
+    __syncthreads();
+    if constexpr (!RES)
+      for (int p = 0; p < NBUF - 1; ++p) issue_step(p);
+  }
   for (int st = 0; st < nsteps; ++st) {
     int A, B;
     tw.lines(st, A, B);
@@ -760,6 +845,9 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   __syncthreads();
   for (int k = tid; k < w * NR; k += nt) Y[(size_t)m * w * NR + k] = xm[k];
   __syncthreads();
+  }  // passes
+  // the solution entry idx: x0 + delta after a refinement step, else the solve's result
+  auto xv = [&](size_t idx) -> double { return REF ? (double)X0[idx] + (double)Y[idx] : (double)Y[idx]; };
 
   // ---------------- outputs
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -826,7 +914,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
     for (int k = tid; k < hgt * w * NR; k += nt) {
       const int r = k % NR, c = k / NR, J = c / w, x = c % w;
       if (active(g, b.ox + x, b.oy + J))
-        a.out[((size_t)r * g.nq + a.q) * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = (double)Y[k];
+        a.out[((size_t)r * g.nq + a.q) * g.nx * g.ny + (size_t)(b.oy + J) * g.nx + b.ox + x] = xv(k);
     }
     // moments: 16 (side, function) pairs, one warp each
     for (int pr = wid; pr < 16; pr += nw) {
@@ -848,7 +936,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
             cf[3] = area / tau;
           }
           const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + kside) * g.smax + t];
-          const double fl = tr * ((double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r] - ph);
+          const double fl = tr * (xv(((size_t)(gy - b.oy) * w + (gx - b.ox)) * NR + r) - ph);
           const double pw = area * ph + beta * fl;
 #pragma unroll
           for (int qt = 0; qt < 2; ++qt)
@@ -882,8 +970,8 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
           double Tf, beta, tau;
           gamma_face(g, s, k, f, gx, gy, ox2, oy2, Tf);
           face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, &beta, &tau);
-          const double qc = (double)Y[((gy - b.oy) * w + (gx - b.ox)) * NR + r];
-          const double qo = (double)Y[((oy2 - b.oy) * w + (ox2 - b.ox)) * NR + r];
+          const double qc = xv(((size_t)(gy - b.oy) * w + (gx - b.ox)) * NR + r);
+          const double qo = xv(((size_t)(oy2 - b.oy) * w + (ox2 - b.ox)) * NR + r);
           const double F = Tf * (qc - qo);
           const double pi = qc - F / tau;
           const double area = k < 2 ? g.hy * g.hz : g.hx * g.hz;
@@ -900,7 +988,9 @@ static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
   const size_t lines = NBUF == 0 ? (size_t)h * a.LS : 2 * NBUF * (size_t)a.LS;
   const size_t ecn = ((size_t)h * w + 3) & ~(size_t)3;
-  return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32;
+  const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
+  return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32 +
+         (REF ? sizeof(T) * (size_t)h * w * NR + 16 : 0);
 }
 
 template <typename T, int MODE, int NR, int NBUF>
@@ -987,20 +1077,20 @@ __global__ void k_phi_indicator(Geo g, double* phi) {
 }
 
 cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags,
-                            cudaStream_t st) {
+                            cudaStream_t st, const double* coef) {
   if (g.l == 0) {
     if (q > 0) return cudaSuccess;  // one launch writes the functions of every degree
     k_phi_indicator<<<g.mx * g.my, 128, 0, st>>>(g, phi);
     count_launch(1);
     return cudaGetLastError();
   }
-  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags, -1, q};
+  SolveArgs a{Linv, LS, nullptr, phi, nullptr, nullptr, flags, -1, q, coef};
   return launch_solve<MODE_INFORMED, 4>(g, a, true, fp32, st);
 }
 
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
-                         double* mom, int* flags, cudaStream_t st) {
-  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags, -1, q};
+                         double* mom, int* flags, cudaStream_t st, const double* coef) {
+  SolveArgs a{Linv, LS, phi, psi, mom, nullptr, flags, -1, q, coef};
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 

@@ -38,6 +38,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
     return "smooth_kind must be MRCM_SMOOTH_ADDITIVE or MRCM_SMOOTH_MULTIPLICATIVE";
   if (q.iface_degree != 0 && q.iface_degree != 1) return "iface_degree must be 0 or 1";
   if (q.coarse_pivoting != 0 && q.coarse_pivoting != 1) return "coarse_pivoting must be 0 or 1";
+  if (q.refine_setup != 0 && q.refine_setup != 1) return "refine_setup must be 0 or 1";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
     if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";
@@ -211,6 +212,11 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.Linv_loc = take(L.elt * S * box_stride(L.wl, L.hl, L.LSl));
   L.Linv_ohat_r = take(P.l > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
   L.Linv_ohat_d = take(q.smooth_steps > 0 ? L.elt * S * box_stride(L.wo, L.ho, L.LSo) : 0);
+  // the FP32 informed and basis solves refine once against the FP64 box operator, whose line
+  // coefficients the factorisation keeps here
+  const bool refine = q.local_prec == MRCM_PREC_FP32 && q.refine_setup;
+  L.coef_o = take(refine && P.l > 0 ? 8 * 3 * S * (size_t)L.wo * L.ho : 0);
+  L.coef_l = take(refine ? 8 * 3 * S * (size_t)L.wl * L.hl : 0);
   L.phi = take(8 * S * 16 * nq * L.smax);
   L.psi = take(8 * 4 * nq * n);
   L.mom = take(8 * S * 32 * nq * nq);

@@ -38,7 +38,8 @@ class mrcm_params(C.Structure):
     _fields_ = [("sub", C.c_int32 * 3), ("oversample", C.c_int32), ("smooth_steps", C.c_int32),
                 ("alpha", C.c_double), ("tol", C.c_double), ("tol_relative", C.c_int32),
                 ("restart", C.c_int32), ("max_iter", C.c_int32), ("local_prec", C.c_int32),
-                ("smooth_kind", C.c_int32), ("iface_degree", C.c_int32), ("coarse_pivoting", C.c_int32)]
+                ("smooth_kind", C.c_int32), ("iface_degree", C.c_int32), ("coarse_pivoting", C.c_int32),
+                ("refine_setup", C.c_int32)]
 
 
 class mrcm_result(C.Structure):
@@ -144,6 +145,7 @@ def make_params(params):
     q.smooth_kind = int(getattr(params, "smooth_kind", 0))
     q.iface_degree = int(getattr(params, "iface_degree", 0))
     q.coarse_pivoting = int(getattr(params, "coarse_pivoting", 0))
+    q.refine_setup = int(getattr(params, "refine_setup", 0))
     return q
 
 

@@ -565,6 +565,50 @@ def test_full_size_lognormal_2048_matches_oracle(mrcm):
             assert err < 1e-6, err
         s.close()
     assert its[W.PREC_FP32] <= its[W.PREC_FP64] + 2, its
+    # the set-up solves refined once in FP64: the count of the FP64 form
+    q.local_prec, q.refine_setup = W.PREC_FP32, 1
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    p, info = s.solve()
+    pn = p.cpu().numpy()
+    r = b - grid.matvec(T, pn.reshape(prob.K.shape), 2)
+    assert info["status"] == 0 and np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(b)
+    assert info["iterations"] <= its[W.PREC_FP64] + 1, (info["iterations"], its)
+    assert np.linalg.norm(pn[idx] - ps) / np.linalg.norm(ps) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("name,degree", [("lognormal-128", 0), ("lognormal-128", 1), ("os-96x64-l4s2", 0),
+                                         ("uneven-61x45", 0), ("ragged-60x36", 1), ("column-12x96", 0)])
+def test_refined_fp32_setup_solves(mrcm, name, degree):
+    # refine_setup: the FP32 informed and basis solves take one FP64 residual and a second solve.
+    # One step contracts the solve error by about cond(box) eps_32: on a smooth field (the
+    # log-normal workloads) that is small and the side moments come much closer to the FP64 path's;
+    # on the contrast-1e3 white-noise boxes it is near one and the step changes little.  On every
+    # case the true residual meets the tolerance and GMRES needs at most one iteration more than FP64.
+    if name == "lognormal-128":
+        prob, q = W.lognormal(128, seed=5, variance=2.0, corr=0.1, sub=16, oversample=2, smooth_steps=1)
+    else:
+        prob, q = _case(name)
+    q.iface_degree, q.tol = degree, 1e-8
+    T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
+    b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
+    res = {}
+    for prec, ref in ((W.PREC_FP64, 0), (W.PREC_FP32, 0), (W.PREC_FP32, 1)):
+        q.local_prec, q.refine_setup = prec, ref
+        s = mrcm.Solver(prob, q)
+        s.factor()
+        p, info = s.solve()
+        assert info["status"] == 0
+        r = b - grid.matvec(T, p.cpu().numpy().reshape(prob.K.shape), 2)
+        assert np.linalg.norm(r) <= 1.0001e-8 * np.linalg.norm(b)
+        res[(prec, ref)] = (s.debug(mrcm.MRCM_DBG_MOMENTS), info["iterations"])
+        s.close()
+    m64, it64 = res[(W.PREC_FP64, 0)]
+    (m_plain, it_plain), (m_ref, it_ref) = res[(W.PREC_FP32, 0)], res[(W.PREC_FP32, 1)]
+    if name == "lognormal-128":
+        assert _rel(m_ref, m64) < 0.25 * _rel(m_plain, m64), (_rel(m_ref, m64), _rel(m_plain, m64))
+    assert it_ref <= it64 + 1, (it64, it_plain, it_ref)
 
 
 @pytest.mark.parametrize("contrast", [1e6, 1e9])
