@@ -122,8 +122,10 @@ __device__ __forceinline__ void tri_advance(int& i, int& j, int step) {
 // per iteration on one half of the CTA (each half with its own working arrays), and the middle line
 // follows; nch = 1: the lines one after the other (boxes too wide for two sets of working arrays).
 // Each line: Schur complement, right-looking Cholesky (the next diagonal's square root is taken by
-// the thread that updates it, so a column costs one barrier), L^-1 by elimination on the identity,
-// and S^-1 = L^-T L^-1.
+// the thread that updates it), L^-1 by elimination on the identity, and S^-1 = L^-T L^-1.  The
+// scaled column of L (Cholesky) and the scaled row of L^-1 are written before the updates that
+// read them (two barriers per column), so every update entry is one FMA: the FP64 pipe, which
+// bounds the FP64 factorisation, does half the work of scaling inside the update.
 template <typename T>
 __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __restrict__ Linv, int* flags, int nch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -221,16 +223,20 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
     }
     __syncthreads();
     for (int k = 0; k < w; ++k) {
+      // column k of L first (one barrier), then the trailing update with one FMA per entry
+      const int mm = w - k - 1;
       if (active) {
         const T rd = rinv[k];
-        const int mm = w - k - 1;
         for (int i = tidh; i < mm; i += nth) Lm[(k + 1 + i) * w + k] = Sm[(k + 1 + i) * w + k] * rd;
+      }
+      __syncthreads();
+      if (active) {
         const int nup = mm * (mm + 1) / 2;
         int ii, jj;
         tri_at(tidh, ii, jj);
         for (int t = tidh; t < nup; t += nth, tri_advance(ii, jj, nth)) {
           const int i = k + 1 + ii, j = k + 1 + jj;
-          const T v = Sm[i * w + j] - (Sm[i * w + k] * rd) * (Sm[j * w + k] * rd);
+          const T v = Sm[i * w + j] - Lm[i * w + k] * Lm[j * w + k];
           Sm[i * w + j] = v;
           if (t == 0) {  // the next diagonal: its square root for column k + 1
             T p = v;
@@ -254,13 +260,17 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
       }
     __syncthreads();
     for (int k = 0; k < w; ++k) {
+      // row k of L^-1 first (one barrier), then the rows below with one FMA per entry
       if (active) {
         const T rk = rinv[k];
         for (int c = tidh; c <= k; c += nth) Lc[k * w + c] = Sm[k * w + c] * rk;
+      }
+      __syncthreads();
+      if (active) {
         const int rows = w - k - 1, cols = k + 1;
         for (int t = tidh; t < rows * cols; t += nth) {
           const int i = k + 1 + t / cols, c = t % cols;
-          Sm[i * w + c] -= Lm[i * w + k] * (Sm[k * w + c] * rk);
+          Sm[i * w + c] -= Lm[i * w + k] * Lc[k * w + c];
         }
       }
       __syncthreads();
