@@ -312,6 +312,282 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   if (tid == 0 && bad) atomicOr(flags, FLAG_SINGULAR_LOCAL);
 }
 
+// --------------------------------------------------------------------------------------------
+// FP32 factorisation for boxes up to 36 cells wide, register-resident: one warp per recursion of
+// the twisted order (two warps per box), lane i holding row i of the line block; a width W above
+// 32 keeps the (W-32) x (W-32) corner of the last rows in every lane (the rest of those rows is
+// columns 32.. of the lanes' rows, by symmetry).  Each line: the Schur complement from the
+// previous line's inverse (still in registers), Jacobi scaling to a unit diagonal, and S^-1 by the
+// symmetric Gauss-Jordan sweep (pivot k: a_ij -= a_ik a_kj / a_kk for i, j != k, row and column k
+// divided by the pivot, a_kk = -1 / a_kk; after every pivot the array holds -S^-1).  The pivots of
+// the scaled SPD block lie in (0, 1], so the pivot row takes the same one-FMA update as the others
+// (a_kj - (1 - 1/d) a_kj, rounding error at most |d - 1| eps).  The pivot row is published through
+// shared memory (double-buffered, one warp barrier per pivot).  S_J^-1 = -R a R is written in the
+// packed lower layout of k_factor, E_J after the blocks.
+// --------------------------------------------------------------------------------------------
+template <int W>
+struct SweepSmem {
+  static constexpr int STG = (W * (W + 1) / 2 + 3) & ~3;
+  float bc[2][W];                  // pivot row
+  float dv[W], ov[W], uv[W], rv[W], vv[W];
+  float stage[STG];                // S_J^-1, packed lower
+};
+
+// coefficients of cell x of line J as floats (identity rows past the box width)
+__device__ __forceinline__ void line_coeffs_f(const Geo& g, const Box& b, bool robin, int J, int x, float& d, float& o,
+                                              float& e) {
+  if (x >= b.w) {
+    d = 1.f;
+    o = 0.f;
+    e = 0.f;
+    return;
+  }
+  double dd, oo, ee;
+  line_coeffs(g, b, robin, J, x, dd, oo, ee);
+  d = (float)dd;
+  o = (float)oo;
+  e = (float)ee;
+}
+
+template <int W>
+__global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, float* __restrict__ Linv,
+                                                     int* flags) {
+  static_assert(W % 4 == 0 && W <= 36, "sweep widths: multiples of 4 up to 36");
+  constexpr int C = W > 32 ? W - 32 : 0;   // corner size
+  constexpr int C1 = C > 0 ? C : 1;
+  constexpr int R0 = W < 32 ? W : 32;      // rows held one per lane
+  __shared__ __align__(16) SweepSmem<W> sm_all[2];
+  const int s = blockIdx.x;
+  const bool ohat = kind != BOX_OMEGA_ROBIN;
+  const bool robin = kind != BOX_OHAT_DIRICHLET;
+  const Box b = box_of(g, s, ohat);
+  const int w = b.w, h = b.h, m = h / 2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  SweepSmem<W>& sm = sm_all[wid];
+  float* out = Linv + (size_t)s * box_stride(w, h, LS);
+  float* ec_out = out + (size_t)h * LS;
+  bool bad = false;
+
+  float a[W];          // row `lane` of the working array
+  float c[C1][C1];     // corner rows / columns 32.. (W > 32), the same in every lane
+  float r_own = 1.f;   // Jacobi scale of row `lane` of the previous line
+  float rc[C1];        // Jacobi scales of the corner rows
+  float ep0 = 0.f, ep1 = 0.f;   // bottom recursion: E_{J+1} of cells lane and 32 + lane
+#pragma unroll
+  for (int j = 0; j < W; ++j) a[j] = 0.f;
+#pragma unroll
+  for (int p = 0; p < C1; ++p) {
+    rc[p] = 1.f;
+#pragma unroll
+    for (int q = 0; q < C1; ++q) c[p][q] = 0.f;
+  }
+
+  // top lines 0..m-1 (warp 0) and bottom lines h-1..m+1 (warp 1) side by side, then the middle
+  // line m on warp 0 once both recursions are done
+  const int nsteps = wid == 0 ? m : h - 1 - m;
+  const int iters = m > h - 1 - m ? m : h - 1 - m;
+  for (int it = 0; it <= iters; ++it) {
+    const bool mid = it == iters;
+    if (mid) __syncthreads();
+    if (mid ? wid != 0 : it >= nsteps) continue;
+    const bool top = !mid && wid == 0;
+    const int J = mid ? m : (top ? it : h - 1 - it);
+    const bool has_prev = mid ? m > 0 : it > 0;
+    const bool dn = mid && m + 1 < h;      // the middle line's second neighbour S_{m+1}^-1
+    // (1) line data: diagonal, right coupling, u_x = E_x r_x towards the previous line
+    float d0, o0, e0, d1 = 1.f, o1 = 0.f, e1 = 0.f;
+    line_coeffs_f(g, b, robin, J, lane, d0, o0, e0);
+    if (lane < C) line_coeffs_f(g, b, robin, J, 32 + lane, d1, o1, e1);
+    if (lane < w) ec_out[(size_t)J * w + lane] = e0;
+    if (lane < C && 32 + lane < w) ec_out[(size_t)J * w + 32 + lane] = e1;
+    const float eu0 = (top || mid) ? e0 : ep0, eu1 = (top || mid) ? e1 : ep1;
+    ep0 = e0;
+    ep1 = e1;
+    float f0 = 0.f, f1 = 0.f;
+    if (dn) {
+      float d_, o_;
+      line_coeffs_f(g, b, robin, m + 1, lane, d_, o_, f0);
+      if (lane < C) line_coeffs_f(g, b, robin, m + 1, 32 + lane, d_, o_, f1);
+    }
+    if (lane < W) {
+      sm.dv[lane] = d0;
+      sm.ov[lane] = o0;
+      sm.uv[lane] = has_prev ? eu0 * r_own : 0.f;
+      sm.vv[lane] = f0;
+    }
+    if (lane < C) {
+      sm.dv[32 + lane] = d1;
+      sm.ov[32 + lane] = o1;
+      float rl = 1.f;
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+        if (p == lane) rl = rc[p];
+      sm.uv[32 + lane] = has_prev ? eu1 * rl : 0.f;
+      sm.vv[32 + lane] = f1;
+    }
+    __syncwarp();
+    // (2) Schur complement: row `lane` and the corner
+    {
+      const float ui = lane < W ? sm.uv[lane] : 0.f;
+      const float di = lane < W ? sm.dv[lane] : 1.f;
+      const float oi = lane < W ? sm.ov[lane] : 0.f;
+      const float om = (lane > 0 && lane < W) ? sm.ov[lane - 1] : 0.f;
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        float v = (ui * sm.uv[j]) * a[j];
+        if (j == lane) v += di;
+        if (j == lane + 1) v -= oi;
+        if (j == lane - 1) v -= om;
+        a[j] = v;
+      }
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          float v = (sm.uv[32 + p] * sm.uv[32 + q]) * c[p][q];
+          if (p == q) v += sm.dv[32 + p];
+          if (q == p + 1) v -= sm.ov[32 + p];
+          if (q == p - 1) v -= sm.ov[32 + q];
+          c[p][q] = v;
+        }
+      if (dn) {   // - E_{m+1} S_{m+1}^-1 E_{m+1}, from the bottom recursion's staged last block
+        const float* sx = sm_all[1].stage;
+        const float vi = lane < w ? sm.vv[lane] : 0.f;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (lane < w && j < w) {
+            const int hi = j > lane ? j : lane, lo = j > lane ? lane : j;
+            a[j] -= (vi * sm.vv[j]) * sx[hi * (hi + 1) / 2 + lo];
+          }
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+#pragma unroll
+          for (int q = 0; q < C; ++q)
+            if (32 + p < w && 32 + q < w) {
+              const int hi = p > q ? p : q, lo = p > q ? q : p;
+              c[p][q] -= (sm.vv[32 + p] * sm.vv[32 + q]) * sx[(32 + hi) * (33 + hi) / 2 + 32 + lo];
+            }
+      }
+    }
+    // (3) Jacobi scaling to a unit diagonal
+    {
+      float dg = 1.f;
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j == lane) dg = a[j];
+      if (lane < W && !(dg > 0.f && isfinite(dg))) {
+        bad = true;
+        dg = 1.f;
+      }
+      r_own = lane < W ? rsqrtf(dg) : 1.f;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        float cp = c[p][p];
+        if (!(cp > 0.f && isfinite(cp))) {
+          bad = true;
+          cp = 1.f;
+        }
+        rc[p] = rsqrtf(cp);
+      }
+      if (lane < W) sm.rv[lane] = r_own;
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < W; ++j) a[j] *= r_own * (j < 32 ? sm.rv[j] : rc[j - 32]);
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q < C; ++q) c[p][q] *= rc[p] * rc[q];
+    }
+    // (4) symmetric Gauss-Jordan sweep over the W pivots
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      float* bk = sm.bc[k & 1];
+      constexpr int RW = W;   // entries published for a pivot row held by one lane
+      if (k < 32) {
+        if (lane == k) {
+#pragma unroll
+          for (int j = 0; j < RW; j += 4)
+            *reinterpret_cast<float4*>(bk + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+        }
+      } else {
+        bk[lane] = a[k];
+      }
+      __syncwarp();
+      const int nr = k < 32 ? W : R0;
+      float rowk[W];
+#pragma unroll
+      for (int j = 0; j < W; j += 4)
+        if (j < nr) {
+          const float4 t = *reinterpret_cast<const float4*>(bk + j);
+          rowk[j] = t.x;
+          rowk[j + 1] = t.y;
+          rowk[j + 2] = t.z;
+          rowk[j + 3] = t.w;
+        }
+      if (k >= 32) {
+#pragma unroll
+        for (int q = 0; q < C; ++q) rowk[32 + q] = c[k - 32][q];
+      }
+      float dk = rowk[k];
+      if (!(dk > 0.f && isfinite(dk))) {
+        bad = true;
+        dk = 1.f;
+      }
+      const float rinv = 1.f / dk;
+      const bool me = k < 32 && lane == k;
+      const float gsc = me ? 1.f - rinv : a[k] * rinv;
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j != k) a[j] = fmaf(-gsc, rowk[j], a[j]);
+      a[k] = me ? -rinv : gsc;
+      if (C > 0) {
+        float gk[C1];
+#pragma unroll
+        for (int p = 0; p < C; ++p) gk[p] = rowk[32 + p] * rinv;
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+#pragma unroll
+          for (int q = 0; q < C; ++q) {
+            if (32 + p == k && 32 + q == k) c[p][q] = -rinv;
+            else if (32 + p == k) c[p][q] = gk[q];
+            else if (32 + q == k) c[p][q] = gk[p];
+            else c[p][q] = fmaf(-gk[p], rowk[32 + q], c[p][q]);
+          }
+      }
+    }
+    // (5) S^-1 = -R a R, packed lower, through the staging array
+    __syncwarp();
+    if (lane < w) {
+      const int base = lane * (lane + 1) / 2;
+#pragma unroll
+      for (int j = 0; j < R0; ++j)
+        if (j <= lane) sm.stage[base + j] = -(r_own * sm.rv[j]) * a[j];
+#pragma unroll
+      for (int p = 0; p < C; ++p)   // rows 32 + p, columns lane < 32
+        if (32 + p < w) sm.stage[(32 + p) * (33 + p) / 2 + lane] = -(r_own * rc[p]) * a[32 + p];
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+#pragma unroll
+        for (int q = 0; q <= p; ++q)
+          if (32 + p < w) sm.stage[(32 + p) * (33 + p) / 2 + 32 + q] = -(rc[p] * rc[q]) * c[p][q];
+    }
+    __syncwarp();
+    const int npk = w * (w + 1) / 2;
+    for (int t = lane; t < npk; t += 32) out[(size_t)J * LS + t] = sm.stage[t];
+    __syncwarp();
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_SINGULAR_LOCAL);
+}
+
+template <int W>
+static cudaError_t launch_factor_sweep(const Geo& g, int kind, int LS, float* Linv, int* flags, cudaStream_t st) {
+  k_factor_sweep<W><<<g.mx * g.my, 64, 0, st>>>(g, kind, LS, Linv, flags);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 // FP64 line coefficients [diagonal, x coupling to the right, y coupling to the line above] of every
 // cell of every box of one kind, for the refinement step of the FP32 set-up solves
 __global__ void k_line_coef(Geo g, int kind, double* __restrict__ coef) {
@@ -348,6 +624,15 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
   // both recursions at once when two sets of working arrays still leave room for two CTAs per SM
   const int nch = factor_smem_bytes(w, fp32, 2) <= 112 * 1024 ? 2 : 1;
   const size_t sm = factor_smem_bytes(w, fp32, nch);
+  if (fp32 && w <= 36) {   // register-resident sweep, box width padded to a multiple of 4
+    float* L = (float*)Linv;
+    if (w <= 16) return launch_factor_sweep<16>(g, kind, LS, L, flags, st);
+    if (w <= 20) return launch_factor_sweep<20>(g, kind, LS, L, flags, st);
+    if (w <= 24) return launch_factor_sweep<24>(g, kind, LS, L, flags, st);
+    if (w <= 28) return launch_factor_sweep<28>(g, kind, LS, L, flags, st);
+    if (w <= 32) return launch_factor_sweep<32>(g, kind, LS, L, flags, st);
+    return launch_factor_sweep<36>(g, kind, LS, L, flags, st);
+  }
   if (fp32) {
     const cudaError_t e = raise_smem_limit<k_factor<float>>();
     if (e != cudaSuccess) return e;
