@@ -13,7 +13,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(ROOT, "_build", "libmrcm")
 LIB = os.path.join(LIBDIR, "libmrcm.so")
 
-CUDA_SOURCES = ["api.cu", "k_grid.cu", "k_local.cu", "k_coarse.cu", "k_krylov.cu", "noalloc.cu"]
+CUDA_SOURCES = ["api.cu", "k_grid.cu", "k_local.cu", "k_coarse.cu", "k_mf.cu", "k_krylov.cu", "noalloc.cu"]
 CXX_SOURCES = ["plan.cpp", "server.cpp", "tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -155,6 +155,25 @@ CoarseDev coarse(mrcm_handle h) {
   return c;
 }
 
+MfDev mfdev(mrcm_handle h) {
+  MfDev m;
+  const Layout& L = h->lay;
+  const Plan& P = h->plan;
+  m.fr = at<MfFront>(h, L.mf_fr);
+  m.order = at<int>(h, L.mf_ord);
+  m.lvl = at<int>(h, L.mf_lvl);
+  m.idx = at<int>(h, L.mf_idx);
+  m.asmv = at<int2>(h, L.mf_asm);
+  m.map = at<int>(h, L.mf_map);
+  m.task = at<int4>(h, L.mf_task);
+  m.F = at<double>(h, L.mf_F);
+  m.V = at<double>(h, L.mf_V);
+  m.scr = at<unsigned>(h, L.mf_scr);
+  m.levels = P.mf_level.empty() ? 0 : (int)P.mf_level.size() - 1;
+  m.max_f = P.mf_max_f;
+  return m;
+}
+
 size_t ncell(mrcm_handle h) { return (size_t)h->n[0] * h->n[1] * h->n[2]; }
 
 std::string supported(const mrcm_problem& p, const mrcm_params& q) {
@@ -299,6 +318,20 @@ mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, v
     for (int k = 0; k < 4; ++k) tab.push_back(P.rank[6 * s + k] >= 0 ? P.off[s] + P.rank[6 * s + k] : -1);
   h->tab_host = tab;
   cudaError_t e = cudaMemcpyAsync(at<int>(h, L.tab), h->tab_host.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st);
+  if (P.mf) {   // multifrontal tables (the host copies live in h->plan)
+    const Plan& HP = h->plan;
+    auto up = [&](size_t off, const void* src, size_t bytes) {
+      if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(h->ws + off, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    up(L.mf_fr, HP.mf_front.data(), sizeof(MfFront) * HP.mf_front.size());
+    up(L.mf_ord, HP.mf_order.data(), 4 * HP.mf_order.size());
+    up(L.mf_lvl, HP.mf_level.data(), 4 * HP.mf_level.size());
+    up(L.mf_idx, HP.mf_idx.data(), 4 * HP.mf_idx.size());
+    up(L.mf_asm, HP.mf_asm.data(), 4 * HP.mf_asm.size());
+    up(L.mf_map, HP.mf_map.data(), 4 * HP.mf_map.size());
+    up(L.mf_task, HP.mf_task.data(), 4 * HP.mf_task.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.mf_scr, 0, 64, st);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(at<unsigned char>(h, L.red), 0, 8 * RED_DOUBLES + 64, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<int>(h, L.flags), 0, 4 * 64, st);
   if (e != cudaSuccess) {
@@ -414,11 +447,15 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     return MRCM_OK;
   };
   h->coarse_pivoted = h->prm.coarse_pivoting != 0;
+  h->coarse_mf = P.mf && !h->coarse_pivoted;
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     if (h->coarse_pivoted) {
       const mrcm_status rc = pivoted();
       if (rc != MRCM_OK) return rc;
+    } else if (h->coarse_mf) {   // nested-dissection multifrontal LU (k_mf.cu), G read from the band copy
+      CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
+      CK(h, launch_mf_factor(mfdev(h), P, c.ab, flags, st));
     } else {
       CK(h, launch_coarse_assemble(c, at<double>(h, L.mom), P.E, st));
       CK(h, launch_coarse_factor_nopiv(c, flags, np_scratch, st));
@@ -427,7 +464,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
     if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
-    else CK(h, launch_coarse_blocks(c, st));
+    else if (!h->coarse_mf) CK(h, launch_coarse_blocks(c, st));
   }
   CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   int hf = 0;
@@ -443,6 +480,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     CK(h, cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     h->coarse_pivoted = true;
+    h->coarse_mf = false;
   }
   if (hf & FLAG_NONFINITE) return fail(h, MRCM_ERR_INVALID_ARG, "K must be positive and finite");
   if (hf & FLAG_SINGULAR_LOCAL) return fail(h, MRCM_ERR_SINGULAR, "non-positive pivot in a local factorisation");
@@ -472,6 +510,8 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
     Phase ph(h, MRCM_PH_COARSE_SOLVE, st);
     if (P.NC <= COARSE_DENSE_MAX) {
       CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
+    } else if (h->coarse_mf) {
+      CK(h, launch_mf_solve(mfdev(h), c, at<double>(h, L.mom0), P.E, at<int>(h, L.flags), st));
     } else {
       CK(h, launch_coarse_solve(c, at<double>(h, L.mom0), P.E, st));
     }
@@ -713,6 +753,15 @@ mrcm_status mrcm_solve_host(mrcm_handle h, const double* K_host, double* p_host,
 void mrcm_destroy(mrcm_handle h) { delete h; }
 
 int64_t mrcm_launch_count(void) { return g_launches.load(); }
+
+mrcm_status mrcm_coarse_method(mrcm_handle h, int32_t* method) {
+  if (!h || !method) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
+  if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "the handle is not factored");
+  if (h->plan.NC <= COARSE_DENSE_MAX) *method = MRCM_COARSE_INVERSE;
+  else if (h->coarse_mf) *method = MRCM_COARSE_MULTIFRONTAL;
+  else *method = h->coarse_pivoted ? MRCM_COARSE_BAND_PIVOTED : MRCM_COARSE_BAND;
+  return MRCM_OK;
+}
 
 mrcm_status mrcm_measure_fp64_peak(double* tflops_out, void* stream) {
   if (!tflops_out) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");

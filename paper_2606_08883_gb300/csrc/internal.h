@@ -16,6 +16,26 @@ namespace mrcm {
 // ------------------------------------------------------------------------------------------
 // Host plan: partition and coupling-system numbering (MRCM-OS step 1), integer only.
 // ------------------------------------------------------------------------------------------
+// One front of the nested-dissection multifrontal factorisation of G: the pivot unknowns P (the
+// interfaces on the separator of its rectangle of subdomains, or every interface inside a leaf
+// rectangle) and the update unknowns U (the interfaces on the rectangle's boundary), P first.  The
+// dense front F = [F11 F12; F21 F22] (row-major, f = np + nu) is overwritten by F11^-1,
+// D = F11^-1 F12 and S = F22 - F21 D; B = F21 F11^-1 (nu x np) follows F.
+struct MfFront {
+  long long fo;   // offset (doubles) of F in the front buffer
+  int np, nu;
+  int io;         // first of its np + nu unknowns in the index list
+  int vo;         // offset (doubles) of its solve vectors [v_P, w_U]
+  int ao, na;     // its assembly pairs
+  int nch;        // children (0..2)
+  int ch[2];      // child front ids
+  int mo[2];      // offsets of the children's maps
+  int pad;
+};
+constexpr int MF_LEAF = 16;       // leaf rectangles of at most this many subdomains
+constexpr int MF_MAX_NP = 128;    // largest pivot block (its inverse is formed in shared memory)
+constexpr int MF_TILE = 32;       // tile of the D, B and S products
+
 struct Plan {
   int dim = 2;
   int n[3] = {1, 1, 1};
@@ -38,6 +58,21 @@ struct Plan {
   // the lower subdomain's +axis side, the pressure row at the upper subdomain's -axis side
   std::vector<int> row_home;   // [2E] canonical row -> banded row
   int kl = 0, ku = 0;          // band widths of G in the banded order
+  // nested-dissection multifrontal factorisation of G (2-D coupling systems above
+  // COARSE_DENSE_MAX unknowns; mf is set when every front fits the kernels of k_mf.cu)
+  bool mf = false;
+  std::vector<MfFront> mf_front;   // postorder (children before parents)
+  std::vector<int> mf_order;       // front ids grouped by level (leaves are level 0)
+  std::vector<int> mf_level;       // [levels + 1] starts of the levels in mf_order
+  std::vector<int> mf_idx;         // unknowns of each front, P then U
+  std::vector<int> mf_asm;         // (dst, src) pairs: front-local offset, band offset of G
+  std::vector<int> mf_map;         // child U position -> parent front position
+  std::vector<int> mf_task;        // (front, kind, r0, c0) tile tasks
+  std::vector<int> mf_task_b;      // [levels + 1] starts of each level's D / B tasks
+  std::vector<int> mf_task_c;      // [levels + 1] starts of each level's Schur-complement tasks
+  size_t mf_fbuf = 0;              // doubles of all fronts (F and B)
+  size_t mf_vbuf = 0;              // doubles of the solve vectors
+  int mf_max_np = 0, mf_max_f = 0;
 };
 
 // Returns an empty string on success, else the reason the input is invalid.
@@ -57,6 +92,8 @@ struct Layout {
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
   size_t gtr;                             // Robin coefficients of the Gamma faces, k_local.cu
   size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
+  size_t mf_fr, mf_ord, mf_lvl, mf_idx, mf_asm, mf_map, mf_task;   // multifrontal tables, k_mf.cu
+  size_t mf_F, mf_V, mf_scr;              // fronts, solve vectors, barrier and statistics words
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
@@ -140,6 +177,7 @@ struct mrcm_ctx {
   size_t ws_bytes;
   bool factored = false;
   bool coarse_pivoted = false;   // the last factorisation of G fell back to partial pivoting
+  bool coarse_mf = false;        // G factored by the multifrontal LU (k_mf.cu)
   std::string err;
   int coarse_n;       // 2E
   std::vector<int> tab_host;  // plan tables uploaded to the device
@@ -250,6 +288,31 @@ cudaError_t launch_coarse_factor_nopiv(const CoarseDev& c, int* flags, unsigned*
 // set-up of the blocked substitution (2E nq > COARSE_DENSE_MAX), after the factorisation
 cudaError_t launch_coarse_blocks(const CoarseDev& c, cudaStream_t st);
 cudaError_t launch_coarse_apply(const CoarseDev& c, const double* Ginv, const double* mom0, int E, cudaStream_t st);
+
+// Multifrontal factorisation of G (k_mf.cu): device copies of the plan's tables and buffers.
+struct MfDev {
+  const MfFront* fr;
+  const int* order;
+  const int* lvl;       // [levels + 1]
+  const int* idx;
+  const int2* asmv;
+  const int* map;
+  const int4* task;
+  double* F;
+  double* V;
+  unsigned* scr;        // [0, 2) grid barrier, [2, 6) two 8-byte maxima: |G| entries, |S| entries
+  int levels;
+  int max_f;            // largest front (np + nu)
+};
+// Set-up: fronts level by level (assembly from the band copy of G and F11^-1, then the D and B
+// tiles, then the Schur-complement tiles) and a final growth check that sets FLAG_NOPIV_REJECTED
+// when a pivot is zero or not finite or |S| grows past NOPIV_MAX_GROWTH max |G| (the caller then
+// falls back to the pivoted band LU).
+cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, int* flags, cudaStream_t st);
+// Per apply: right-hand side from mom0 (through c), then one cooperative launch: forward through
+// the levels, backward down them; the solution replaces c.g.
+cudaError_t launch_mf_solve(const MfDev& m, const CoarseDev& c, const double* mom0, int E, int* flags,
+                            cudaStream_t st);
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,
                            double* sn, double* gv, double* out, double* wbuf, double* part, double* tot, double* Tm,
                            unsigned* bar, int* flags, cudaStream_t st);

@@ -1,0 +1,302 @@
+// Coupling system of MRCM-O (Eq. 13-14) by a multifrontal LU over a nested dissection of the
+// subdomain grid, without row interchanges.
+//
+// Each interface carries 2 nq unknowns and the 2 nq rows homed at them (flux and pressure rows),
+// and a row couples the unknowns of the one or two subdomains it joins, so a rectangle of
+// subdomains whose interior interfaces are eliminated leaves couplings only among the interfaces of
+// its boundary.  The host plan (plan.cpp) cuts the grid recursively; a front eliminates the
+// separator of its rectangle (or every interior interface of a leaf rectangle).  With the front
+// F = [F11 F12; F21 F22] (pivot unknowns P first, boundary unknowns U after),
+//   F11^-1 (Gauss-Jordan without pivoting),  D = F11^-1 F12,  B = F21 F11^-1,
+//   S = F22 - F21 D  (added into the parent front),
+// and a solve of G x = g runs forward through the levels, v_P = g_P + children's w, w_U = v_U - B v_P,
+// then backward, x_P = F11^-1 v_P - D x_U.  Every product has a fixed order, so the solution is
+// deterministic.  A zero or non-finite pivot, or |S| above NOPIV_MAX_GROWTH max |G|, sets
+// FLAG_NOPIV_REJECTED and the caller falls back to the pivoted band LU of k_coarse.cu.
+#include "common.cuh"
+
+namespace mrcm {
+
+constexpr int MF_THREADS = 256;
+
+// largest of a non-negative double across the CTA into an 8-byte maximum in global memory (the
+// bit patterns of non-negative doubles order like the values; +inf above every finite value)
+__device__ __forceinline__ void cta_max_to(double v, unsigned long long* dst) {
+  __shared__ double red[MF_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__device__ __forceinline__ double mag(double v) { return isfinite(v) ? fabs(v) : __longlong_as_double(0x7ff0000000000000LL); }
+
+// C (M x N) = (acc ? C : 0) + alpha A (M x K) B (K x N), row-major operands with leading
+// dimensions, in global or shared memory; one CTA of MF_THREADS, 32 x 32 output tiles with 2 x 2
+// outputs per thread, K in chunks of 32 staged in shared memory (sm: 2048 doubles).  Returns the
+// largest |C| written (+inf for a non-finite entry).
+__device__ double cta_gemm(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                           int ldc, double alpha, bool acc, double* sm) {
+  double* As = sm;          // As[k * 32 + r] = A[m0 + r][k0 + k]
+  double* Bs = sm + 1024;   // Bs[k * 32 + c] = B[k0 + k][n0 + c]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double cmax = 0.0;
+  for (int m0 = 0; m0 < M; m0 += 32)
+    for (int n0 = 0; n0 < N; n0 += 32) {
+      double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int t = tid; t < 1024; t += MF_THREADS) {
+          const int k = t >> 5, r = t & 31;
+          As[t] = (m0 + r < M && k0 + k < K) ? A[(size_t)(m0 + r) * lda + k0 + k] : 0.0;
+          Bs[t] = (k0 + k < K && n0 + r < N) ? B[(size_t)(k0 + k) * ldb + n0 + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const double a0 = As[k * 32 + ty], a1 = As[k * 32 + ty + 16];
+          const double b0 = Bs[k * 32 + tx], b1 = Bs[k * 32 + tx + 16];
+          c00 = fma(a0, b0, c00);
+          c01 = fma(a0, b1, c01);
+          c10 = fma(a1, b0, c10);
+          c11 = fma(a1, b1, c11);
+        }
+        __syncthreads();
+      }
+      const double cv[2][2] = {{c00, c01}, {c10, c11}};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
+          if (r < M && c < N) {
+            double* p = C + (size_t)r * ldc + c;
+            const double v = (acc ? *p : 0.0) + alpha * cv[i][j];
+            *p = v;
+            cmax = fmax(cmax, mag(v));
+          }
+        }
+    }
+  return cmax;
+}
+
+__device__ __forceinline__ unsigned long long* mf_stats(const MfDev& m) {
+  return reinterpret_cast<unsigned long long*>(m.scr + 2);
+}
+
+// One CTA per front of a level: assembly (zero, the original entries of the pivot rows and
+// columns, the children's Schur complements in child order) and F11^-1 in place.
+__global__ void __launch_bounds__(MF_THREADS) k_mf_front(MfDev m, const double* __restrict__ ab, int first,
+                                                         int* flags) {
+  extern __shared__ __align__(16) double smd[];
+  const int fid = m.order[first + blockIdx.x];
+  const MfFront fr = m.fr[fid];
+  const int np = fr.np, nu = fr.nu, f = np + nu;
+  double* F = m.F + fr.fo;
+  for (size_t t = threadIdx.x; t < (size_t)f * f; t += MF_THREADS) F[t] = 0.0;
+  __syncthreads();
+  double amax = 0.0;
+  for (int t = threadIdx.x; t < fr.na; t += MF_THREADS) {
+    const int2 p = m.asmv[fr.ao + t];
+    const double v = ab[p.y];
+    F[p.x] = v;
+    amax = fmax(amax, mag(v));
+  }
+  __syncthreads();
+  for (int c = 0; c < fr.nch; ++c) {
+    const MfFront cf = m.fr[c == 0 ? fr.ch[0] : fr.ch[1]];
+    const int fc = cf.np + cf.nu, nuc = cf.nu;
+    const double* S = m.F + cf.fo + (size_t)cf.np * fc + cf.np;
+    const int* mp = m.map + (c == 0 ? fr.mo[0] : fr.mo[1]);
+    for (int t = threadIdx.x; t < nuc * nuc; t += MF_THREADS) {
+      const int i = t / nuc, j = t - i * nuc;
+      F[(size_t)mp[i] * f + mp[j]] += S[(size_t)i * fc + j];
+    }
+    __syncthreads();
+  }
+  cta_max_to(amax, mf_stats(m));
+  // Gauss-Jordan on F11 (np x np) in shared memory: pivot k takes the scaled row r_k = A_k. / a_kk
+  // and the column c_k = A_.k, then a_ij -= c_i r_j off row and column k, row k = r_k, column
+  // k = -c_k / a_kk, a_kk = 1 / a_kk; after the np pivots A = F11^-1
+  double* A = smd;
+  double* rk = A + np * np;
+  double* ck = rk + np;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < np; i += MF_THREADS / 32)
+    for (int j = lane; j < np; j += 32) A[i * np + j] = F[(size_t)i * f + j];
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < np; ++k) {
+    double d = A[k * np + k];
+    if (!(fabs(d) > 0.0) || !isfinite(d)) {
+      bad = true;
+      d = 1.0;
+    }
+    const double r = 1.0 / d;
+    for (int j = threadIdx.x; j < np; j += MF_THREADS) {
+      rk[j] = A[k * np + j] * r;
+      ck[j] = A[j * np + k];
+    }
+    __syncthreads();
+    for (int i = wid; i < np; i += MF_THREADS / 32) {
+      const double ci = ck[i];
+      for (int j = lane; j < np; j += 32) {
+        double v;
+        if (i == k) v = j == k ? r : rk[j];
+        else if (j == k) v = -ci * r;
+        else v = fma(-ci, rk[j], A[i * np + j]);
+        A[i * np + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = wid; i < np; i += MF_THREADS / 32)
+    for (int j = lane; j < np; j += 32) F[(size_t)i * f + j] = A[i * np + j];
+  if (bad && lane == 0) atomicOr(flags, FLAG_NOPIV_REJECTED);
+}
+
+// Tile tasks of a level: kind 0, columns c0.. of D = F11^-1 F12 (in place of F12, from a shared
+// copy); kind 1, rows r0.. of B = F21 F11^-1; kind 2, the (r0, c0) tile of S = F22 - F21 D.
+__global__ void __launch_bounds__(MF_THREADS) k_mf_tiles(MfDev m, int first) {
+  extern __shared__ __align__(16) double smd[];
+  const int4 tk = m.task[first + blockIdx.x];
+  const MfFront fr = m.fr[tk.x];
+  const int np = fr.np, nu = fr.nu, f = np + nu;
+  double* F = m.F + fr.fo;
+  double* Bx = F + (size_t)f * f;
+  double* stage = smd + 2048;
+  if (tk.y == 0) {
+    const int cols = min(MF_TILE, nu - tk.w);
+    for (int t = threadIdx.x; t < np * MF_TILE; t += MF_THREADS) {
+      const int i = t / MF_TILE, j = t - i * MF_TILE;
+      stage[t] = j < cols ? F[(size_t)i * f + np + tk.w + j] : 0.0;
+    }
+    __syncthreads();
+    cta_gemm(np, cols, np, F, f, stage, MF_TILE, F + np + tk.w, f, 1.0, false, smd);
+  } else if (tk.y == 1) {
+    const int rows = min(MF_TILE, nu - tk.z);
+    cta_gemm(rows, np, np, F + (size_t)(np + tk.z) * f, f, F, f, Bx + (size_t)tk.z * np, np, 1.0, false, smd);
+  } else {
+    const int rows = min(MF_TILE, nu - tk.z), cols = min(MF_TILE, nu - tk.w);
+    const double smax = cta_gemm(rows, cols, np, F + (size_t)(np + tk.z) * f, f, F + np + tk.w, f,
+                                 F + (size_t)(np + tk.z) * f + np + tk.w, f, -1.0, true, smd);
+    cta_max_to(smax, mf_stats(m) + 1);
+  }
+}
+
+__global__ void k_mf_check(MfDev m, int* flags) {
+  const unsigned long long* st = mf_stats(m);
+  const double gmax = __longlong_as_double((long long)st[0]), smax = __longlong_as_double((long long)st[1]);
+  if (!(smax <= NOPIV_MAX_GROWTH * gmax) || !isfinite(gmax)) atomicOr(flags, FLAG_NOPIV_REJECTED);
+}
+
+cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, int* flags, cudaStream_t st) {
+  const size_t sm_front = 8 * ((size_t)P.mf_max_np * P.mf_max_np + 2 * (size_t)P.mf_max_np);
+  const size_t sm_tiles = 8 * (2048 + (size_t)P.mf_max_np * MF_TILE);
+  cudaError_t e = cudaFuncSetAttribute(k_mf_front, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_front);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mf_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tiles);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(m.scr, 0, 64, st);
+  if (e != cudaSuccess) return e;
+  for (int L = 0; L + 1 < (int)P.mf_level.size(); ++L) {
+    const int nf = P.mf_level[L + 1] - P.mf_level[L];
+    if (nf > 0) {
+      k_mf_front<<<nf, MF_THREADS, sm_front, st>>>(m, ab, P.mf_level[L], flags);
+      count_launch(1);
+    }
+    const int nb = P.mf_task_c[L] - P.mf_task_b[L];
+    if (nb > 0) {
+      k_mf_tiles<<<nb, MF_THREADS, sm_tiles, st>>>(m, P.mf_task_b[L]);
+      count_launch(1);
+    }
+    const int nc = P.mf_task_b[L + 1] - P.mf_task_c[L];
+    if (nc > 0) {
+      k_mf_tiles<<<nc, MF_THREADS, sm_tiles, st>>>(m, P.mf_task_c[L]);
+      count_launch(1);
+    }
+  }
+  k_mf_check<<<1, 1, 0, st>>>(m, flags);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// Solve, one cooperative launch (one CTA per SM): forward through the levels, then backward.  A
+// front's rows are dotted by whole warps (lanes over the columns, then a fixed shuffle tree).
+__global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __restrict__ g, int* flags) {
+  extern __shared__ __align__(16) double v[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = MF_THREADS / 32;
+  unsigned* bar = m.scr;
+  // forward: v_P = g_P + the children's w mapped into P, v_U = their part mapped into U;
+  // keep v_P, pass w_U = v_U - B v_P up
+  for (int L = 0; L < m.levels; ++L) {
+    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1]; b += gridDim.x) {
+      const MfFront fr = m.fr[m.order[b]];
+      const int np = fr.np, nu = fr.nu, f = np + nu;
+      for (int t = threadIdx.x; t < f; t += MF_THREADS) v[t] = t < np ? g[m.idx[fr.io + t]] : 0.0;
+      __syncthreads();
+      for (int c = 0; c < fr.nch; ++c) {
+        const MfFront cf = m.fr[c == 0 ? fr.ch[0] : fr.ch[1]];
+        const int* mp = m.map + (c == 0 ? fr.mo[0] : fr.mo[1]);
+        const double* wc = m.V + cf.vo + cf.np;
+        for (int t = threadIdx.x; t < cf.nu; t += MF_THREADS) v[mp[t]] += wc[t];
+        __syncthreads();
+      }
+      double* Vf = m.V + fr.vo;
+      for (int t = threadIdx.x; t < np; t += MF_THREADS) Vf[t] = v[t];
+      const double* Bx = m.F + fr.fo + (size_t)f * f;
+      for (int r = wid; r < nu; r += NW) {
+        double s = 0.0;
+        for (int k = lane; k < np; k += 32) s = fma(Bx[(size_t)r * np + k], v[k], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) Vf[np + r] = v[np + r] - s;
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, flags)) return;
+  }
+  // backward: x_P = [F11^-1 D] [v_P; -x_U], the ancestors' x_U already in g
+  for (int L = m.levels - 1; L >= 0; --L) {
+    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1]; b += gridDim.x) {
+      const MfFront fr = m.fr[m.order[b]];
+      const int np = fr.np, nu = fr.nu, f = np + nu;
+      const double* Vf = m.V + fr.vo;
+      for (int t = threadIdx.x; t < f; t += MF_THREADS) v[t] = t < np ? Vf[t] : -g[m.idx[fr.io + t]];
+      __syncthreads();
+      const double* F = m.F + fr.fo;
+      for (int r = wid; r < np; r += NW) {
+        double s = 0.0;
+        for (int k = lane; k < f; k += 32) s = fma(F[(size_t)r * f + k], v[k], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) g[m.idx[fr.io + r]] = s;
+      }
+      __syncthreads();
+    }
+    if (L > 0 && !grid_barrier(bar, flags)) return;
+  }
+}
+
+cudaError_t launch_mf_solve(const MfDev& m, const CoarseDev& c, const double* mom0, int E, int* flags,
+                            cudaStream_t st) {
+  cudaError_t e = launch_coarse_rhs(c, mom0, E, st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  MfDev mm = m;
+  double* g = c.g;
+  int* fl = flags;
+  void* args[] = {(void*)&mm, (void*)&g, (void*)&fl};
+  e = cudaLaunchCooperativeKernel((const void*)k_mf_solve, dim3(sms), dim3(MF_THREADS), args, 8 * (size_t)m.max_f,
+                                  st);
+  count_launch(1);
+  return e;
+}
+
+}  // namespace mrcm

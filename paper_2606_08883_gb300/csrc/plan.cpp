@@ -1,7 +1,9 @@
 // Host planner: validation, partition and coupling numbering (MRCM-OS step 1, Sec. 2.1), workspace
 // layout.  Integer work only; the tables it exports match the oracle's bit for bit.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <functional>
 #include <sstream>
 
 #include "internal.h"
@@ -9,6 +11,8 @@
 namespace mrcm {
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static bool plan_mf(Plan& P);
 
 std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   std::ostringstream why;
@@ -39,6 +43,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
   if (q.iface_degree != 0 && q.iface_degree != 1) return "iface_degree must be 0 or 1";
   if (q.coarse_pivoting != 0 && q.coarse_pivoting != 1) return "coarse_pivoting must be 0 or 1";
   if (q.refine_setup != 0 && q.refine_setup != 1) return "refine_setup must be 0 or 1";
+  if (q.coarse_solver != 0 && q.coarse_solver != 1) return "coarse_solver must be 0 or 1";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
     if (p.bc_kind[s] != MRCM_BC_DIRICHLET && p.bc_kind[s] != MRCM_BC_NEUMANN) return "bc_kind must be 0 or 1";
@@ -130,7 +135,183 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
       }
     }
   }
+  P.mf = false;
+  if (p.dim == 2 && P.NC > COARSE_DENSE_MAX && q.coarse_solver == 0 && q.coarse_pivoting == 0) P.mf = plan_mf(P);
+  if (!P.mf) {
+    P.mf_front.clear();
+    P.mf_idx.clear();
+    P.mf_asm.clear();
+    P.mf_map.clear();
+    P.mf_task.clear();
+    P.mf_fbuf = P.mf_vbuf = 0;
+  }
   return std::string();
+}
+
+// Nested dissection of the subdomain grid into fronts for the multifrontal factorisation of G.
+// Interface unknowns (a flux row and a pressure row homed at each, so rows and columns share the
+// index) are grouped per interface; a rectangle of subdomains eliminates the interfaces of its
+// separator (the cut between its halves) after its halves, or all its interior interfaces when it
+// is a leaf.  The structural nonzeros of G couple the interfaces of one or two neighbouring
+// subdomains, so a rectangle's remaining couplings after elimination are its boundary interfaces.
+// Returns false (multifrontal path not used) when a front exceeds the kernels' limits.
+static bool plan_mf(Plan& P) {
+  const int mx = P.m[0], my = P.m[1], nq = P.nq;
+  const int kv = P.kl + P.ku, ldab = 2 * P.kl + P.ku + 1;
+  // interface ids by (axis, lower subdomain)
+  std::vector<int> vid(2 * (size_t)mx * my, -1);
+  for (int e = 0; e < P.E; ++e) vid[(size_t)P.iface[3 * e] * mx * my + P.iface[3 * e + 1]] = e;
+  auto X = [&](int I, int J) { return vid[(size_t)J * mx + I]; };                      // (I,J)-(I+1,J)
+  auto Y = [&](int I, int J) { return vid[(size_t)mx * my + (size_t)J * mx + I]; };    // (I,J)-(I,J+1)
+  auto add_unknowns = [&](int e, std::vector<int>& out) {
+    for (int q = 0; q < nq; ++q) out.push_back(P.row_home[2 * e] * nq + q);
+    for (int q = 0; q < nq; ++q) out.push_back(P.row_home[2 * e + 1] * nq + q);
+  };
+  P.mf_front.clear();
+  P.mf_idx.clear();
+  std::vector<int> level;
+  bool ok = true;
+  std::function<int(int, int, int, int)> build = [&](int x0, int x1, int y0, int y1) -> int {
+    std::vector<int> piv, ch;
+    if ((x1 - x0) * (y1 - y0) <= MF_LEAF) {
+      for (int J = y0; J < y1; ++J)
+        for (int I = x0; I + 1 < x1; ++I) piv.push_back(X(I, J));
+      for (int J = y0; J + 1 < y1; ++J)
+        for (int I = x0; I < x1; ++I) piv.push_back(Y(I, J));
+    } else if (x1 - x0 >= y1 - y0) {
+      const int xm = (x0 + x1) / 2;
+      ch = {build(x0, xm, y0, y1), build(xm, x1, y0, y1)};
+      for (int J = y0; J < y1; ++J) piv.push_back(X(xm - 1, J));
+    } else {
+      const int ym = (y0 + y1) / 2;
+      ch = {build(x0, x1, y0, ym), build(x0, x1, ym, y1)};
+      for (int I = x0; I < x1; ++I) piv.push_back(Y(I, ym - 1));
+    }
+    ch.erase(std::remove(ch.begin(), ch.end(), -1), ch.end());
+    if (piv.empty() && ch.empty()) return -1;
+    std::vector<int> bnd;
+    for (int J = y0; J < y1; ++J) {
+      if (x0 > 0) bnd.push_back(X(x0 - 1, J));
+      if (x1 < mx) bnd.push_back(X(x1 - 1, J));
+    }
+    for (int I = x0; I < x1; ++I) {
+      if (y0 > 0) bnd.push_back(Y(I, y0 - 1));
+      if (y1 < my) bnd.push_back(Y(I, y1 - 1));
+    }
+    MfFront fr{};
+    fr.io = (int)P.mf_idx.size();
+    for (int e : piv) add_unknowns(e, P.mf_idx);
+    fr.np = (int)P.mf_idx.size() - fr.io;
+    for (int e : bnd) add_unknowns(e, P.mf_idx);
+    fr.nu = (int)P.mf_idx.size() - fr.io - fr.np;
+    fr.nch = (int)ch.size();
+    int lv = 0;
+    for (int c = 0; c < fr.nch; ++c) {
+      fr.ch[c] = ch[c];
+      lv = std::max(lv, level[ch[c]] + 1);
+    }
+    if (fr.np > MF_MAX_NP || fr.np == 0) ok = false;
+    P.mf_front.push_back(fr);
+    level.push_back(lv);
+    return (int)P.mf_front.size() - 1;
+  };
+  const int root = build(0, mx, 0, my);
+  const int nf = (int)P.mf_front.size();
+  if (!ok || root != nf - 1 || nf == 0) return false;
+  // the front that eliminates each unknown
+  std::vector<int> efront(P.NC, -1);
+  for (int f = 0; f < nf; ++f) {
+    const MfFront& fr = P.mf_front[f];
+    for (int t = 0; t < fr.np; ++t) {
+      int& ef = efront[P.mf_idx[fr.io + t]];
+      if (ef >= 0) return false;
+      ef = f;
+    }
+  }
+  for (int u = 0; u < P.NC; ++u)
+    if (efront[u] < 0) return false;
+  // structural nonzeros of G, each assembled by the first front that eliminates its row or column
+  std::vector<std::vector<std::pair<int, int>>> nz(nf);
+  for (int e = 0; e < P.E; ++e) {
+    const int s = P.iface[3 * e + 1], s2 = P.iface[3 * e + 2];
+    for (int qt = 0; qt < nq; ++qt)
+      for (int row : {P.row_home[2 * e] * nq + qt, P.row_home[2 * e + 1] * nq + qt})
+        for (int t : {s, s2})
+          for (int col = P.off[t] * nq; col < (P.off[t] + P.N[t]) * nq; ++col)
+            nz[std::min(efront[row], efront[col])].push_back({row, col});
+  }
+  std::vector<int> pos(P.NC, -1);
+  P.mf_asm.clear();
+  P.mf_map.clear();
+  size_t fo = 0, vo = 0;
+  P.mf_max_np = P.mf_max_f = 0;
+  for (int f = 0; f < nf; ++f) {
+    MfFront& fr = P.mf_front[f];
+    const int fs = fr.np + fr.nu;
+    for (int t = 0; t < fs; ++t) pos[P.mf_idx[fr.io + t]] = t;
+    fr.ao = (int)P.mf_asm.size() / 2;
+    for (auto [row, col] : nz[f]) {
+      if (pos[row] < 0 || pos[col] < 0) return false;
+      const long long src = (long long)kv + row - col + (long long)col * ldab;
+      if (src > INT32_MAX) return false;
+      P.mf_asm.push_back(pos[row] * fs + pos[col]);
+      P.mf_asm.push_back((int)src);
+    }
+    fr.na = (int)P.mf_asm.size() / 2 - fr.ao;
+    for (int c = 0; c < fr.nch; ++c) {
+      const MfFront& cf = P.mf_front[fr.ch[c]];
+      fr.mo[c] = (int)P.mf_map.size();
+      for (int t = 0; t < cf.nu; ++t) {
+        const int p = pos[P.mf_idx[cf.io + cf.np + t]];
+        if (p < 0) return false;
+        P.mf_map.push_back(p);
+      }
+    }
+    for (int t = 0; t < fs; ++t) pos[P.mf_idx[fr.io + t]] = -1;
+    fr.fo = (long long)fo;
+    fo += (size_t)fs * fs + (size_t)fr.nu * fr.np;
+    fr.vo = (int)vo;
+    vo += fs;
+    P.mf_max_np = std::max(P.mf_max_np, fr.np);
+    P.mf_max_f = std::max(P.mf_max_f, fs);
+  }
+  if (vo > (size_t)INT32_MAX) return false;
+  P.mf_fbuf = fo;
+  P.mf_vbuf = vo;
+  // levels and the tile tasks of each level
+  const int nl = *std::max_element(level.begin(), level.end()) + 1;
+  P.mf_level.assign(nl + 1, 0);
+  P.mf_order.clear();
+  P.mf_task.clear();
+  P.mf_task_b.assign(nl + 1, 0);
+  P.mf_task_c.assign(nl + 1, 0);
+  std::vector<int> tc;
+  for (int L = 0; L < nl; ++L) {
+    P.mf_level[L] = (int)P.mf_order.size();
+    P.mf_task_b[L] = (int)P.mf_task.size() / 4;
+    for (int f = 0; f < nf; ++f)
+      if (level[f] == L) P.mf_order.push_back(f);
+    for (int i = P.mf_level[L]; i < (int)P.mf_order.size(); ++i) {
+      const int f = P.mf_order[i];
+      const MfFront& fr = P.mf_front[f];
+      for (int t = 0; t < fr.nu; t += MF_TILE) {
+        P.mf_task.insert(P.mf_task.end(), {f, 0, 0, t});   // D columns t ..
+        P.mf_task.insert(P.mf_task.end(), {f, 1, t, 0});   // B rows t ..
+      }
+    }
+    P.mf_task_c[L] = (int)P.mf_task.size() / 4;
+    for (int i = P.mf_level[L]; i < (int)P.mf_order.size(); ++i) {
+      const int f = P.mf_order[i];
+      const MfFront& fr = P.mf_front[f];
+      for (int r = 0; r < fr.nu; r += MF_TILE)
+        for (int c = 0; c < fr.nu; c += MF_TILE) P.mf_task.insert(P.mf_task.end(), {f, 2, r, c});
+    }
+  }
+  P.mf_level[nl] = (int)P.mf_order.size();
+  P.mf_task_b[nl] = P.mf_task_c[nl] = (int)P.mf_task.size() / 4;
+  // B and C task starts: a level's S tasks follow its D / B tasks, so the B range of level L is
+  // [task_b[L], task_c[L]) and the C range [task_c[L], task_b[L + 1])
+  return true;
 }
 
 std::vector<int32_t> export_plan(const Plan& P) {
@@ -240,6 +421,17 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
     L.gbF = take(8 * nbk * WU);
     L.gbC = take(8 * nbk * kv);
   }
+  // multifrontal factorisation of G (k_mf.cu): tables, fronts, solve vectors, scratch words
+  L.mf_fr = take(sizeof(MfFront) * P.mf_front.size());
+  L.mf_ord = take(4 * P.mf_order.size());
+  L.mf_lvl = take(4 * P.mf_level.size());
+  L.mf_idx = take(4 * P.mf_idx.size());
+  L.mf_asm = take(4 * P.mf_asm.size());
+  L.mf_map = take(4 * P.mf_map.size());
+  L.mf_task = take(4 * P.mf_task.size());
+  L.mf_F = take(8 * P.mf_fbuf);
+  L.mf_V = take(8 * P.mf_vbuf);
+  L.mf_scr = take(64);
   L.rho = take(8 * n);
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);

@@ -26,6 +26,7 @@ MRCM_ERR_TIMEOUT, MRCM_ERR_CUDA, MRCM_ERR_BUSY, MRCM_ERR_UNSUPPORTED, MRCM_ERR_C
 MRCM_BC_DIRICHLET, MRCM_BC_NEUMANN = 0, 1
 MRCM_PREC_FP64, MRCM_PREC_FP32 = 0, 1
 MRCM_DBG_TRANS, MRCM_DBG_PHI, MRCM_DBG_PSI, MRCM_DBG_MOMENTS, MRCM_DBG_G, MRCM_DBG_COARSE, MRCM_DBG_ZMRCM = range(7)
+COARSE_METHODS = ("inverse", "band", "band_pivoted", "multifrontal")   # mrcm_coarse_method codes
 
 
 class mrcm_problem(C.Structure):
@@ -39,7 +40,8 @@ class mrcm_params(C.Structure):
                 ("alpha", C.c_double), ("tol", C.c_double), ("tol_relative", C.c_int32),
                 ("restart", C.c_int32), ("max_iter", C.c_int32), ("local_prec", C.c_int32),
                 ("smooth_kind", C.c_int32), ("iface_degree", C.c_int32), ("coarse_pivoting", C.c_int32),
-                ("refine_setup", C.c_int32)]
+                ("refine_setup", C.c_int32),
+                ("coarse_solver", C.c_int32)]
 
 
 class mrcm_result(C.Structure):
@@ -71,6 +73,7 @@ _SIGS = {
     "mrcm_profile_read": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32, C.c_int32, C.c_void_p], C.c_int),
     "mrcm_launch_count": ([], C.c_int64),
     "mrcm_measure_fp64_peak": ([C.POINTER(C.c_double), C.c_void_p], C.c_int32),
+    "mrcm_coarse_method": ([_H, C.POINTER(C.c_int32)], C.c_int32),
     "mrcm_residual_norm_noalloc": ([_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "mrcm_server_create": ([C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
     "mrcm_submit": ([C.c_void_p, _P, _Q, C.POINTER(C.c_uint64)], C.c_int),
@@ -146,6 +149,7 @@ def make_params(params):
     q.iface_degree = int(getattr(params, "iface_degree", 0))
     q.coarse_pivoting = int(getattr(params, "coarse_pivoting", 0))
     q.refine_setup = int(getattr(params, "refine_setup", 0))
+    q.coarse_solver = int(getattr(params, "coarse_solver", 0))
     return q
 
 
@@ -279,6 +283,12 @@ class Solver:
         if rc not in (MRCM_OK, MRCM_ERR_NOT_CONVERGED):
             _check(rc, self.handle)
         return {"iterations": res.iterations, "abs_res": res.abs_res, "rel_res": res.rel_res, "status": res.status}
+
+    def coarse_method(self):
+        """How the last factor() factored G: one of COARSE_METHODS (mrcm_coarse_method)."""
+        v = C.c_int32(-1)
+        _check(mrcm_coarse_method(self.handle, C.byref(v)), self.handle)
+        return COARSE_METHODS[v.value]
 
     def debug(self, what, enable_only=False):
         n = C.c_size_t(0)

@@ -52,6 +52,7 @@ class Params:
     iface_degree: int = 0         # 0 piecewise-constant, 1 piecewise-linear side functions
     coarse_pivoting: int = 0      # 0 no-pivot coupling LU with a pivoted fallback, 1 always pivoted
     refine_setup: int = 0         # 1: FP32 set-up solves refined once against the FP64 box operators
+    coarse_solver: int = 0        # 0: nested-dissection multifrontal G (large 2-D systems); 1: band LU
 
 
 # ---------------------------------------------------------------------------------------------

@@ -703,3 +703,32 @@ def test_coupling_lu_without_pivoting_matches_the_pivoted_one(mrcm, name, degree
         assert _rel(z, parts["z"]) < 1e-10
         s.close()
     assert _rel(out[0][0], out[1][0]) < 1e-11
+
+
+@pytest.mark.parametrize("kind", ["random-256", "lognormal-512"])
+def test_multifrontal_coupling_matches_the_band_lu_and_the_oracle(mrcm, kind):
+    # 64 x 64 subdomains (16,128 coupling unknowns): the nested-dissection multifrontal LU
+    # (coarse_solver = 0) against the band LU (coarse_solver = 1) and the oracle (SuperLU with
+    # threshold pivoting on the same G): coefficients c and T(r) to rounding
+    if kind == "random-256":
+        prob = W.random_problem((256, 256, 1), seed=23, contrast=1e3)
+        q = W.Params(sub=(4, 4, 1), oversample=2, smooth_steps=1, tol=1e-10, restart=30, max_iter=300)
+    else:
+        prob, q = W.lognormal(512, seed=3, sub=8, oversample=2, smooth_steps=1, prec=W.PREC_FP64)
+    pre = _oracle(prob, q)
+    assert pre.n_coarse == 16128
+    r = np.random.default_rng(29).standard_normal(prob.K.shape)
+    parts = pre.apply_parts(r)
+    out = {}
+    for solver, method in ((0, "multifrontal"), (1, "band")):
+        q.coarse_solver = solver
+        s = mrcm.Solver(prob, q)
+        s.factor()
+        assert s.coarse_method() == method
+        s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+        z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+        out[solver] = (s.debug(mrcm.MRCM_DBG_COARSE), z)
+        assert _rel(out[solver][0], parts["c"]) < 1e-9
+        assert _rel(z, parts["z"]) < 1e-10
+        s.close()
+    assert _rel(out[0][0], out[1][0]) < 1e-11
