@@ -106,13 +106,13 @@ typedef struct mrcm_params {
                                spaces and basis functions) once against the FP64 box operators, which
                                brings the GMRES count to the FP64 one at the cost of a longer set-up;
                                0 (the default) does not.  Ignored for FP64 local solves. */
-  int32_t coarse_solver;    /* coupling systems of more than 4096 unknowns in 2-D: 0 (the default)
-                               factors G by nested dissection of the subdomain grid (a multifrontal
-                               LU without row interchanges, fronts of dense blocks; Eq. 13-14 solved
-                               exactly up to rounding) and falls back to the pivoted band LU under
-                               the coarse_pivoting rule; 1 always uses the band LU with the blocked
-                               substitution.  Smaller systems keep an explicit G^-1; coarse_pivoting
-                               = 1 implies the band LU. */
+  int32_t coarse_solver;    /* the coupling matrix G in 2-D: 0 (the default) factors it by nested
+                               dissection of the subdomain grid (a multifrontal LU without row
+                               interchanges, fronts of dense blocks; Eq. 13-14 solved exactly up to
+                               rounding) and falls back to partial pivoting under the coarse_pivoting
+                               rule (or when a separator exceeds 128 unknowns); 1 uses the band LU:
+                               an explicit G^-1 up to 4096 unknowns, the blocked substitution above.
+                               coarse_pivoting = 1 and 3-D problems imply the band LU. */
 } mrcm_params;
 
 enum { MRCM_SMOOTH_ADDITIVE = 0, MRCM_SMOOTH_MULTIPLICATIVE = 1 };
@@ -249,9 +249,10 @@ mrcm_status mrcm_profile_read(mrcm_handle h, double* ms, int64_t* launches, int3
 int64_t mrcm_launch_count(void);
 
 /* How the last mrcm_factor_local() factored the coupling matrix G (Eq. 13-14), into the host int
- * *method: MRCM_COARSE_INVERSE (explicit G^-1, systems up to 4096 unknowns), MRCM_COARSE_BAND
- * (band LU without row interchanges), MRCM_COARSE_BAND_PIVOTED (band LU with partial pivoting,
- * asked for or fallen back to), MRCM_COARSE_MULTIFRONTAL (nested dissection, coarse_solver = 0);
+ * *method: MRCM_COARSE_MULTIFRONTAL (nested dissection, coarse_solver = 0), MRCM_COARSE_INVERSE
+ * (band LU and an explicit G^-1, systems up to 4096 unknowns), MRCM_COARSE_BAND (band LU without
+ * row interchanges, blocked substitution), MRCM_COARSE_BAND_PIVOTED (band LU with partial
+ * pivoting above 4096 unknowns, asked for or fallen back to);
  * MRCM_ERR_INVALID_ARG for a null argument or a handle not yet factored. */
 enum { MRCM_COARSE_INVERSE = 0, MRCM_COARSE_BAND = 1, MRCM_COARSE_BAND_PIVOTED = 2, MRCM_COARSE_MULTIFRONTAL = 3 };
 mrcm_status mrcm_coarse_method(mrcm_handle h, int32_t* method);

@@ -169,8 +169,11 @@ MfDev mfdev(mrcm_handle h) {
   m.F = at<double>(h, L.mf_F);
   m.V = at<double>(h, L.mf_V);
   m.scr = at<unsigned>(h, L.mf_scr);
+  m.done = at<unsigned>(h, L.mf_done);
+  m.nfront = (int)P.mf_front.size();
   m.levels = P.mf_level.empty() ? 0 : (int)P.mf_level.size() - 1;
   m.max_f = P.mf_max_f;
+  m.mcap = P.mf_mcap;
   return m;
 }
 
@@ -331,6 +334,7 @@ mrcm_status mrcm_setup(const mrcm_problem* problem, const mrcm_params* params, v
     up(L.mf_map, HP.mf_map.data(), 4 * HP.mf_map.size());
     up(L.mf_task, HP.mf_task.data(), 4 * HP.mf_task.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.mf_scr, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.mf_done, 0, 8 * HP.mf_front.size(), st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(at<unsigned char>(h, L.red), 0, 8 * RED_DOUBLES + 64, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<int>(h, L.flags), 0, 4 * 64, st);
@@ -463,8 +467,12 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   }
   {
     Phase ph(h, MRCM_PH_COARSE_FACTOR, st);
-    if (P.NC <= COARSE_DENSE_MAX) CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
-    else if (!h->coarse_mf) CK(h, launch_coarse_blocks(c, st));
+    if (h->coarse_mf) {
+    } else if (P.NC <= COARSE_DENSE_MAX) {
+      CK(h, launch_coarse_invert(c, at<double>(h, L.Ginv), st));
+    } else {
+      CK(h, launch_coarse_blocks(c, st));
+    }
   }
   CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   int hf = 0;
@@ -508,10 +516,10 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   CoarseDev c = coarse(h);
   {
     Phase ph(h, MRCM_PH_COARSE_SOLVE, st);
-    if (P.NC <= COARSE_DENSE_MAX) {
-      CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
-    } else if (h->coarse_mf) {
+    if (h->coarse_mf) {
       CK(h, launch_mf_solve(mfdev(h), c, at<double>(h, L.mom0), P.E, at<int>(h, L.flags), st));
+    } else if (P.NC <= COARSE_DENSE_MAX) {
+      CK(h, launch_coarse_apply(c, at<double>(h, L.Ginv), at<double>(h, L.mom0), P.E, st));
     } else {
       CK(h, launch_coarse_solve(c, at<double>(h, L.mom0), P.E, st));
     }
@@ -757,8 +765,8 @@ int64_t mrcm_launch_count(void) { return g_launches.load(); }
 mrcm_status mrcm_coarse_method(mrcm_handle h, int32_t* method) {
   if (!h || !method) return fail(h, MRCM_ERR_INVALID_ARG, "null argument");
   if (!h->factored) return fail(h, MRCM_ERR_INVALID_ARG, "the handle is not factored");
-  if (h->plan.NC <= COARSE_DENSE_MAX) *method = MRCM_COARSE_INVERSE;
-  else if (h->coarse_mf) *method = MRCM_COARSE_MULTIFRONTAL;
+  if (h->coarse_mf) *method = MRCM_COARSE_MULTIFRONTAL;
+  else if (h->plan.NC <= COARSE_DENSE_MAX) *method = MRCM_COARSE_INVERSE;
   else *method = h->coarse_pivoted ? MRCM_COARSE_BAND_PIVOTED : MRCM_COARSE_BAND;
   return MRCM_OK;
 }

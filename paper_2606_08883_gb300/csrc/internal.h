@@ -30,7 +30,7 @@ struct MfFront {
   int nch;        // children (0..2)
   int ch[2];      // child front ids
   int mo[2];      // offsets of the children's maps
-  int pad;
+  int par;        // parent front id (-1 at the root)
 };
 constexpr int MF_LEAF = 16;       // leaf rectangles of at most this many subdomains
 constexpr int MF_MAX_NP = 128;    // largest pivot block (its inverse is formed in shared memory)
@@ -73,6 +73,8 @@ struct Plan {
   size_t mf_fbuf = 0;              // doubles of all fronts (F and B)
   size_t mf_vbuf = 0;              // doubles of the solve vectors
   int mf_max_np = 0, mf_max_f = 0;
+  int mf_mcap = 0;                 // front rows staged by the solve (doubles): the largest B or
+                                   // [F11^-1 D], capped at 24576 (192 KB)
 };
 
 // Returns an empty string on success, else the reason the input is invalid.
@@ -93,7 +95,7 @@ struct Layout {
   size_t gtr;                             // Robin coefficients of the Gamma faces, k_local.cu
   size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
   size_t mf_fr, mf_ord, mf_lvl, mf_idx, mf_asm, mf_map, mf_task;   // multifrontal tables, k_mf.cu
-  size_t mf_F, mf_V, mf_scr;              // fronts, solve vectors, barrier and statistics words
+  size_t mf_F, mf_V, mf_scr, mf_done;     // fronts, solve vectors, scratch words, completion flags
   size_t rho, zt;                         // smoothing residual, apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
@@ -300,9 +302,13 @@ struct MfDev {
   const int4* task;
   double* F;
   double* V;
-  unsigned* scr;        // [0, 2) grid barrier, [2, 6) two 8-byte maxima: |G| entries, |S| entries
+  unsigned* scr;        // [2, 6) two 8-byte maxima (|G| entries, |S| entries); [8] solve epoch,
+                        // [9] CTAs finished in the current solve
+  unsigned* done;       // [2 nfront] forward / backward completion epochs of each front
   int levels;
+  int nfront;
   int max_f;            // largest front (np + nu)
+  int mcap;             // doubles of front rows the solve stages in shared memory
 };
 // Set-up: fronts level by level (assembly from the band copy of G and F11^-1, then the D and B
 // tiles, then the Schur-complement tiles) and a final growth check that sets FLAG_NOPIV_REJECTED
@@ -310,7 +316,8 @@ struct MfDev {
 // falls back to the pivoted band LU).
 cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, int* flags, cudaStream_t st);
 // Per apply: right-hand side from mom0 (through c), then one cooperative launch: forward through
-// the levels, backward down them; the solution replaces c.g.
+// the levels, backward down them, each front waiting on its children's (parent's) completion
+// flags; the solution replaces c.g.
 cudaError_t launch_mf_solve(const MfDev& m, const CoarseDev& c, const double* mom0, int E, int* flags,
                             cudaStream_t st);
 cudaError_t launch_arnoldi(const Geo& g, const double* z, double* V, int j, size_t n, double* H, int ldh, double* cs,

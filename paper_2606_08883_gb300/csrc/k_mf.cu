@@ -202,7 +202,7 @@ cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, in
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mf_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tiles);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(m.scr, 0, 64, st);
+  e = cudaMemsetAsync(m.scr + 2, 0, 16, st);   // the statistics; the solve epoch runs on
   if (e != cudaSuccess) return e;
   for (int L = 0; L + 1 < (int)P.mf_level.size(); ++L) {
     const int nf = P.mf_level[L + 1] - P.mf_level[L];
@@ -226,59 +226,148 @@ cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, in
   return cudaGetLastError();
 }
 
-// Solve, one cooperative launch (one CTA per SM): forward through the levels, then backward.  A
-// front's rows are dotted by whole warps (lanes over the columns, then a fixed shuffle tree).
-__global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __restrict__ g, int* flags) {
-  extern __shared__ __align__(16) double v[];
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Solve, one cooperative launch (one CTA per SM), fronts taken level by level in round robin: a
+// front's forward step waits for its children's, its backward step for its parent's (the
+// ancestors have then written x_U), through completion flags stamped with the solve's epoch.  The
+// epoch lives in device memory: every CTA reads it at the start, the last CTA to finish advances
+// it, so repeated launches (also from a captured graph) never see a stale flag as current.  All
+// CTAs are resident and each takes its fronts in increasing level (decreasing, backward), so
+// every wait ends; the spins are bounded all the same (FLAG_TIMEOUT).  Everything a step reads
+// that does not depend on the wait (the front's indices, its right-hand side entries, its B or
+// [F11^-1 D] rows, copied asynchronously into shared memory) is requested before the wait, so a
+// level costs about one flag hand-over and one read.  A front's rows are dotted by whole warps
+// (lanes over the columns, then a fixed shuffle tree), so the result is deterministic.
+__global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __restrict__ g, int* flags, int mcap) {
+  extern __shared__ __align__(16) double smd[];
+  double* v = smd;                                   // [max_f]
+  double* M = v + m.max_f;                           // [mcap] rows of B or of [F11^-1 D]
+  int* ix = reinterpret_cast<int*>(M + mcap);        // [max_f]
+  __shared__ unsigned s_ep;
+  __shared__ int s_ok;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int NW = MF_THREADS / 32;
-  unsigned* bar = m.scr;
+  volatile unsigned* vep = m.scr + 8;
+  if (threadIdx.x == 0) {
+    s_ep = *vep + 1u;
+    s_ok = 1;
+  }
+  __syncthreads();
+  const unsigned E = s_ep;
+  volatile unsigned* fdone = m.done;
+  volatile unsigned* bdone = m.done + m.nfront;
+  // thread 0 polls the flag; the CTA proceeds together (false: the wait gave up)
+  auto wait_for = [&](volatile unsigned* fl) -> bool {
+    if (threadIdx.x == 0) {
+      long long spins = 0;
+      while (*fl != E) {
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicOr(flags, FLAG_TIMEOUT);
+          s_ok = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+  auto publish = [&](volatile unsigned* fl) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *fl = E;
+  };
+  bool ok = true;
   // forward: v_P = g_P + the children's w mapped into P, v_U = their part mapped into U;
   // keep v_P, pass w_U = v_U - B v_P up
-  for (int L = 0; L < m.levels; ++L) {
-    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1]; b += gridDim.x) {
-      const MfFront fr = m.fr[m.order[b]];
+  for (int L = 0; L < m.levels && ok; ++L) {
+    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1] && ok; b += gridDim.x) {
+      const int fid = m.order[b];
+      const MfFront fr = m.fr[fid];
       const int np = fr.np, nu = fr.nu, f = np + nu;
+      const double* Bx = m.F + fr.fo + (size_t)f * f;
+      const bool staged = nu * np <= mcap;
+      if (staged)
+        for (int t = threadIdx.x; t < nu * np; t += MF_THREADS) cp_async8(M + t, Bx + t);
       for (int t = threadIdx.x; t < f; t += MF_THREADS) v[t] = t < np ? g[m.idx[fr.io + t]] : 0.0;
       __syncthreads();
-      for (int c = 0; c < fr.nch; ++c) {
-        const MfFront cf = m.fr[c == 0 ? fr.ch[0] : fr.ch[1]];
+      for (int c = 0; c < fr.nch && ok; ++c) {
+        const int cid = c == 0 ? fr.ch[0] : fr.ch[1];
+        const MfFront cf = m.fr[cid];
         const int* mp = m.map + (c == 0 ? fr.mo[0] : fr.mo[1]);
         const double* wc = m.V + cf.vo + cf.np;
-        for (int t = threadIdx.x; t < cf.nu; t += MF_THREADS) v[mp[t]] += wc[t];
+        ok = wait_for(fdone + cid);
+        if (!ok) break;
+        for (int t = threadIdx.x; t < cf.nu; t += MF_THREADS) v[mp[t]] += __ldcg(wc + t);
         __syncthreads();
       }
+      if (!ok) break;
+      cp_async_wait_all();
+      __syncthreads();
       double* Vf = m.V + fr.vo;
       for (int t = threadIdx.x; t < np; t += MF_THREADS) Vf[t] = v[t];
-      const double* Bx = m.F + fr.fo + (size_t)f * f;
+      const double* Bs = staged ? M : Bx;
       for (int r = wid; r < nu; r += NW) {
         double s = 0.0;
-        for (int k = lane; k < np; k += 32) s = fma(Bx[(size_t)r * np + k], v[k], s);
+        for (int k = lane; k < np; k += 32) s = fma(Bs[(size_t)r * np + k], v[k], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) Vf[np + r] = v[np + r] - s;
       }
-      __syncthreads();
+      publish(fdone + fid);
     }
-    if (!grid_barrier(bar, flags)) return;
   }
-  // backward: x_P = [F11^-1 D] [v_P; -x_U], the ancestors' x_U already in g
-  for (int L = m.levels - 1; L >= 0; --L) {
-    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1]; b += gridDim.x) {
-      const MfFront fr = m.fr[m.order[b]];
+  // backward: x_P = [F11^-1 D] [v_P; -x_U], x_U written by the ancestors
+  for (int L = m.levels - 1; L >= 0 && ok; --L) {
+    for (int b = m.lvl[L] + blockIdx.x; b < m.lvl[L + 1] && ok; b += gridDim.x) {
+      const int fid = m.order[b];
+      const MfFront fr = m.fr[fid];
       const int np = fr.np, nu = fr.nu, f = np + nu;
-      const double* Vf = m.V + fr.vo;
-      for (int t = threadIdx.x; t < f; t += MF_THREADS) v[t] = t < np ? Vf[t] : -g[m.idx[fr.io + t]];
-      __syncthreads();
       const double* F = m.F + fr.fo;
+      const double* Vf = m.V + fr.vo;
+      const bool staged = np * f <= mcap;
+      if (staged)
+        for (int t = threadIdx.x; t < np * f; t += MF_THREADS) cp_async8(M + t, F + t);
+      for (int t = threadIdx.x; t < f; t += MF_THREADS) {
+        ix[t] = m.idx[fr.io + t];
+        if (t < np) v[t] = Vf[t];
+      }
+      if (fr.par >= 0) {
+        ok = wait_for(bdone + fr.par);
+        if (!ok) break;
+      } else {
+        __syncthreads();
+      }
+      for (int t = np + threadIdx.x; t < f; t += MF_THREADS) v[t] = -__ldcg(g + ix[t]);
+      cp_async_wait_all();
+      __syncthreads();
+      const double* Fs = staged ? M : F;
       for (int r = wid; r < np; r += NW) {
         double s = 0.0;
-        for (int k = lane; k < f; k += 32) s = fma(F[(size_t)r * f + k], v[k], s);
+        for (int k = lane; k < f; k += 32) s = fma(Fs[(size_t)r * f + k], v[k], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g[m.idx[fr.io + r]] = s;
+        if (lane == 0) g[ix[r]] = s;
       }
-      __syncthreads();
+      publish(bdone + fid);
     }
-    if (L > 0 && !grid_barrier(bar, flags)) return;
+  }
+  // the last CTA to finish advances the epoch (a CTA that gave up still counts itself)
+  cp_async_wait_all();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(m.scr + 9, 1u) == gridDim.x - 1) {
+      m.scr[9] = 0u;
+      __threadfence();
+      *vep = E;
+    }
   }
 }
 
@@ -289,12 +378,17 @@ cudaError_t launch_mf_solve(const MfDev& m, const CoarseDev& c, const double* mo
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // shared memory: v and the indices of the largest front, and its matrix rows when they fit in
+  // about 192 KB (larger fronts read them from global memory)
+  int mcap = m.mcap;
+  const size_t sm = 12 * (size_t)m.max_f + 8 * (size_t)mcap;
+  e = cudaFuncSetAttribute(k_mf_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   MfDev mm = m;
   double* g = c.g;
   int* fl = flags;
-  void* args[] = {(void*)&mm, (void*)&g, (void*)&fl};
-  e = cudaLaunchCooperativeKernel((const void*)k_mf_solve, dim3(sms), dim3(MF_THREADS), args, 8 * (size_t)m.max_f,
-                                  st);
+  void* args[] = {(void*)&mm, (void*)&g, (void*)&fl, (void*)&mcap};
+  e = cudaLaunchCooperativeKernel((const void*)k_mf_solve, dim3(sms), dim3(MF_THREADS), args, sm, st);
   count_launch(1);
   return e;
 }

@@ -136,7 +136,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
     }
   }
   P.mf = false;
-  if (p.dim == 2 && P.NC > COARSE_DENSE_MAX && q.coarse_solver == 0 && q.coarse_pivoting == 0) P.mf = plan_mf(P);
+  if (p.dim == 2 && P.NC > 0 && q.coarse_solver == 0 && q.coarse_pivoting == 0) P.mf = plan_mf(P);
   if (!P.mf) {
     P.mf_front.clear();
     P.mf_idx.clear();
@@ -218,6 +218,9 @@ static bool plan_mf(Plan& P) {
   const int root = build(0, mx, 0, my);
   const int nf = (int)P.mf_front.size();
   if (!ok || root != nf - 1 || nf == 0) return false;
+  for (int f = 0; f < nf; ++f) P.mf_front[f].par = -1;
+  for (int f = 0; f < nf; ++f)
+    for (int c = 0; c < P.mf_front[f].nch; ++c) P.mf_front[P.mf_front[f].ch[c]].par = f;
   // the front that eliminates each unknown
   std::vector<int> efront(P.NC, -1);
   for (int f = 0; f < nf; ++f) {
@@ -244,7 +247,7 @@ static bool plan_mf(Plan& P) {
   P.mf_asm.clear();
   P.mf_map.clear();
   size_t fo = 0, vo = 0;
-  P.mf_max_np = P.mf_max_f = 0;
+  P.mf_max_np = P.mf_max_f = P.mf_mcap = 0;
   for (int f = 0; f < nf; ++f) {
     MfFront& fr = P.mf_front[f];
     const int fs = fr.np + fr.nu;
@@ -274,6 +277,7 @@ static bool plan_mf(Plan& P) {
     vo += fs;
     P.mf_max_np = std::max(P.mf_max_np, fr.np);
     P.mf_max_f = std::max(P.mf_max_f, fs);
+    P.mf_mcap = std::max(P.mf_mcap, std::min(24576, std::max(fr.np * fs, fr.nu * fr.np)));
   }
   if (vo > (size_t)INT32_MAX) return false;
   P.mf_fbuf = fo;
@@ -432,6 +436,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.mf_F = take(8 * P.mf_fbuf);
   L.mf_V = take(8 * P.mf_vbuf);
   L.mf_scr = take(64);
+  L.mf_done = take(8 * P.mf_front.size());
   L.rho = take(8 * n);
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);
