@@ -813,14 +813,303 @@ struct Twist {
   }
 };
 
+// ---------------------------------------------------------------------------------------------
+// FP32 twisted solve of a resident box of width w <= W (W = 32 or 36) on two warps: warp 0 runs
+// the top recursion and the middle line, warp 1 the bottom recursion, each lane one row of the
+// line blocks (the W - 32 last rows of a 36-wide box from the lanes' columns, by symmetry, with a
+// shared-memory transpose sum).  Row i of the packed block is read at T(i) + j for j <= i and at
+// T(j) + i above (T(k) = k (k + 1) / 2): both conflict-free across a warp.  The warps hand steps
+// over through warp barriers only and meet at the middle line; the bottom recursion's contribution
+// to the middle goes to cb, added before the middle step.  Same arithmetic per output as the block
+// kernel's line products up to the order of the sums.  Returns false when a line block never
+// arrived (the caller reports the timeout).
+template <int W, int NR>
+__device__ __forceinline__ void warp_line_product(const float* __restrict__ S, const float* __restrict__ in, int w,
+                                                  int lane, float (&y)[NR], float& yc, float* part) {
+  constexpr int C = W > 32 ? W - 32 : 0;
+  const int i = lane < w ? lane : 0;
+  const int Ti = i * (i + 1) / 2;
+  // the lane's row of S first, all loads issued before any product: the row-form entries
+  // (T(i) + j) and the column-form ones (T(j) + i) as separate loads, each conflict-free
+  float sr[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    if (j < w) {
+      if (j == 0) {
+        sr[j] = S[Ti];
+      } else if (j >= 32) {
+        sr[j] = S[j * (j + 1) / 2 + i];
+      } else {
+        const float lo = S[Ti + j], up = S[j * (j + 1) / 2 + i];
+        sr[j] = j <= i ? lo : up;
+      }
+    } else {
+      sr[j] = 0.f;
+    }
+  }
+  float a0[NR], a1[NR], own[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    a0[r] = 0.f;
+    a1[r] = 0.f;
+    own[r] = in[i * NR + r];
+  }
+  float pc[C > 0 ? C : 1][NR];
+  if constexpr (NR == 1) {
+    float u[W];   // broadcast reads (a line of one right-hand side starts at any 4-byte offset)
+#pragma unroll
+    for (int j = 0; j < W; ++j) u[j] = j < w ? in[j] : 0.f;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      if (j & 1) a1[0] = fmaf(sr[j], u[j], a1[0]);
+      else a0[0] = fmaf(sr[j], u[j], a0[0]);
+      if (j >= 32) pc[(j - 32) % (C > 0 ? C : 1)][0] = sr[j] * own[0];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      float4 t = *reinterpret_cast<const float4*>(in + j * NR);
+      if (j >= w) t = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a0[r] = fmaf(sr[j], v[r], a0[r]);
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) pc[(j - 32) % (C > 0 ? C : 1)][r] = sr[j] * own[r];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) y[r] = a0[r] + a1[r];
+  yc = 0.f;
+  if (C > 0) {
+    // rows 32 + p: sum over the lanes (columns j < 32) by a transpose through shared memory, then
+    // the corner block
+#pragma unroll
+    for (int p = 0; p < (C > 0 ? C : 1); ++p)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) part[(p * NR + r) * 32 + lane] = lane < w ? pc[p][r] : 0.f;
+    __syncwarp();
+    if (lane < C * NR) {
+      const int p = lane / NR, r = lane - p * NR;
+      if (32 + p < w) {
+        const float4* pp = reinterpret_cast<const float4*>(part + lane * 32);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          const float4 u = pp[k], v = pp[k + 1];
+          s0 += (u.x + u.y) + (u.z + u.w);
+          s1 += (v.x + v.y) + (v.z + v.w);
+        }
+        float cs = s0 + s1;
+        for (int q = 0; q < C; ++q) {
+          if (32 + q >= w) break;
+          const int hi = p > q ? p : q, lo = p > q ? q : p;
+          cs = fmaf(S[(32 + hi) * (33 + hi) / 2 + 32 + lo], in[(32 + q) * NR + r], cs);
+        }
+        yc = cs;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Waits for the phase of the given parity of bar; gives up (false) after a bounded number of polls.
+__device__ __forceinline__ bool mbar_wait_parity(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+constexpr int ENG_NBUF = 16;   // k_solve depth code of the two-warp steps with a ring per warp
+constexpr int ENG_D = 4;       // line blocks in flight per warp
+
+// Line blocks of the two-warp steps: either resident (every block of the box in shared memory,
+// one mbarrier each, copied at the start) or streamed, each warp through its own ring of ENG_D
+// slots refilled by a bulk copy as soon as the warp has used a slot.  A warp takes its blocks in
+// a fixed order, numbered across the refinement passes (seq): warp 0 lines 0..m-1, m, then m-1
+// down to lo_keep; warp 1 lines h-1 down to m+1, then m+1 up to hi_keep.
+struct LineSrc {
+  bool ring;
+  const float* Lb;             // resident blocks
+  unsigned long long* bars;    // resident: one per line; ring: [2][ENG_D]
+  const float* Lg;             // ring: the box's blocks in global memory
+  float* slots;                // ring: [2][ENG_D][LS]
+  int LS;
+};
+
+__device__ __forceinline__ int eng_line(const Twist& tw, int wid, int k) {
+  if (wid == 0) return k <= tw.m ? k : 2 * tw.m - k;
+  const int ne = tw.h - 1 - tw.m;
+  return k < ne ? tw.h - 1 - k : tw.m + 1 + (k - ne);
+}
+__device__ __forceinline__ int eng_count(const Twist& tw, int wid) {
+  return wid == 0 ? tw.m + 1 + (tw.m - tw.lo_keep) : (tw.h - 1 - tw.m) + (tw.hi_keep - tw.m);
+}
+
+template <int W, int NR>
+__device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& base, float* Y, const float* Ec,
+                               float* cb, float* xm, float* tv, float* part_all) {
+  constexpr int C = W > 32 ? W - 32 : 0;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int h = tw.h, m = tw.m, LS = src.LS;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  float* part = part_all + (wid & 1) * (C > 0 ? C : 1) * NR * 32;
+  const int xr = lane < w ? lane : -1;                       // this lane's row
+  const int xc = (C > 0 && lane < C * NR) ? 32 + lane / NR : -1;   // its corner row (one rhs)
+  const int rc = (C > 0 && lane < C * NR) ? lane % NR : 0;
+  const bool xc_on = xc >= 0 && xc < w;
+  float y[NR], yc;
+  const int nseq = wid < 2 ? eng_count(tw, wid) : 0;
+  // ring: lane 0 of the warp issues the copy of block k of this pass into slot (base + k) % ENG_D
+  auto issue = [&](int k) {
+    if (!src.ring || wid >= 2 || lane != 0 || k >= nseq) return;
+    const int gk = base + k, slot = gk % ENG_D;
+    float* dst = src.slots + ((size_t)wid * ENG_D + slot) * LS;
+    bulk_load(dst, src.Lg + (size_t)eng_line(tw, wid, k) * LS, (unsigned)(LS * sizeof(float)),
+              &src.bars[wid * ENG_D + slot]);
+  };
+  // block k of this pass: refill the slot freed by block k - 1, then wait for block k
+  auto fetch = [&](int k) -> const float* {
+    const float* S;
+    bool ok;
+    if (src.ring) {
+      issue(k + ENG_D - 1);
+      const int gk = base + k, slot = gk % ENG_D;
+      ok = mbar_wait_parity(&src.bars[wid * ENG_D + slot], (unsigned)(gk / ENG_D) & 1u);
+      S = src.slots + ((size_t)wid * ENG_D + slot) * LS;
+    } else {
+      const int L = eng_line(tw, wid, k);
+      ok = mbar_wait0(&src.bars[L]);
+      S = src.Lb + (size_t)L * LS;
+    }
+    if (!ok && lane == 0) s_fail = 1;
+    __syncwarp();
+    return S;
+  };
+  for (int k = 0; k < ENG_D - 1; ++k) issue(k);
+  int k = 0;
+  // ---- elimination: warp 0 from the top (u_{A+1} += E_{A+1} S_A^-1 u_A), warp 1 from the bottom
+  //      (u_{B-1} += E_B S_B^-1 u_B, into cb at the middle line)
+  if (wid == 0) {
+    for (int A = 0; A < m; ++A, ++k) {
+      const float* S = fetch(k);
+      warp_line_product<W, NR>(S, Y + (size_t)A * w * NR, w, lane, y, yc, part);
+      float* dst = Y + (size_t)(A + 1) * w * NR;
+      const float* e = Ec + (size_t)(A + 1) * w;
+      if (xr >= 0 && xr < 32)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) dst[xr * NR + r] += e[xr] * y[r];
+      if (xc_on) dst[xc * NR + rc] += e[xc] * yc;
+      __syncwarp();
+    }
+  } else if (wid == 1) {
+    for (int B = h - 1; B >= m + 1; --B, ++k) {
+      const float* S = fetch(k);
+      warp_line_product<W, NR>(S, Y + (size_t)B * w * NR, w, lane, y, yc, part);
+      float* dst = B - 1 == m ? cb : Y + (size_t)(B - 1) * w * NR;
+      const float* e = Ec + (size_t)B * w;
+      if (xr >= 0 && xr < 32)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) dst[xr * NR + r] += e[xr] * y[r];
+      if (xc_on) dst[xc * NR + rc] += e[xc] * yc;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < w * NR; t += blockDim.x) Y[(size_t)m * w * NR + t] += cb[t];
+  __syncthreads();
+  float* tA0 = tv;
+  float* tA1 = tv + w * NR;
+  float* tB0 = tv + 2 * w * NR;
+  float* tB1 = tv + 3 * w * NR;
+  // ---- middle line: x_m = S_m^-1 u_m; the first back inputs u_{m-1} + E_m x_m, u_{m+1} + E_{m+1} x_m
+  if (wid == 0) {
+    const float* S = fetch(k++);
+    warp_line_product<W, NR>(S, Y + (size_t)m * w * NR, w, lane, y, yc, part);
+    const bool up = m - 1 >= tw.lo_keep, dn = m + 1 <= tw.hi_keep;
+    auto emit = [&](int x, int r, float v) {
+      xm[x * NR + r] = v;
+      if (up) tA0[x * NR + r] = Y[((size_t)(m - 1) * w + x) * NR + r] + Ec[(size_t)m * w + x] * v;
+      if (dn) tB0[x * NR + r] = Y[((size_t)(m + 1) * w + x) * NR + r] + Ec[(size_t)(m + 1) * w + x] * v;
+    };
+    if (xr >= 0 && xr < 32)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
+    if (xc_on) emit(xc, rc, yc);
+    __syncwarp();
+  }
+  __syncthreads();
+  // ---- back substitution: x_A = S_A^-1 (u_A + E_{A+1} x_{A+1}) upwards from m - 1 (warp 0),
+  //      x_B = S_B^-1 (u_B + E_B x_{B-1}) downwards from m + 1 (warp 1)
+  if (wid == 0) {
+    int t = 0;
+    for (int A = m - 1; A >= tw.lo_keep; --A, ++t, ++k) {
+      const float* in = (t & 1) ? tA1 : tA0;
+      float* nx = (t & 1) ? tA0 : tA1;
+      const float* S = fetch(k);
+      warp_line_product<W, NR>(S, in, w, lane, y, yc, part);
+      const bool more = A - 1 >= tw.lo_keep;
+      auto emit = [&](int x, int r, float v) {
+        Y[((size_t)A * w + x) * NR + r] = v;
+        if (more) nx[x * NR + r] = Y[((size_t)(A - 1) * w + x) * NR + r] + Ec[(size_t)A * w + x] * v;
+      };
+      if (xr >= 0 && xr < 32)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
+      if (xc_on) emit(xc, rc, yc);
+      __syncwarp();
+    }
+  } else if (wid == 1) {
+    int t = 0;
+    for (int B = m + 1; B <= tw.hi_keep; ++B, ++t, ++k) {
+      const float* in = (t & 1) ? tB1 : tB0;
+      float* nx = (t & 1) ? tB0 : tB1;
+      const float* S = fetch(k);
+      warp_line_product<W, NR>(S, in, w, lane, y, yc, part);
+      const bool more = B + 1 <= tw.hi_keep;
+      auto emit = [&](int x, int r, float v) {
+        Y[((size_t)B * w + x) * NR + r] = v;
+        if (more) nx[x * NR + r] = Y[((size_t)(B + 1) * w + x) * NR + r] + Ec[(size_t)(B + 1) * w + x] * v;
+      };
+      if (xr >= 0 && xr < 32)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
+      if (xc_on) emit(xc, rc, yc);
+      __syncwarp();
+    }
+  }
+  base += nseq;
+  __syncthreads();
+  if (s_fail && src.ring && wid < 2 && lane == 0) {
+    // a copy never arrived: let this warp's copies in flight land (bounded) before returning
+    for (int kk = 0; kk < ENG_D; ++kk) {
+      const int gk = base - 1 - kk;
+      if (gk >= 0) (void)mbar_wait_parity(&src.bars[wid * ENG_D + gk % ENG_D], (unsigned)(gk / ENG_D) & 1u);
+    }
+  }
+  __syncthreads();
+  return s_fail == 0;
+}
+
 // NBUF steps of line blocks in flight (two blocks per step; prefetch distance NBUF - 1), or, for
 // NBUF = 0, the whole box resident: every line block is copied once at the start (one bulk copy and
 // one mbarrier per line, issued in the order the elimination uses them) and serves both the
 // elimination and the back substitution.
 template <typename T, int MODE, int NR, int NBUF>
-__global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
+__global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool RES = NBUF == 0;
+  constexpr bool ENG = NBUF == ENG_NBUF;   // FP32 two-warp steps, a line ring per warp (64 threads)
   const int s = (MODE == MODE_SCHWARZ && a.colour >= 0) ? colour_box(g, a.colour, blockIdx.x) : (int)blockIdx.x;
   // the particular solve runs on the extended region when there is one (the source term's basis
   // function is built there like the others; its restriction to Omega_s is psi_s0)
@@ -828,7 +1117,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   const Box b = box_of(g, s, ohat);
   const int w = b.w, hgt = b.h, LS = a.LS;
   T* Lb = reinterpret_cast<T*>(smem_raw);    // [NBUF][2][LS] line blocks, or [hgt][LS] (resident)
-  T* Y = Lb + (RES ? (size_t)hgt * LS : (size_t)2 * NBUF * LS);  // [hgt][w][NR]: b, u, then x
+  T* Y = Lb + (RES ? (size_t)hgt * LS : ENG ? (size_t)2 * ENG_D * LS : (size_t)2 * NBUF * LS);  // [hgt][w][NR]: b, u, then x
   T* tv = Y + (size_t)hgt * w * NR;          // [4][w][NR] ping-pong inputs of the back steps (top, bottom)
   T* xm = tv + 4 * w * NR;                   // [w][NR] x of the middle line
   T* cb = xm + w * NR;                       // [w][NR] bottom contribution to the middle (odd h)
@@ -843,12 +1132,15 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
   T* X0 = reinterpret_cast<T*>(                // [hgt][w][NR] first solution (REF only)
       smem_raw + ((reinterpret_cast<unsigned char*>(bars + hgt) - smem_raw + 15) & ~(size_t)15));
+  float* part_all = reinterpret_cast<float*>(  // [2 warps][4][NR][32] corner-row sums (FP32 two-warp steps)
+      smem_raw + ((reinterpret_cast<unsigned char*>(X0 + (REF ? (size_t)hgt * w * NR : 0)) - smem_raw + 15) &
+                  ~(size_t)15));
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * box_stride(w, hgt, LS);
   // the couplings join the first copy group (ring) or their own group (resident)
   for (int c = tid; c < ecn * (int)sizeof(T) / 16; c += nt)
     cp_async16(reinterpret_cast<unsigned char*>(Ec) + 16 * c, reinterpret_cast<const unsigned char*>(Lg + (size_t)hgt * LS) + 16 * c);
-  if (RES) cp_async_commit();
+  if (RES || ENG) cp_async_commit();
   Twist tw;
   tw.h = hgt;
   tw.m = hgt / 2;
@@ -864,7 +1156,7 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
   }
   const int nsteps = tw.nf + 1 + tw.nb;
   auto issue_step = [&](int st) {
-    if (RES) return;
+    if (RES || ENG) return;
     if (st < nsteps) {
       int A, B;
       tw.lines(st, A, B);
@@ -889,6 +1181,12 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       }
       bulk_load(Lb + (size_t)tw.m * LS, Lg + (size_t)tw.m * LS, bytes, &bars[tw.m]);
     }
+  } else if constexpr (ENG) {
+    if (tid == 0) {
+      for (int k = 0; k < 2 * ENG_D; ++k) mbar_init(&bars[k], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
   } else {
     for (int p = 0; p < NBUF - 1; ++p) issue_step(p);  // NBUF = 1: no prefetch, each step loads its own lines
   }
@@ -996,13 +1294,14 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       __syncthreads();
     }
   }
-  if constexpr (RES) cp_async_wait<0>();  // couplings (each thread waits for its own copies)
+  if constexpr (RES || ENG) cp_async_wait<0>();  // couplings (each thread waits for its own copies)
 
   const int m = tw.m;
   T* tA0 = tv;                   // top back inputs (ping-pong)
   T* tA1 = tv + w * NR;
   T* tB0 = tv + 2 * w * NR;      // bottom back inputs (ping-pong)
   T* tB1 = tv + 3 * w * NR;
+  int eng_base = 0;   // line blocks the two-warp steps have taken so far (ring slots and phases)
   for (int pass = 0; pass < (REF ? 2 : 1); ++pass) {
   if (REF && pass == 1) {
     // x0 aside; r = b - A x0 in FP64 per cell (A from the box's FP64 line coefficients: diagonal d,
@@ -1054,10 +1353,41 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
       }
     }
     __syncthreads();
-    if constexpr (!RES)
+    if constexpr (!RES && !ENG)
       for (int p = 0; p < NBUF - 1; ++p) issue_step(p);
   }
-  for (int st = 0; st < nsteps; ++st) {
+  bool two_warp = false;
+  if constexpr ((RES || ENG) && sizeof(T) == 4) {
+    // FP32 boxes up to 36 wide: the two-warp steps (no block barrier per step), on the resident
+    // blocks or on a ring per warp (the launcher takes ENG only for such boxes)
+    if (ENG || (w <= 36 && hgt >= 2)) {
+      LineSrc src;
+      src.ring = ENG;
+      src.Lb = reinterpret_cast<const float*>(Lb);
+      src.bars = bars;
+      src.Lg = reinterpret_cast<const float*>(Lg);
+      src.slots = reinterpret_cast<float*>(Lb);
+      src.LS = LS;
+      float* Yf = reinterpret_cast<float*>(Y);
+      const float* Ef = reinterpret_cast<const float*>(Ec);
+      float* cf = reinterpret_cast<float*>(cb);
+      float* xf = reinterpret_cast<float*>(xm);
+      float* tf = reinterpret_cast<float*>(tv);
+      const bool ok = w <= 32 ? twisted_engine<32, NR>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all)
+                              : twisted_engine<36, NR>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all);
+      if (!ok) {
+        if (tid == 0) {
+          atomicOr(a.flags, FLAG_TIMEOUT);
+          if (RES)
+            for (int L = 0; L < hgt; ++L) (void)mbar_wait0(&bars[L]);
+        }
+        __syncthreads();
+        return;
+      }
+      two_warp = true;
+    }
+  }
+  for (int st = 0; st < (two_warp ? 0 : nsteps); ++st) {
     int A, B;
     tw.lines(st, A, B);
     const T* LA;
@@ -1281,11 +1611,12 @@ __global__ void __launch_bounds__(512) k_solve(Geo g, SolveArgs a) {
 template <typename T, int MODE, int NR, int NBUF>
 static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
-  const size_t lines = NBUF == 0 ? (size_t)h * a.LS : 2 * NBUF * (size_t)a.LS;
+  const size_t lines = NBUF == 0 ? (size_t)h * a.LS : NBUF == ENG_NBUF ? 2 * ENG_D * (size_t)a.LS : 2 * NBUF * (size_t)a.LS;
   const size_t ecn = ((size_t)h * w + 3) & ~(size_t)3;
   const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
   return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32 +
-         (REF ? sizeof(T) * (size_t)h * w * NR + 16 : 0);
+         (REF ? sizeof(T) * (size_t)h * w * NR + 16 : 0) +
+         (sizeof(T) == 4 && (NBUF == 0 || NBUF == ENG_NBUF) ? 4 * (2 * 4 * NR * 32) + 16 : 0);
 }
 
 template <typename T, int MODE, int NR, int NBUF>
@@ -1296,6 +1627,7 @@ static cudaError_t launch_solve_nb(const Geo& g, const SolveArgs& a, size_t sm, 
   const int w = g.sx + (ohat ? 2 * g.l : 0);
   int threads = (2 * w * LineTPR<T>::value + 31) / 32 * 32;
   if (threads < 128) threads = 128;
+  if (NBUF == ENG_NBUF) threads = 64;   // the two warps of the two-warp steps
   int grid = g.mx * g.my;
   if (MODE == MODE_SCHWARZ && a.colour >= 0)
     grid = ((g.mx - (a.colour & 1) + 1) / 2) * ((g.my - ((a.colour >> 1) & 1) + 1) / 2);
@@ -1316,6 +1648,10 @@ template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_depth(const Geo& g, const SolveArgs& a, bool ohat, int nbuf, cudaStream_t st) {
   switch (nbuf) {
     case 0: return launch_solve_nb<T, MODE, NR, 0>(g, a, solve_smem<T, MODE, NR, 0>(g, a, ohat), ohat, st);
+    case ENG_NBUF:
+      if constexpr (sizeof(T) == 4)
+        return launch_solve_nb<T, MODE, NR, ENG_NBUF>(g, a, solve_smem<T, MODE, NR, ENG_NBUF>(g, a, ohat), ohat, st);
+      return cudaErrorInvalidValue;
     case 8: return launch_solve_nb<T, MODE, NR, 8>(g, a, solve_smem<T, MODE, NR, 8>(g, a, ohat), ohat, st);
     case 4: return launch_solve_nb<T, MODE, NR, 4>(g, a, solve_smem<T, MODE, NR, 4>(g, a, ohat), ohat, st);
     case 2: return launch_solve_nb<T, MODE, NR, 2>(g, a, solve_smem<T, MODE, NR, 2>(g, a, ohat), ohat, st);
@@ -1327,18 +1663,23 @@ template <typename T, int MODE, int NR>
 static cudaError_t launch_solve_t(const Geo& g, const SolveArgs& a, bool ohat, cudaStream_t st) {
   constexpr size_t kMaxSmem = 227 * 1024;
   constexpr size_t kBudget = 100 * 1024;  // keep two CTAs per SM when possible
-  const size_t sm[5] = {solve_smem<T, MODE, NR, 0>(g, a, ohat), solve_smem<T, MODE, NR, 8>(g, a, ohat),
+  const size_t sm[6] = {solve_smem<T, MODE, NR, 0>(g, a, ohat), solve_smem<T, MODE, NR, 8>(g, a, ohat),
                         solve_smem<T, MODE, NR, 4>(g, a, ohat), solve_smem<T, MODE, NR, 2>(g, a, ohat),
-                        solve_smem<T, MODE, NR, 1>(g, a, ohat)};
-  const int depth[5] = {0, 8, 4, 2, 1};
+                        solve_smem<T, MODE, NR, 1>(g, a, ohat), solve_smem<T, MODE, NR, ENG_NBUF>(g, a, ohat)};
+  const int depth[6] = {0, 8, 4, 2, 1, ENG_NBUF};
+  // FP32 boxes up to 36 wide (at least 2 ENG_D lines high) take the two-warp steps with a line
+  // ring per warp by default
+  const int bw = g.sx + (ohat ? 2 * g.l : 0), bh = g.sy + (ohat ? 2 * g.l : 0);
+  const bool eng = sizeof(T) == 4 && bw <= 36 && bh >= 2 * ENG_D && sm[5] <= kMaxSmem;
   int builtin = 1;
-  if (sizeof(T) == 4 && sm[0] <= kBudget + 14 * 1024) builtin = 0;
+  if (eng) builtin = ENG_NBUF;
+  else if (sizeof(T) == 4 && sm[0] <= kBudget + 14 * 1024) builtin = 0;
   else if (sizeof(T) == 4 && sm[1] <= kBudget) builtin = 8;
   else if (sm[2] <= kMaxSmem) builtin = 4;
   else if (sm[3] <= kMaxSmem) builtin = 2;
-  int cand[5], nc = 0;
-  for (int i = 0; i < 5; ++i)
-    if (sm[i] <= kMaxSmem) cand[nc++] = depth[i];
+  int cand[6], nc = 0;
+  for (int i = 0; i < 6; ++i)
+    if (sm[i] <= kMaxSmem && (i < 5 || eng)) cand[nc++] = depth[i];
   const bool repeatable = !(MODE == MODE_SCHWARZ && a.zin == a.out);
   if (repeatable && nc > 1) {
     const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
