@@ -510,7 +510,8 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
     // there), on the subdomains' own Robin factors when l = 0
     const bool ext = P.l > 0;
     CK(h, launch_particular(g, at<void>(h, ext ? L.Linv_ohat_r : L.Linv_loc), ext ? L.LSo : L.LSl, fp32, r,
-                            at<double>(h, L.psi0), at<double>(h, L.mom0), at<int>(h, L.flags), st));
+                            at<double>(h, L.psi0), at<double>(h, L.mom0), at<int>(h, L.flags), st,
+                            at<float>(h, L.rho)));
   }
   // coupling system
   CoarseDev c = coarse(h);
@@ -546,7 +547,8 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
     } else {
       const double* zin = zb[(s - it) & 1];
       double* zout = zb[(s - it - 1) & 1];
-      CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), -1, st));
+      CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), -1, st,
+                           at<float>(h, L.rho)));
     }
   }
   return MRCM_OK;

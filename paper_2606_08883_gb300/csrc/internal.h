@@ -96,7 +96,7 @@ struct Layout {
   size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
   size_t mf_fr, mf_ord, mf_lvl, mf_idx, mf_asm, mf_map, mf_task;   // multifrontal tables, k_mf.cu
   size_t mf_F, mf_V, mf_scr, mf_done;     // fronts, solve vectors, scratch words, completion flags
-  size_t rho, zt;                         // smoothing residual, apply output scratch
+  size_t rho, zt;                         // FP32 staged right-hand sides (k_stage32), apply output scratch
   size_t V, Z, w, Hs, red, flags, tmpv;   // Krylov basis and scratch
   size_t tab;                             // device copies of the plan tables
   size_t apart, atot, aT;                 // Arnoldi partial sums, totals, (I + R)^-1
@@ -244,10 +244,11 @@ cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, d
                             const double* coef = nullptr);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
                          double* mom, int* flags, cudaStream_t st, const double* coef = nullptr);
+// stage32 (FP32 solves, optional): n floats of scratch for the right-hand side formed once on the grid
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, int* flags, cudaStream_t st);
+                              double* mom0, int* flags, cudaStream_t st, float* stage32 = nullptr);
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, int colour, cudaStream_t st);
+                           double* zout, int* flags, int colour, cudaStream_t st, float* stage32 = nullptr);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
 size_t factor_smem_bytes(int w, bool fp32, int nch);

@@ -698,6 +698,8 @@ struct SolveArgs {
   int colour;          // schwarz: -1 all boxes, else only the boxes of this colour (see colour_box)
   int q;               // informed, basis: the degree of the side functions this launch handles
   const double* coef;  // FP32 informed, basis: the box's FP64 line coefficients [S][h][w][d, o, e]
+  const float* in32;   // FP32 particular, additive Schwarz: the right-hand side already formed on the grid
+                       // in FP32 (r, or the sweep's residual r - A z), fetched by asynchronous copies
 };
 
 // Degree-q function of a box side at its face t of len: 1, or the linear function of the position
@@ -856,9 +858,24 @@ __device__ __forceinline__ void warp_line_product(const float* __restrict__ S, c
   }
   float pc[C > 0 ? C : 1][NR];
   if constexpr (NR == 1) {
-    float u[W];   // broadcast reads (a line of one right-hand side starts at any 4-byte offset)
+    float u[W];   // broadcast reads: four at a time when the line starts on 16 bytes (w % 4 == 0)
+    if ((w & 3) == 0) {
 #pragma unroll
-    for (int j = 0; j < W; ++j) u[j] = j < w ? in[j] : 0.f;
+      for (int j = 0; j < W; j += 4) {
+        if (j < w) {
+          const float4 t = *reinterpret_cast<const float4*>(in + j);
+          u[j] = t.x;
+          u[j + 1] = t.y;
+          u[j + 2] = t.z;
+          u[j + 3] = t.w;
+        } else {
+          u[j] = u[j + 1] = u[j + 2] = u[j + 3] = 0.f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < W; ++j) u[j] = j < w ? in[j] : 0.f;
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       if (j & 1) a1[0] = fmaf(sr[j], u[j], a1[0]);
@@ -1195,7 +1212,26 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
   for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
   for (int k = tid; k < w * NR; k += nt) cb[k] = (T)0;
   __syncthreads();
-  if (MODE == MODE_PARTICULAR) {
+  bool staged = false;
+  if constexpr (sizeof(T) == 4 && NR == 1 && (MODE == MODE_PARTICULAR || MODE == MODE_SCHWARZ)) {
+    if (a.in32 != nullptr) {
+      // one round of 4-byte asynchronous copies of the box's cells (cells off the grid stay 0)
+      for (int k = tid; k < hgt * w; k += nt) {
+        const int J = k / w, x = k - J * w;
+        const int gx = b.ox + x, gy = b.oy + J;
+        if (active(g, gx, gy)) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(Y + k);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(a.in32 + (size_t)gy * g.nx + gx)
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();
+      staged = true;
+    }
+  }
+  if (staged) {
+  } else if (MODE == MODE_PARTICULAR) {
     // four cells per thread per pass, all loads before the stores
     const double* __restrict__ rin = a.in;
     for (int k0 = tid; k0 < hgt * w; k0 += 4 * nt) {
@@ -1730,9 +1766,41 @@ cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, cons
   return launch_solve<MODE_BASIS, 4>(g, a, false, fp32, st);
 }
 
+// FP32 right-hand sides of the FP32 particular solves and additive sweeps, formed once on the grid
+// (z == nullptr: r; else the sweep's residual r - A z in FP64, rounded once), so that each box
+// fetches its cells with one round of asynchronous copies instead of forming them
+__global__ void k_stage32(Geo g, const double* __restrict__ r, const double* __restrict__ z, float* __restrict__ out) {
+  const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+  if (gx >= g.nx) return;
+  const size_t c = (size_t)gy * g.nx + gx;
+  double v = r[c];
+  if (z) {
+    const double zc = z[c];
+    const double zw = gx > 0 ? z[c - 1] : 0.0, ze = gx < g.nx - 1 ? z[c + 1] : 0.0;
+    const double zs = gy > 0 ? z[c - g.nx] : 0.0, zn = gy < g.ny - 1 ? z[c + g.nx] : 0.0;
+    const size_t cx = (size_t)gy * (g.nx + 1) + gx;
+    const double wx = g.Tx[cx + 1] * (zc - ze) - g.Tx[cx] * (zw - zc);
+    const double wy = g.Ty[c + g.nx] * (zc - zn) - g.Ty[c] * (zs - zc);
+    v -= wx + wy;
+  }
+  out[c] = (float)v;
+}
+
+static cudaError_t launch_stage32(const Geo& g, const double* r, const double* z, float* out, cudaStream_t st) {
+  dim3 grid((g.nx + 255) / 256, g.ny);
+  k_stage32<<<grid, 256, 0, st>>>(g, r, z, out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, int* flags, cudaStream_t st) {
+                              double* mom0, int* flags, cudaStream_t st, float* stage32) {
   SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags, -1};
+  if (fp32 && stage32) {
+    const cudaError_t e = launch_stage32(g, r, nullptr, stage32, st);
+    if (e != cudaSuccess) return e;
+    a.in32 = stage32;
+  }
   return launch_solve<MODE_PARTICULAR, 1>(g, a, g.l > 0, fp32, st);
 }
 
@@ -1741,8 +1809,13 @@ cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32,
 // is narrower than a subdomain, so no box reads (region plus the stencil's one-cell rim) a cell
 // that another box of its colour writes.
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, int colour, cudaStream_t st) {
+                           double* zout, int* flags, int colour, cudaStream_t st, float* stage32) {
   SolveArgs a{Linv, LS, r, zout, nullptr, zin, flags, colour};
+  if (fp32 && stage32 && colour < 0) {   // additive: every box from the same residual
+    const cudaError_t e = launch_stage32(g, r, zin, stage32, st);
+    if (e != cudaSuccess) return e;
+    a.in32 = stage32;
+  }
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 

@@ -437,7 +437,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.mf_V = take(8 * P.mf_vbuf);
   L.mf_scr = take(64);
   L.mf_done = take(8 * P.mf_front.size());
-  L.rho = take(8 * n);
+  L.rho = take(8 * n);                     // FP32 right-hand sides staged on the grid (k_stage32)
   L.zt = take(8 * n);
   L.V = take(8 * (size_t)(L.m + 1) * n);
   L.Z = take(8 * (size_t)L.m * n);
