@@ -1118,6 +1118,16 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
   return s_fail == 0;
 }
 
+// Position of cell (x, J) on the perimeter of a w x h box (-1 inside): the first line, the last
+// line, then the first and the last column between them.
+__device__ __forceinline__ int perim_index(int x, int J, int w, int h) {
+  if (J == 0) return x;
+  if (J == h - 1) return w + x;
+  if (x == 0) return 2 * w + J - 1;
+  if (x == w - 1) return 2 * w + (h - 2) + J - 1;
+  return -1;
+}
+
 // NBUF steps of line blocks in flight (two blocks per step; prefetch distance NBUF - 1), or, for
 // NBUF = 0, the whole box resident: every line block is copied once at the start (one bulk copy and
 // one mbarrier per line, issued in the order the elimination uses them) and serves both the
@@ -1152,6 +1162,10 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
   float* part_all = reinterpret_cast<float*>(  // [2 warps][4][NR][32] corner-row sums (FP32 two-warp steps)
       smem_raw + ((reinterpret_cast<unsigned char*>(X0 + (REF ? (size_t)hgt * w * NR : 0)) - smem_raw + 15) &
                   ~(size_t)15));
+  // REF: the right-hand side on the box perimeter in FP64 [2w + 2h - 4][NR] (it is zero inside), kept
+  // from the prologue for the refinement residual
+  double* bE = reinterpret_cast<double*>(
+      smem_raw + ((reinterpret_cast<unsigned char*>(part_all + 2 * 4 * NR * 32) - smem_raw + 15) & ~(size_t)15));
   const int tid = threadIdx.x, nt = blockDim.x;
   const T* Lg = reinterpret_cast<const T*>(a.Linv) + (size_t)s * box_stride(w, hgt, LS);
   // the couplings join the first copy group (ring) or their own group (resident)
@@ -1211,6 +1225,8 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
   // ---------------- right-hand sides into Y
   for (int k = tid; k < hgt * w * NR; k += nt) Y[k] = (T)0;
   for (int k = tid; k < w * NR; k += nt) cb[k] = (T)0;
+  if (REF)
+    for (int k = tid; k < (2 * w + 2 * hgt - 4) * NR; k += nt) bE[k] = 0.0;
   __syncthreads();
   bool staged = false;
   if constexpr (sizeof(T) == 4 && NR == 1 && (MODE == MODE_PARTICULAR || MODE == MODE_SCHWARZ)) {
@@ -1307,7 +1323,9 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
           const int hi = ax == 0 ? min(b.oy + hgt, g.ny) : min(b.ox + w, g.nx);
           lam = side_fn(a.q, (ax == 0 ? gy : gx) - lo, hi - lo);
         }
-        Y[(J * w + x) * NR + r] += (T)(face_tr(g, gx, gy, ax, dir, nullptr, nullptr) * lam);
+        const double bv = face_tr(g, gx, gy, ax, dir, nullptr, nullptr) * lam;
+        Y[(J * w + x) * NR + r] += (T)bv;
+        if (REF) bE[perim_index(x, J, w, hgt) * NR + r] += bv;
       }
       __syncthreads();
     }
@@ -1325,6 +1343,7 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
         for (int r = 0; r < NR; ++r) {
           const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + t];
           Y[(J * w + x) * NR + r] += (T)(tr * ph);
+          if (REF) bE[perim_index(x, J, w, hgt) * NR + r] += tr * ph;
         }
       }
       __syncthreads();
@@ -1359,32 +1378,9 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
         if (x > 0) ax -= oL * (double)X0[(c - 1) * NR + r];
         if (J > 0) ax -= e * (double)X0[(c - w) * NR + r];
         if (J + 1 < hgt) ax -= eD * (double)X0[(c + w) * NR + r];
-        double bv = 0.0;
-        if (on && MODE == MODE_INFORMED && robin_side(g, s, r)) {
-          // lambda^r on the faces of side r of the oversampled box
-          const bool edge = r == 0 ? x == 0 : (r == 1 ? x == w - 1 : (r == 2 ? J == 0 : J == hgt - 1));
-          if (edge) {
-            const int ax_ = r < 2 ? 0 : 1, dir = (r & 1) ? 1 : -1;
-            double lam = 1.0;
-            if (a.q) {
-              const int lo = ax_ == 0 ? max(b.oy, 0) : max(b.ox, 0);
-              const int hi = ax_ == 0 ? min(b.oy + hgt, g.ny) : min(b.ox + w, g.nx);
-              lam = side_fn(a.q, (ax_ == 0 ? gy : gx) - lo, hi - lo);
-            }
-            bv = face_tr(g, gx, gy, ax_, dir, nullptr, nullptr) * lam;
-          }
-        } else if (on && MODE == MODE_BASIS) {
-          // t_R phi^r on the Gamma faces of the subdomain's Robin sides that touch this cell
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const bool edge = k == 0 ? x == 0 : (k == 1 ? x == w - 1 : (k == 2 ? J == 0 : J == hgt - 1));
-            if (!edge || !robin_side(g, s, k)) continue;
-            const int t = k < 2 ? J : x;
-            if (t >= side_len(g, s, k)) continue;
-            const double tr = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, nullptr, nullptr);
-            bv += tr * a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + t];
-          }
-        }
+        // the right-hand side, kept in FP64 on the perimeter by the prologue
+        const int pe = perim_index(x, J, w, hgt);
+        const double bv = (on && pe >= 0) ? bE[pe * NR + r] : 0.0;
         Y[c * NR + r] = (T)(bv - ax);
       }
     }
@@ -1652,7 +1648,8 @@ static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
   return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32 +
          (REF ? sizeof(T) * (size_t)h * w * NR + 16 : 0) +
-         (sizeof(T) == 4 && (NBUF == 0 || NBUF == ENG_NBUF) ? 4 * (2 * 4 * NR * 32) + 16 : 0);
+         (sizeof(T) == 4 && (NBUF == 0 || NBUF == ENG_NBUF) ? 4 * (2 * 4 * NR * 32) + 16 : 0) +
+         (REF ? 4 * (2 * 4 * NR * 32) + 8 * (size_t)(2 * w + 2 * h) * NR + 32 : 0);
 }
 
 template <typename T, int MODE, int NR, int NBUF>
