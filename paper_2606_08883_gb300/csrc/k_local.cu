@@ -502,22 +502,20 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
 #pragma unroll
     for (int k = 0; k < W; ++k) {
       float* bk = sm.bc[k & 1];
-      constexpr int RW = W;   // entries published for a pivot row held by one lane
-      if (k < 32) {
-        if (lane == k) {
+      // the pivot row, published as column k (symmetric up to rounding): one entry per lane, and
+      // for k < 32 the corner columns of row k from lane k
+      if (lane < W) bk[lane] = a[k];
+      if (C > 0 && k < 32 && lane == k) {
 #pragma unroll
-          for (int j = 0; j < RW; j += 4)
-            *reinterpret_cast<float4*>(bk + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
-        }
-      } else {
-        bk[lane] = a[k];
+        for (int q = 0; q < C; q += 4)
+          *reinterpret_cast<float4*>(bk + 32 + q) = make_float4(a[32 + q], a[33 + q], a[34 + q], a[35 + q]);
       }
       __syncwarp();
       const int nr = k < 32 ? W : R0;
       float rowk[W];
 #pragma unroll
       for (int j = 0; j < W; j += 4)
-        if (j < nr) {
+        if (j < nr && j < R0 + (k < 32 ? C : 0)) {
           const float4 t = *reinterpret_cast<const float4*>(bk + j);
           rowk[j] = t.x;
           rowk[j + 1] = t.y;
@@ -533,7 +531,7 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         bad = true;
         dk = 1.f;
       }
-      const float rinv = 1.f / dk;
+      const float rinv = __frcp_rn(dk);
       const bool me = k < 32 && lane == k;
       const float gsc = me ? 1.f - rinv : a[k] * rinv;
 #pragma unroll
