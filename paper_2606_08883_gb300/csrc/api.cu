@@ -397,16 +397,16 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * P.nq * L.smax, st));
   // FP32 set-up solves refined once against the FP64 box operators (refine_setup)
   const bool refine = fp32 && h->prm.refine_setup != 0;
-  if (refine && P.l > 0) CK(h, launch_line_coef(g, BOX_OHAT_ROBIN, at<double>(h, L.coef_o), st));
   if (P.l > 0) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
-    CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st));
+    CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st,
+                        refine ? at<double>(h, L.coef_o) : nullptr));
   }
   const bool smooth = h->prm.smooth_steps > 0;
   {
     Phase ph(h, MRCM_PH_FACTOR_OMEGA, h->side);
-    CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, h->side));
-    if (refine) CK(h, launch_line_coef(g, BOX_OMEGA_ROBIN, at<double>(h, L.coef_l), h->side));
+    CK(h, launch_factor(g, BOX_OMEGA_ROBIN, L.wl, L.hl, L.LSl, at<void>(h, L.Linv_loc), fp32, flags, h->side,
+                        refine ? at<double>(h, L.coef_l) : nullptr));
   }
   CK(h, cudaEventRecord(h->omega_ev, h->side));
   if (smooth) {

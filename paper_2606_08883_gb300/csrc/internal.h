@@ -235,8 +235,9 @@ cudaError_t launch_fluxes(const Geo& g, const int* bc_kind, const double* const*
 
 // local factor / solve (k_local.cu)
 enum BoxKind : int { BOX_OMEGA_ROBIN = 0, BOX_OHAT_ROBIN = 1, BOX_OHAT_DIRICHLET = 2 };
+// coef (optional): the box kind's FP64 line coefficients [S][h][w][d, o, e], written on the way
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
-                          cudaStream_t st);
+                          cudaStream_t st, double* coef = nullptr);
 // each cell's FP64 line coefficients [S][h][w][diagonal, x coupling, y coupling] of the boxes of
 // one kind; given to the FP32 informed and basis solves (coef), they refine once against them
 cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st);

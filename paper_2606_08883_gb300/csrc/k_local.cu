@@ -333,9 +333,10 @@ struct SweepSmem {
   float stage[STG];                // S_J^-1, packed lower
 };
 
-// coefficients of cell x of line J as floats (identity rows past the box width)
+// coefficients of cell x of line J as floats (identity rows past the box width); with cf, also
+// stored there in FP64 [d, o, e] (the refinement of the FP32 set-up solves reads them)
 __device__ __forceinline__ void line_coeffs_f(const Geo& g, const Box& b, bool robin, int J, int x, float& d, float& o,
-                                              float& e) {
+                                              float& e, double* cf = nullptr) {
   if (x >= b.w) {
     d = 1.f;
     o = 0.f;
@@ -347,11 +348,16 @@ __device__ __forceinline__ void line_coeffs_f(const Geo& g, const Box& b, bool r
   d = (float)dd;
   o = (float)oo;
   e = (float)ee;
+  if (cf) {
+    cf[0] = dd;
+    cf[1] = oo;
+    cf[2] = ee;
+  }
 }
 
 template <int W>
 __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, float* __restrict__ Linv,
-                                                     int* flags) {
+                                                     int* flags, double* __restrict__ coef) {
   static_assert(W % 4 == 0 && W <= 36, "sweep widths: multiples of 4 up to 36");
   constexpr int C = W > 32 ? W - 32 : 0;   // corner size
   constexpr int C1 = C > 0 ? C : 1;
@@ -396,8 +402,9 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
     const bool dn = mid && m + 1 < h;      // the middle line's second neighbour S_{m+1}^-1
     // (1) line data: diagonal, right coupling, u_x = E_x r_x towards the previous line
     float d0, o0, e0, d1 = 1.f, o1 = 0.f, e1 = 0.f;
-    line_coeffs_f(g, b, robin, J, lane, d0, o0, e0);
-    if (lane < C) line_coeffs_f(g, b, robin, J, 32 + lane, d1, o1, e1);
+    double* cfl = coef ? coef + (((size_t)s * h + J) * w) * 3 : nullptr;   // this line's FP64 coefficients
+    line_coeffs_f(g, b, robin, J, lane, d0, o0, e0, cfl ? cfl + 3 * lane : nullptr);
+    if (lane < C) line_coeffs_f(g, b, robin, J, 32 + lane, d1, o1, e1, cfl ? cfl + 3 * (32 + lane) : nullptr);
     if (lane < w) ec_out[(size_t)J * w + lane] = e0;
     if (lane < C && 32 + lane < w) ec_out[(size_t)J * w + 32 + lane] = e1;
     const float eu0 = (top || mid) ? e0 : ep0, eu1 = (top || mid) ? e1 : ep1;
@@ -580,8 +587,9 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
 }
 
 template <int W>
-static cudaError_t launch_factor_sweep(const Geo& g, int kind, int LS, float* Linv, int* flags, cudaStream_t st) {
-  k_factor_sweep<W><<<g.mx * g.my, 64, 0, st>>>(g, kind, LS, Linv, flags);
+static cudaError_t launch_factor_sweep(const Geo& g, int kind, int LS, float* Linv, int* flags, double* coef,
+                                       cudaStream_t st) {
+  k_factor_sweep<W><<<g.mx * g.my, 64, 0, st>>>(g, kind, LS, Linv, flags, coef);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -616,7 +624,7 @@ size_t factor_smem_bytes(int w, bool fp32, int nch) {
 }
 
 cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* Linv, bool fp32, int* flags,
-                          cudaStream_t st) {
+                          cudaStream_t st, double* coef) {
   (void)hgt;
   const int S = g.mx * g.my;
   // both recursions at once when two sets of working arrays still leave room for two CTAs per SM
@@ -624,12 +632,16 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
   const size_t sm = factor_smem_bytes(w, fp32, nch);
   if (fp32 && w <= 36) {   // register-resident sweep, box width padded to a multiple of 4
     float* L = (float*)Linv;
-    if (w <= 16) return launch_factor_sweep<16>(g, kind, LS, L, flags, st);
-    if (w <= 20) return launch_factor_sweep<20>(g, kind, LS, L, flags, st);
-    if (w <= 24) return launch_factor_sweep<24>(g, kind, LS, L, flags, st);
-    if (w <= 28) return launch_factor_sweep<28>(g, kind, LS, L, flags, st);
-    if (w <= 32) return launch_factor_sweep<32>(g, kind, LS, L, flags, st);
-    return launch_factor_sweep<36>(g, kind, LS, L, flags, st);
+    if (w <= 16) return launch_factor_sweep<16>(g, kind, LS, L, flags, coef, st);
+    if (w <= 20) return launch_factor_sweep<20>(g, kind, LS, L, flags, coef, st);
+    if (w <= 24) return launch_factor_sweep<24>(g, kind, LS, L, flags, coef, st);
+    if (w <= 28) return launch_factor_sweep<28>(g, kind, LS, L, flags, coef, st);
+    if (w <= 32) return launch_factor_sweep<32>(g, kind, LS, L, flags, coef, st);
+    return launch_factor_sweep<36>(g, kind, LS, L, flags, coef, st);
+  }
+  if (coef) {   // the other factorisations leave the coefficients to their own kernel
+    const cudaError_t e = launch_line_coef(g, kind, coef, st);
+    if (e != cudaSuccess) return e;
   }
   if (fp32) {
     const cudaError_t e = raise_smem_limit<k_factor<float>>();
