@@ -376,6 +376,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_ASSEMBLE, st);
     CK(h, launch_assemble(g, h->bc_kind, bcp, h->has_f ? at<double>(h, L.f) : nullptr, at<double>(h, L.Tx),
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
+    CK(h, launch_gamma_coef(g, st));
   }
   // The factorisations depend only on A and are latency-bound (a barrier per column), so
   // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 and then the

@@ -140,8 +140,8 @@ struct Geo {
   const double* Ky;        // the y component (equal to K for a scalar field)
   const double* Tx;        // ny x (nx+1)
   const double* Ty;        // (ny+1) x nx
-  double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta, T_f, |f| / tau) of the Gamma faces: written by the basis
-                           // solves at set-up, read by the particular solves' moments
+  double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta, T_f, |f| / tau) of the Gamma faces: written once per
+                           // set-up (k_gamma_coef), read by the informed, basis and particular solves
 };
 
 // ------------------------------------------------------------------------------------------
@@ -241,6 +241,8 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
 // each cell's FP64 line coefficients [S][h][w][diagonal, x coupling, y coupling] of the boxes of
 // one kind; given to the FP32 informed and basis solves (coef), they refine once against them
 cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st);
+// the Robin coefficients of every Gamma face into g.gtr (after the transmissibilities)
+cudaError_t launch_gamma_coef(const Geo& g, cudaStream_t st);
 cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st,
                             const double* coef = nullptr);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,

@@ -1347,7 +1347,7 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
         int gx, gy, ox2, oy2;
         double Tf;
         gamma_face(g, s, k, t, gx, gy, ox2, oy2, Tf);
-        const double tr = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, nullptr, nullptr);
+        const double tr = g.gtr[(((size_t)s * 4 + k) * g.smax + t) * 4];
         const int x = gx - b.ox, J = gy - b.oy;
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -1591,17 +1591,11 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
         const int len = side_len(g, s, kside);
         for (int t = lane; t < len; t += 32) {
           int gx, gy, ox2, oy2;
-          double Tf, beta, tau;
+          double Tf;
           gamma_face(g, s, kside, t, gx, gy, ox2, oy2, Tf);
-          const double tr = face_tr(g, gx, gy, kside / 2, (kside & 1) ? 1 : -1, &beta, &tau);
+          const double* cf = g.gtr + (((size_t)s * 4 + kside) * g.smax + t) * 4;   // [t_R, beta, T_f, |f|/tau]
+          const double tr = cf[0], beta = cf[1];
           const double area = kside < 2 ? g.hy * g.hz : g.hx * g.hz;
-          if (a.q == 0 && r == 0) {  // kept for the particular solves' moments
-            double* cf = g.gtr + (((size_t)s * 4 + kside) * g.smax + t) * 4;
-            cf[0] = tr;
-            cf[1] = beta;
-            cf[2] = Tf;
-            cf[3] = area / tau;
-          }
           const double ph = a.in[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + kside) * g.smax + t];
           const double fl = tr * (xv(((size_t)(gy - b.oy) * w + (gx - b.ox)) * NR + r) - ph);
           const double pw = area * ph + beta * fl;
@@ -1634,15 +1628,15 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
         double ph = 0.0;
         if (rs && robin_side(g, s, r)) {
           int gx, gy, ox2, oy2;
-          double Tf, beta, tau;
+          double Tf;
           gamma_face(g, s, k, f, gx, gy, ox2, oy2, Tf);
-          face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, &beta, &tau);
+          const double* cf = g.gtr + (((size_t)s * 4 + k) * g.smax + f) * 4;   // [t_R, beta, T_f, |f|/tau]
           const double qc = xv(((size_t)(gy - b.oy) * w + (gx - b.ox)) * NR + r);
           const double qo = xv(((size_t)(oy2 - b.oy) * w + (ox2 - b.ox)) * NR + r);
           const double F = Tf * (qc - qo);
-          const double pi = qc - F / tau;
           const double area = k < 2 ? g.hy * g.hz : g.hx * g.hz;
-          ph = -beta * F / area + pi;
+          const double pi = qc - F * cf[3] / area;
+          ph = -cf[1] * F / area + pi;
         }
         a.out[((((size_t)s * 4 + r) * g.nq + a.q) * 4 + k) * g.smax + f] = ph;
       }
@@ -1824,6 +1818,33 @@ cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, co
     a.in32 = stage32;
   }
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
+}
+
+// Robin coefficients of every Gamma face of every subdomain, [S][4 sides][smax][t_R, beta, T_f,
+// |f| / tau] (Eq. 6), formed once per set-up: the basis and informed solves and the particular
+// solves' moments read them instead of evaluating the harmonic means and divisions per use
+__global__ void k_gamma_coef(Geo g) {
+  const int s = blockIdx.x;
+  for (int u = threadIdx.x; u < 4 * g.smax; u += blockDim.x) {
+    const int k = u / g.smax, t = u - k * g.smax;
+    if (!robin_side(g, s, k) || t >= side_len(g, s, k)) continue;
+    int gx, gy, ox2, oy2;
+    double Tf, beta, tau;
+    gamma_face(g, s, k, t, gx, gy, ox2, oy2, Tf);
+    const double tr = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, &beta, &tau);
+    const double area = k < 2 ? g.hy * g.hz : g.hx * g.hz;
+    double* cf = g.gtr + (((size_t)s * 4 + k) * g.smax + t) * 4;
+    cf[0] = tr;
+    cf[1] = beta;
+    cf[2] = Tf;
+    cf[3] = area / tau;
+  }
+}
+
+cudaError_t launch_gamma_coef(const Geo& g, cudaStream_t st) {
+  k_gamma_coef<<<g.mx * g.my, 128, 0, st>>>(g);
+  count_launch(1);
+  return cudaGetLastError();
 }
 
 // z = psi0 + sum over Robin sides k and degrees q of c_{s,k,q} psi_{k,q}   (reconstruction, per cell)
