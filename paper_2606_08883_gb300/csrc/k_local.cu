@@ -835,10 +835,11 @@ struct Twist {
 // to the middle goes to cb, added before the middle step.  Same arithmetic per output as the block
 // kernel's line products up to the order of the sums.  Returns false when a line block never
 // arrived (the caller reports the timeout).
-template <int W, int NR>
-__device__ __forceinline__ void warp_line_product(const float* __restrict__ S, const float* __restrict__ in, int w,
+template <int W, int NR, bool EXACT>
+__device__ __forceinline__ void warp_line_product(const float* __restrict__ S, const float* __restrict__ in, int w_rt,
                                                   int lane, float (&y)[NR], float& yc, float* part) {
   constexpr int C = W > 32 ? W - 32 : 0;
+  const int w = EXACT ? W : w_rt;   // the box width (a compile-time constant when it equals W)
   const int i = lane < w ? lane : 0;
   const int Ti = i * (i + 1) / 2;
   // the lane's row of S first, all loads issued before any product: the row-form entries
@@ -981,9 +982,10 @@ __device__ __forceinline__ int eng_count(const Twist& tw, int wid) {
   return wid == 0 ? tw.m + 1 + (tw.m - tw.lo_keep) : (tw.h - 1 - tw.m) + (tw.hi_keep - tw.m);
 }
 
-template <int W, int NR>
-__device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& base, float* Y, const float* Ec,
+template <int W, int NR, bool EXACT>
+__device__ bool twisted_engine(const Twist& tw, int w_rt, const LineSrc& src, int& base, float* Y, const float* Ec,
                                float* cb, float* xm, float* tv, float* part_all) {
+  const int w = EXACT ? W : w_rt;
   constexpr int C = W > 32 ? W - 32 : 0;
   __shared__ int s_fail;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1030,7 +1032,7 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
   if (wid == 0) {
     for (int A = 0; A < m; ++A, ++k) {
       const float* S = fetch(k);
-      warp_line_product<W, NR>(S, Y + (size_t)A * w * NR, w, lane, y, yc, part);
+      warp_line_product<W, NR, EXACT>(S, Y + (size_t)A * w * NR, w, lane, y, yc, part);
       float* dst = Y + (size_t)(A + 1) * w * NR;
       const float* e = Ec + (size_t)(A + 1) * w;
       if (xr >= 0 && xr < 32)
@@ -1042,7 +1044,7 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
   } else if (wid == 1) {
     for (int B = h - 1; B >= m + 1; --B, ++k) {
       const float* S = fetch(k);
-      warp_line_product<W, NR>(S, Y + (size_t)B * w * NR, w, lane, y, yc, part);
+      warp_line_product<W, NR, EXACT>(S, Y + (size_t)B * w * NR, w, lane, y, yc, part);
       float* dst = B - 1 == m ? cb : Y + (size_t)(B - 1) * w * NR;
       const float* e = Ec + (size_t)B * w;
       if (xr >= 0 && xr < 32)
@@ -1062,7 +1064,7 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
   // ---- middle line: x_m = S_m^-1 u_m; the first back inputs u_{m-1} + E_m x_m, u_{m+1} + E_{m+1} x_m
   if (wid == 0) {
     const float* S = fetch(k++);
-    warp_line_product<W, NR>(S, Y + (size_t)m * w * NR, w, lane, y, yc, part);
+    warp_line_product<W, NR, EXACT>(S, Y + (size_t)m * w * NR, w, lane, y, yc, part);
     const bool up = m - 1 >= tw.lo_keep, dn = m + 1 <= tw.hi_keep;
     auto emit = [&](int x, int r, float v) {
       xm[x * NR + r] = v;
@@ -1084,7 +1086,7 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
       const float* in = (t & 1) ? tA1 : tA0;
       float* nx = (t & 1) ? tA0 : tA1;
       const float* S = fetch(k);
-      warp_line_product<W, NR>(S, in, w, lane, y, yc, part);
+      warp_line_product<W, NR, EXACT>(S, in, w, lane, y, yc, part);
       const bool more = A - 1 >= tw.lo_keep;
       auto emit = [&](int x, int r, float v) {
         Y[((size_t)A * w + x) * NR + r] = v;
@@ -1102,7 +1104,7 @@ __device__ bool twisted_engine(const Twist& tw, int w, const LineSrc& src, int& 
       const float* in = (t & 1) ? tB1 : tB0;
       float* nx = (t & 1) ? tB0 : tB1;
       const float* S = fetch(k);
-      warp_line_product<W, NR>(S, in, w, lane, y, yc, part);
+      warp_line_product<W, NR, EXACT>(S, in, w, lane, y, yc, part);
       const bool more = B + 1 <= tw.hi_keep;
       auto emit = [&](int x, int r, float v) {
         Y[((size_t)B * w + x) * NR + r] = v;
@@ -1143,7 +1145,7 @@ __device__ __forceinline__ int perim_index(int x, int J, int w, int h) {
 // one mbarrier per line, issued in the order the elimination uses them) and serves both the
 // elimination and the back substitution.
 template <typename T, int MODE, int NR, int NBUF>
-__global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
+__global__ void __launch_bounds__(NBUF == ENG_NBUF ? 64 : 512, 1) k_solve(Geo g, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool RES = NBUF == 0;
   constexpr bool ENG = NBUF == ENG_NBUF;   // FP32 two-warp steps, a line ring per warp (64 threads)
@@ -1415,8 +1417,11 @@ __global__ void __launch_bounds__(512, 1) k_solve(Geo g, SolveArgs a) {
       float* cf = reinterpret_cast<float*>(cb);
       float* xf = reinterpret_cast<float*>(xm);
       float* tf = reinterpret_cast<float*>(tv);
-      const bool ok = w <= 32 ? twisted_engine<32, NR>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all)
-                              : twisted_engine<36, NR>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all);
+      // exact-width instantiations for boxes 32 and 36 wide (no per-column width tests)
+      const bool ok = w == 32   ? twisted_engine<32, NR, true>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all)
+                      : w == 36 ? twisted_engine<36, NR, true>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all)
+                      : w <= 32 ? twisted_engine<32, NR, false>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all)
+                                : twisted_engine<36, NR, false>(tw, w, src, eng_base, Yf, Ef, cf, xf, tf, part_all);
       if (!ok) {
         if (tid == 0) {
           atomicOr(a.flags, FLAG_TIMEOUT);
