@@ -957,7 +957,7 @@ __device__ __forceinline__ bool mbar_wait_parity(unsigned long long* bar, unsign
 }
 
 constexpr int ENG_NBUF = 16;   // k_solve depth code of the two-warp steps with a ring per warp
-constexpr int ENG_D = 4;       // line blocks in flight per warp
+constexpr int ENG_D = 3;       // line blocks in flight per warp
 
 // Line blocks of the two-warp steps: either resident (every block of the box in shared memory,
 // one mbarrier each, copied at the start) or streamed, each warp through its own ring of ENG_D
@@ -1029,28 +1029,31 @@ __device__ bool twisted_engine(const Twist& tw, int w_rt, const LineSrc& src, in
   int k = 0;
   // ---- elimination: warp 0 from the top (u_{A+1} += E_{A+1} S_A^-1 u_A), warp 1 from the bottom
   //      (u_{B-1} += E_B S_B^-1 u_B, into cb at the middle line)
+  // the couplings of a step's outputs are loaded before its product (they may come from global memory)
+  auto ecpl = [&](int line, int x) -> float { return x >= 0 ? Ec[(size_t)line * w + x] : 0.f; };
+  const int xr32 = (xr >= 0 && xr < 32) ? xr : -1, xcv = xc_on ? xc : -1;
   if (wid == 0) {
     for (int A = 0; A < m; ++A, ++k) {
+      const float er = ecpl(A + 1, xr32), ec = ecpl(A + 1, xcv);
       const float* S = fetch(k);
       warp_line_product<W, NR, EXACT>(S, Y + (size_t)A * w * NR, w, lane, y, yc, part);
       float* dst = Y + (size_t)(A + 1) * w * NR;
-      const float* e = Ec + (size_t)(A + 1) * w;
-      if (xr >= 0 && xr < 32)
+      if (xr32 >= 0)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) dst[xr * NR + r] += e[xr] * y[r];
-      if (xc_on) dst[xc * NR + rc] += e[xc] * yc;
+        for (int r = 0; r < NR; ++r) dst[xr32 * NR + r] += er * y[r];
+      if (xc_on) dst[xc * NR + rc] += ec * yc;
       __syncwarp();
     }
   } else if (wid == 1) {
     for (int B = h - 1; B >= m + 1; --B, ++k) {
+      const float er = ecpl(B, xr32), ec = ecpl(B, xcv);
       const float* S = fetch(k);
       warp_line_product<W, NR, EXACT>(S, Y + (size_t)B * w * NR, w, lane, y, yc, part);
       float* dst = B - 1 == m ? cb : Y + (size_t)(B - 1) * w * NR;
-      const float* e = Ec + (size_t)B * w;
-      if (xr >= 0 && xr < 32)
+      if (xr32 >= 0)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) dst[xr * NR + r] += e[xr] * y[r];
-      if (xc_on) dst[xc * NR + rc] += e[xc] * yc;
+        for (int r = 0; r < NR; ++r) dst[xr32 * NR + r] += er * y[r];
+      if (xc_on) dst[xc * NR + rc] += ec * yc;
       __syncwarp();
     }
   }
@@ -1063,18 +1066,20 @@ __device__ bool twisted_engine(const Twist& tw, int w_rt, const LineSrc& src, in
   float* tB1 = tv + 3 * w * NR;
   // ---- middle line: x_m = S_m^-1 u_m; the first back inputs u_{m-1} + E_m x_m, u_{m+1} + E_{m+1} x_m
   if (wid == 0) {
+    const float eu_r = ecpl(m, xr32), eu_c = ecpl(m, xcv);
+    const float ed_r = m + 1 < h ? ecpl(m + 1, xr32) : 0.f, ed_c = m + 1 < h ? ecpl(m + 1, xcv) : 0.f;
     const float* S = fetch(k++);
     warp_line_product<W, NR, EXACT>(S, Y + (size_t)m * w * NR, w, lane, y, yc, part);
     const bool up = m - 1 >= tw.lo_keep, dn = m + 1 <= tw.hi_keep;
-    auto emit = [&](int x, int r, float v) {
+    auto emit = [&](int x, int r, float v, float eu, float ed) {
       xm[x * NR + r] = v;
-      if (up) tA0[x * NR + r] = Y[((size_t)(m - 1) * w + x) * NR + r] + Ec[(size_t)m * w + x] * v;
-      if (dn) tB0[x * NR + r] = Y[((size_t)(m + 1) * w + x) * NR + r] + Ec[(size_t)(m + 1) * w + x] * v;
+      if (up) tA0[x * NR + r] = Y[((size_t)(m - 1) * w + x) * NR + r] + eu * v;
+      if (dn) tB0[x * NR + r] = Y[((size_t)(m + 1) * w + x) * NR + r] + ed * v;
     };
-    if (xr >= 0 && xr < 32)
+    if (xr32 >= 0)
 #pragma unroll
-      for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
-    if (xc_on) emit(xc, rc, yc);
+      for (int r = 0; r < NR; ++r) emit(xr32, r, y[r], eu_r, ed_r);
+    if (xc_on) emit(xc, rc, yc, eu_c, ed_c);
     __syncwarp();
   }
   __syncthreads();
@@ -1085,17 +1090,18 @@ __device__ bool twisted_engine(const Twist& tw, int w_rt, const LineSrc& src, in
     for (int A = m - 1; A >= tw.lo_keep; --A, ++t, ++k) {
       const float* in = (t & 1) ? tA1 : tA0;
       float* nx = (t & 1) ? tA0 : tA1;
+      const float er = ecpl(A, xr32), ec = ecpl(A, xcv);
       const float* S = fetch(k);
       warp_line_product<W, NR, EXACT>(S, in, w, lane, y, yc, part);
       const bool more = A - 1 >= tw.lo_keep;
-      auto emit = [&](int x, int r, float v) {
+      auto emit = [&](int x, int r, float v, float e) {
         Y[((size_t)A * w + x) * NR + r] = v;
-        if (more) nx[x * NR + r] = Y[((size_t)(A - 1) * w + x) * NR + r] + Ec[(size_t)A * w + x] * v;
+        if (more) nx[x * NR + r] = Y[((size_t)(A - 1) * w + x) * NR + r] + e * v;
       };
-      if (xr >= 0 && xr < 32)
+      if (xr32 >= 0)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
-      if (xc_on) emit(xc, rc, yc);
+        for (int r = 0; r < NR; ++r) emit(xr32, r, y[r], er);
+      if (xc_on) emit(xc, rc, yc, ec);
       __syncwarp();
     }
   } else if (wid == 1) {
@@ -1103,17 +1109,18 @@ __device__ bool twisted_engine(const Twist& tw, int w_rt, const LineSrc& src, in
     for (int B = m + 1; B <= tw.hi_keep; ++B, ++t, ++k) {
       const float* in = (t & 1) ? tB1 : tB0;
       float* nx = (t & 1) ? tB0 : tB1;
+      const float er = B + 1 < h ? ecpl(B + 1, xr32) : 0.f, ec = B + 1 < h ? ecpl(B + 1, xcv) : 0.f;
       const float* S = fetch(k);
       warp_line_product<W, NR, EXACT>(S, in, w, lane, y, yc, part);
       const bool more = B + 1 <= tw.hi_keep;
-      auto emit = [&](int x, int r, float v) {
+      auto emit = [&](int x, int r, float v, float e) {
         Y[((size_t)B * w + x) * NR + r] = v;
-        if (more) nx[x * NR + r] = Y[((size_t)(B + 1) * w + x) * NR + r] + Ec[(size_t)(B + 1) * w + x] * v;
+        if (more) nx[x * NR + r] = Y[((size_t)(B + 1) * w + x) * NR + r] + e * v;
       };
-      if (xr >= 0 && xr < 32)
+      if (xr32 >= 0)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) emit(xr, r, y[r]);
-      if (xc_on) emit(xc, rc, yc);
+        for (int r = 0; r < NR; ++r) emit(xr32, r, y[r], er);
+      if (xc_on) emit(xc, rc, yc, ec);
       __syncwarp();
     }
   }
@@ -1162,15 +1169,15 @@ __global__ void __launch_bounds__(NBUF == ENG_NBUF ? 64 : 512, 1) k_solve(Geo g,
   T* cb = xm + w * NR;                       // [w][NR] bottom contribution to the middle (odd h)
   T* Ec = reinterpret_cast<T*>(              // [hgt][w] line couplings (16-byte aligned, padded copy)
       smem_raw + ((reinterpret_cast<unsigned char*>(cb + w * NR) - smem_raw + 15) & ~(size_t)15));
-  const int ecn = (hgt * w + 3) & ~3;
-  unsigned long long* bars =                 // [hgt] line-block barriers (resident)
+  const int ecn = ENG ? 0 : (hgt * w + 3) & ~3;   // the ring variant reads the couplings from global memory
+  unsigned long long* bars =                 // [hgt] line-block barriers (resident), [2][ENG_D] (ring)
       reinterpret_cast<unsigned long long*>(smem_raw + ((reinterpret_cast<unsigned char*>(Ec + ecn) - smem_raw + 7) & ~(size_t)7));
   // FP32 set-up solves (informed spaces, basis) may take one step of iterative refinement (when
   // given the box's FP64 line coefficients): the first solution x0 is kept in X0, the residual
   // b - A x0 is formed in FP64 and solved again, and the outputs use x0 + delta in FP64
   const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
   T* X0 = reinterpret_cast<T*>(                // [hgt][w][NR] first solution (REF only)
-      smem_raw + ((reinterpret_cast<unsigned char*>(bars + hgt) - smem_raw + 15) & ~(size_t)15));
+      smem_raw + ((reinterpret_cast<unsigned char*>(bars + (ENG ? 2 * ENG_D : hgt)) - smem_raw + 15) & ~(size_t)15));
   float* part_all = reinterpret_cast<float*>(  // [2 warps][4][NR][32] corner-row sums (FP32 two-warp steps)
       smem_raw + ((reinterpret_cast<unsigned char*>(X0 + (REF ? (size_t)hgt * w * NR : 0)) - smem_raw + 15) &
                   ~(size_t)15));
@@ -1413,7 +1420,7 @@ __global__ void __launch_bounds__(NBUF == ENG_NBUF ? 64 : 512, 1) k_solve(Geo g,
       src.slots = reinterpret_cast<float*>(Lb);
       src.LS = LS;
       float* Yf = reinterpret_cast<float*>(Y);
-      const float* Ef = reinterpret_cast<const float*>(Ec);
+      const float* Ef = reinterpret_cast<const float*>(ENG ? Lg + (size_t)hgt * LS : Ec);
       float* cf = reinterpret_cast<float*>(cb);
       float* xf = reinterpret_cast<float*>(xm);
       float* tf = reinterpret_cast<float*>(tv);
@@ -1653,9 +1660,9 @@ template <typename T, int MODE, int NR, int NBUF>
 static size_t solve_smem(const Geo& g, const SolveArgs& a, bool ohat) {
   const int w = g.sx + (ohat ? 2 * g.l : 0), h = g.sy + (ohat ? 2 * g.l : 0);
   const size_t lines = NBUF == 0 ? (size_t)h * a.LS : NBUF == ENG_NBUF ? 2 * ENG_D * (size_t)a.LS : 2 * NBUF * (size_t)a.LS;
-  const size_t ecn = ((size_t)h * w + 3) & ~(size_t)3;
+  const size_t ecn = NBUF == ENG_NBUF ? 0 : ((size_t)h * w + 3) & ~(size_t)3;
   const bool REF = sizeof(T) == 4 && (MODE == MODE_INFORMED || MODE == MODE_BASIS) && a.coef != nullptr;
-  return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)h + 32 +
+  return sizeof(T) * (lines + (size_t)h * w * NR + 6 * (size_t)w * NR + ecn) + 8 * (size_t)(NBUF == ENG_NBUF ? 2 * ENG_D : h) + 32 +
          (REF ? sizeof(T) * (size_t)h * w * NR + 16 : 0) +
          (sizeof(T) == 4 && (NBUF == 0 || NBUF == ENG_NBUF) ? 4 * (2 * 4 * NR * 32) + 16 : 0) +
          (REF ? 4 * (2 * 4 * NR * 32) + 8 * (size_t)(2 * w + 2 * h) * NR + 32 : 0);
