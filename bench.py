@@ -370,6 +370,8 @@ def phase_model(prob, q, prec):
 NCU_TRAFFIC = {
     ("schwarz", "fp64"): (78.917888e6 + 2.628352e6, "paper_2606_08883_gb300/csrc/k_local.cu",
                           "e6ec0f82f6d373acba41e1c721e808ed7e64d4b84971029fadf4e87547beeb7d"),
+    ("schwarz", "fp32"): (559.7056e6 + 26.664704e6, "paper_2606_08883_gb300/csrc/k_local.cu",
+                          "460fe4400fee60eebdbdea7b9325c45cdd7645c6aeb6f1ba37aaf468e70b6777"),
 }
 
 
