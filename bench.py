@@ -418,7 +418,7 @@ def roofline(prof, prob, q, prec, peaks, iterations):
         achieved = nbytes / per_launch_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         return name, {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                      "traffic": None, "kernel": name, "launch_ms": per_launch_s * 1e3,
+                      "traffic": ncu_traffic(name, prec), "kernel": name, "launch_ms": per_launch_s * 1e3,
                       "algorithmic_bytes_per_launch": nbytes, "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)"}
     fp32_alu = prec == "fp32" and name.startswith("factor")
     peak = NOMINAL_FP32_TFLOPS if fp32_alu else p64
