@@ -13,11 +13,15 @@
 // then backward, x_P = F11^-1 v_P - D x_U.  Every product has a fixed order, so the solution is
 // deterministic.  A zero or non-finite pivot, or |S| above NOPIV_MAX_GROWTH max |G|, sets
 // FLAG_NOPIV_REJECTED and the caller falls back to the pivoted band LU of k_coarse.cu.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace mrcm {
 
 constexpr int MF_THREADS = 256;
+constexpr int MF_GJ_CL = 8;          // CTAs of the cluster that inverts a large pivot block
+constexpr int MF_GJ_CLUSTER_NP = 64; // pivot blocks this large (and divisible by MF_GJ_CL) use it
 
 // largest of a non-negative double across the CTA into an 8-byte maximum in global memory (the
 // bit patterns of non-negative doubles order like the values; +inf above every finite value)
@@ -97,29 +101,65 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_front(MfDev m, const double* 
   const int fid = m.order[first + blockIdx.x];
   const MfFront fr = m.fr[fid];
   const int np = fr.np, nu = fr.nu, f = np + nu;
-  double* F = m.F + fr.fo;
+  double* __restrict__ F = m.F + fr.fo;
   for (size_t t = threadIdx.x; t < (size_t)f * f; t += MF_THREADS) F[t] = 0.0;
   __syncthreads();
+  // assembly in batches of AB entries per thread, every load of a batch issued before its stores
+  // (the positions within one batch, and within one child, are distinct)
+  constexpr int AB = 8;
   double amax = 0.0;
-  for (int t = threadIdx.x; t < fr.na; t += MF_THREADS) {
-    const int2 p = m.asmv[fr.ao + t];
-    const double v = ab[p.y];
-    F[p.x] = v;
-    amax = fmax(amax, mag(v));
+  for (int t0 = threadIdx.x; t0 < fr.na; t0 += AB * MF_THREADS) {
+    int dst[AB];
+    double v[AB];
+#pragma unroll
+    for (int e = 0; e < AB; ++e) {
+      const int t = t0 + e * MF_THREADS;
+      dst[e] = -1;
+      v[e] = 0.0;
+      if (t < fr.na) {
+        const int2 p = m.asmv[fr.ao + t];
+        dst[e] = p.x;
+        v[e] = ab[p.y];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < AB; ++e)
+      if (dst[e] >= 0) {
+        F[dst[e]] = v[e];
+        amax = fmax(amax, mag(v[e]));
+      }
   }
   __syncthreads();
   for (int c = 0; c < fr.nch; ++c) {
     const MfFront cf = m.fr[c == 0 ? fr.ch[0] : fr.ch[1]];
     const int fc = cf.np + cf.nu, nuc = cf.nu;
-    const double* S = m.F + cf.fo + (size_t)cf.np * fc + cf.np;
+    const double* __restrict__ S = m.F + cf.fo + (size_t)cf.np * fc + cf.np;
     const int* mp = m.map + (c == 0 ? fr.mo[0] : fr.mo[1]);
-    for (int t = threadIdx.x; t < nuc * nuc; t += MF_THREADS) {
-      const int i = t / nuc, j = t - i * nuc;
-      F[(size_t)mp[i] * f + mp[j]] += S[(size_t)i * fc + j];
+    for (int t0 = threadIdx.x; t0 < nuc * nuc; t0 += AB * MF_THREADS) {
+      size_t dst[AB];
+      double v[AB], o[AB];
+#pragma unroll
+      for (int e = 0; e < AB; ++e) {
+        const int t = t0 + e * MF_THREADS;
+        dst[e] = ~(size_t)0;
+        v[e] = o[e] = 0.0;
+        if (t < nuc * nuc) {
+          const int i = t / nuc, j = t - i * nuc;
+          dst[e] = (size_t)mp[i] * f + mp[j];
+          v[e] = S[(size_t)i * fc + j];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < AB; ++e)
+        if (dst[e] != ~(size_t)0) o[e] = F[dst[e]];
+#pragma unroll
+      for (int e = 0; e < AB; ++e)
+        if (dst[e] != ~(size_t)0) F[dst[e]] = o[e] + v[e];
     }
     __syncthreads();
   }
   cta_max_to(amax, mf_stats(m));
+  if (np >= MF_GJ_CLUSTER_NP && np % MF_GJ_CL == 0) return;   // F11^-1 by k_mf_gj_cluster
   // Gauss-Jordan on F11 (np x np) in shared memory: pivot k takes the scaled row r_k = A_k. / a_kk
   // and the column c_k = A_.k, then a_ij -= c_i r_j off row and column k, row k = r_k, column
   // k = -c_k / a_kk, a_kk = 1 / a_kk; after the np pivots A = F11^-1
@@ -158,6 +198,69 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_front(MfDev m, const double* 
   for (int i = wid; i < np; i += MF_THREADS / 32)
     for (int j = lane; j < np; j += 32) F[(size_t)i * f + j] = A[i * np + j];
   if (bad && lane == 0) atomicOr(flags, FLAG_NOPIV_REJECTED);
+}
+
+// F11^-1 of a large pivot block by the same Gauss-Jordan steps, over a cluster of MF_GJ_CL CTAs:
+// CTA q keeps columns [q cw, (q + 1) cw) of F11 in shared memory (cw = np / MF_GJ_CL); per pivot the
+// owner of column k publishes it (double-buffered), one cluster barrier, every CTA copies it through
+// distributed shared memory and updates its columns.  Entry by entry the arithmetic is that of the
+// one-CTA form.  One cluster per front of the level; fronts too small for it return at once.
+__global__ void __launch_bounds__(MF_THREADS, 1) k_mf_gj_cluster(MfDev m, int first, int* flags) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double smd[];
+  const int q = (int)cl.block_rank();
+  const int fid = m.order[first + blockIdx.x / MF_GJ_CL];
+  const MfFront fr = m.fr[fid];
+  const int np = fr.np, f = fr.np + fr.nu;
+  if (np < MF_GJ_CLUSTER_NP || np % MF_GJ_CL != 0) return;   // uniform over the cluster
+  const int cw = np / MF_GJ_CL, c0 = q * cw;
+  double* F = m.F + fr.fo;
+  double* A = smd;                 // [np][cw] this CTA's columns
+  double* pub = A + np * cw;       // [2][np] the pivot column, published by its owner
+  double* col = pub + 2 * np;      // [np] the pivot column, copied
+  double* rk = col + np;           // [cw] this CTA's part of the scaled pivot row
+  const int tid = threadIdx.x;
+  for (int t = tid; t < np * cw; t += MF_THREADS) {
+    const int i = t / cw, jj = t - i * cw;
+    A[t] = F[(size_t)i * f + c0 + jj];
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < np; ++k) {
+    const int owner = k / cw, kk = k - owner * cw;
+    double* pb = pub + (k & 1) * np;
+    if (q == owner)
+      for (int i = tid; i < np; i += MF_THREADS) pb[i] = A[i * cw + kk];
+    cl.sync();
+    const double* rp = cl.map_shared_rank(pb, owner);
+    for (int i = tid; i < np; i += MF_THREADS) col[i] = rp[i];
+    __syncthreads();
+    double d = col[k];
+    if (!(fabs(d) > 0.0) || !isfinite(d)) {
+      bad = true;
+      d = 1.0;
+    }
+    const double r = 1.0 / d;
+    for (int jj = tid; jj < cw; jj += MF_THREADS) rk[jj] = A[k * cw + jj] * r;
+    __syncthreads();
+    for (int t = tid; t < np * cw; t += MF_THREADS) {
+      const int i = t / cw, jj = t - i * cw;
+      const int j = c0 + jj;
+      double v;
+      if (i == k) v = j == k ? r : rk[jj];
+      else if (j == k) v = -col[i] * r;
+      else v = fma(-col[i], rk[jj], A[t]);
+      A[t] = v;
+    }
+    __syncthreads();
+  }
+  cl.sync();   // no CTA leaves while another may still read its published column
+  for (int t = tid; t < np * cw; t += MF_THREADS) {
+    const int i = t / cw, jj = t - i * cw;
+    F[(size_t)i * f + c0 + jj] = A[t];
+  }
+  if (bad && tid == 0) atomicOr(flags, FLAG_NOPIV_REJECTED);
 }
 
 // Tile tasks of a level: kind 0, columns c0.. of D = F11^-1 F12 (in place of F12, from a shared
@@ -209,6 +312,32 @@ cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, in
     if (nf > 0) {
       k_mf_front<<<nf, MF_THREADS, sm_front, st>>>(m, ab, P.mf_level[L], flags);
       count_launch(1);
+      bool big = false;   // a pivot block for the cluster form
+      for (int i = P.mf_level[L]; i < P.mf_level[L + 1]; ++i) {
+        const MfFront& fr = P.mf_front[P.mf_order[i]];
+        big = big || (fr.np >= MF_GJ_CLUSTER_NP && fr.np % MF_GJ_CL == 0);
+      }
+      if (big) {
+        const size_t sm_gj = 8 * ((size_t)P.mf_max_np * (P.mf_max_np / MF_GJ_CL) + 3 * (size_t)P.mf_max_np +
+                                  P.mf_max_np / MF_GJ_CL);
+        cudaError_t e2 = cudaFuncSetAttribute(k_mf_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gj);
+        if (e2 != cudaSuccess) return e2;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = MF_GJ_CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(nf * MF_GJ_CL);
+        cfg.blockDim = dim3(MF_THREADS);
+        cfg.dynamicSmemBytes = sm_gj;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e2 = cudaLaunchKernelEx(&cfg, k_mf_gj_cluster, m, P.mf_level[L], flags);
+        if (e2 != cudaSuccess) return e2;
+        count_launch(1);
+      }
     }
     const int nb = P.mf_task_c[L] - P.mf_task_b[L];
     if (nb > 0) {
