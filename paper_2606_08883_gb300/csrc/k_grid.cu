@@ -15,15 +15,18 @@ __global__ void k_trans_x(Geo g, BcDev bc, double* Tx) {
   const int j = blockIdx.y;
   if (i > g.nx || j >= g.ny) return;
   const double area = g.hy * g.hz;
+  const double c = half_trans(1.0, area, g.hx);   // half transmissibility per unit K
   const double* K = g.K + (size_t)j * g.nx;
   double t;
   if (i == 0) {
-    t = bc.kind[0] == MRCM_BC_DIRICHLET ? half_trans(K[0], area, g.hx) : 0.0;
+    t = bc.kind[0] == MRCM_BC_DIRICHLET ? K[0] * c : 0.0;
   } else if (i == g.nx) {
-    t = bc.kind[1] == MRCM_BC_DIRICHLET ? half_trans(K[g.nx - 1], area, g.hx) : 0.0;
+    t = bc.kind[1] == MRCM_BC_DIRICHLET ? K[g.nx - 1] * c : 0.0;
   } else {
-    const double tl = half_trans(K[i - 1], area, g.hx), tr = half_trans(K[i], area, g.hx);
-    t = 1.0 / (1.0 / tl + 1.0 / tr);
+    // harmonic mean of the two half transmissibilities, (1/tl + 1/tr)^-1 = tl tr / (tl + tr): one
+    // FP64 division per face instead of five
+    const double tl = K[i - 1] * c, tr = K[i] * c;
+    t = tl * tr / (tl + tr);
   }
   Tx[(size_t)j * (g.nx + 1) + i] = t;
 }
@@ -33,15 +36,16 @@ __global__ void k_trans_y(Geo g, BcDev bc, double* Ty) {
   const int j = blockIdx.y;  // face index along y, 0..ny
   if (i >= g.nx || j > g.ny) return;
   const double area = g.hx * g.hz;
+  const double c = half_trans(1.0, area, g.hy);   // half transmissibility per unit K
   double t;
   if (j == 0) {
-    t = bc.kind[2] == MRCM_BC_DIRICHLET ? half_trans(g.Ky[i], area, g.hy) : 0.0;
+    t = bc.kind[2] == MRCM_BC_DIRICHLET ? g.Ky[i] * c : 0.0;
   } else if (j == g.ny) {
-    t = bc.kind[3] == MRCM_BC_DIRICHLET ? half_trans(g.Ky[(size_t)(g.ny - 1) * g.nx + i], area, g.hy) : 0.0;
+    t = bc.kind[3] == MRCM_BC_DIRICHLET ? g.Ky[(size_t)(g.ny - 1) * g.nx + i] * c : 0.0;
   } else {
-    const double tl = half_trans(g.Ky[(size_t)(j - 1) * g.nx + i], area, g.hy);
-    const double tr = half_trans(g.Ky[(size_t)j * g.nx + i], area, g.hy);
-    t = 1.0 / (1.0 / tl + 1.0 / tr);
+    const double tl = g.Ky[(size_t)(j - 1) * g.nx + i] * c;
+    const double tr = g.Ky[(size_t)j * g.nx + i] * c;
+    t = tl * tr / (tl + tr);   // (1/tl + 1/tr)^-1 with one division
   }
   Ty[(size_t)j * g.nx + i] = t;
 }
