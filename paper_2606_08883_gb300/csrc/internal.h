@@ -73,7 +73,7 @@ struct Plan {
   size_t mf_fbuf = 0;              // doubles of all fronts (F and B)
   size_t mf_vbuf = 0;              // doubles of the solve vectors
   int mf_max_np = 0, mf_max_f = 0;
-  int mf_mcap = 0;                 // front rows staged by the solve (doubles): the largest B or
+  int mf_mcap = 0;                 // front rows staged by the solve (doubles, padded rows): the largest B or
                                    // [F11^-1 D], capped at 24576 (192 KB)
 };
 

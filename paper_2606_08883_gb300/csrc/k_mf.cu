@@ -355,6 +355,35 @@ cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, in
   return cudaGetLastError();
 }
 
+// y_r = sum_k A[r][k] x[k] for r < rows (A row-major with leading dimension lda, in shared or global
+// memory): tpr threads per row (a power of two up to 8, as many as the CTA has for the rows), each
+// with four partial sums over its columns k = q, q + tpr, ..., then the tpr sums in a fixed shuffle
+// order; emit(r, y) by the first thread of the row.  Deterministic.
+template <class Emit>
+__device__ __forceinline__ void mf_rows(const double* A, int lda, int rows, int cols, const double* x, Emit emit) {
+  int tpr = 1;
+  while (tpr < 8 && tpr * 2 * rows <= MF_THREADS) tpr *= 2;
+  const int q = threadIdx.x % tpr, per = MF_THREADS / tpr;
+  for (int r0 = 0; r0 < rows; r0 += per) {
+    const int r = r0 + threadIdx.x / tpr;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (r < rows) {
+      const double* a = A + (size_t)r * lda;
+      int k = q;
+      for (; k + 3 * tpr < cols; k += 4 * tpr) {
+        s0 = fma(a[k], x[k], s0);
+        s1 = fma(a[k + tpr], x[k + tpr], s1);
+        s2 = fma(a[k + 2 * tpr], x[k + 2 * tpr], s2);
+        s3 = fma(a[k + 3 * tpr], x[k + 3 * tpr], s3);
+      }
+      for (; k < cols; k += tpr) s0 = fma(a[k], x[k], s0);
+    }
+    double t = (s0 + s1) + (s2 + s3);
+    for (int o = 1; o < tpr; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (r < rows && q == 0) emit(r, t);
+  }
+}
+
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
                "l"(gmem)
@@ -374,7 +403,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // that does not depend on the wait (the front's indices, its right-hand side entries, its B or
 // [F11^-1 D] rows, copied asynchronously into shared memory) is requested before the wait, so a
 // level costs about one flag hand-over and one read.  A front's rows are dotted by whole warps
-// (lanes over the columns, then a fixed shuffle tree), so the result is deterministic.
+// (up to eight threads per row, four partial sums each, combined in a fixed order), so the result
+// is deterministic.
 __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __restrict__ g, int* flags, int mcap) {
   extern __shared__ __align__(16) double smd[];
   double* v = smd;                                   // [max_f]
@@ -382,8 +412,6 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __rest
   int* ix = reinterpret_cast<int*>(M + mcap);        // [max_f]
   __shared__ unsigned s_ep;
   __shared__ int s_ok;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int NW = MF_THREADS / 32;
   volatile unsigned* vep = m.scr + 8;
   if (threadIdx.x == 0) {
     s_ep = *vep + 1u;
@@ -423,9 +451,12 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __rest
       const MfFront fr = m.fr[fid];
       const int np = fr.np, nu = fr.nu, f = np + nu;
       const double* Bx = m.F + fr.fo + (size_t)f * f;
-      const bool staged = nu * np <= mcap;
+      // B staged row by row with an odd stride in doubles (np + 1): the rows a warp reads start in
+      // different banks
+      const bool staged = nu * (np + 1) <= mcap;
       if (staged)
-        for (int t = threadIdx.x; t < nu * np; t += MF_THREADS) cp_async8(M + t, Bx + t);
+        for (int r = threadIdx.x >> 5; r < nu; r += MF_THREADS / 32)
+          for (int k = threadIdx.x & 31; k < np; k += 32) cp_async8(M + (size_t)r * (np + 1) + k, Bx + (size_t)r * np + k);
       for (int t = threadIdx.x; t < f; t += MF_THREADS) v[t] = t < np ? g[m.idx[fr.io + t]] : 0.0;
       __syncthreads();
       for (int c = 0; c < fr.nch && ok; ++c) {
@@ -443,13 +474,8 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __rest
       __syncthreads();
       double* Vf = m.V + fr.vo;
       for (int t = threadIdx.x; t < np; t += MF_THREADS) Vf[t] = v[t];
-      const double* Bs = staged ? M : Bx;
-      for (int r = wid; r < nu; r += NW) {
-        double s = 0.0;
-        for (int k = lane; k < np; k += 32) s = fma(Bs[(size_t)r * np + k], v[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) Vf[np + r] = v[np + r] - s;
-      }
+      mf_rows(staged ? M : Bx, staged ? np + 1 : np, nu, np, v,
+              [&](int r, double t) { Vf[np + r] = v[np + r] - t; });
       publish(fdone + fid);
     }
   }
@@ -461,9 +487,10 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __rest
       const int np = fr.np, nu = fr.nu, f = np + nu;
       const double* F = m.F + fr.fo;
       const double* Vf = m.V + fr.vo;
-      const bool staged = np * f <= mcap;
+      const bool staged = np * (f + 1) <= mcap;   // [F11^-1 D], rows with stride f + 1
       if (staged)
-        for (int t = threadIdx.x; t < np * f; t += MF_THREADS) cp_async8(M + t, F + t);
+        for (int r = threadIdx.x >> 5; r < np; r += MF_THREADS / 32)
+          for (int k = threadIdx.x & 31; k < f; k += 32) cp_async8(M + (size_t)r * (f + 1) + k, F + (size_t)r * f + k);
       for (int t = threadIdx.x; t < f; t += MF_THREADS) {
         ix[t] = m.idx[fr.io + t];
         if (t < np) v[t] = Vf[t];
@@ -477,13 +504,7 @@ __global__ void __launch_bounds__(MF_THREADS) k_mf_solve(MfDev m, double* __rest
       for (int t = np + threadIdx.x; t < f; t += MF_THREADS) v[t] = -__ldcg(g + ix[t]);
       cp_async_wait_all();
       __syncthreads();
-      const double* Fs = staged ? M : F;
-      for (int r = wid; r < np; r += NW) {
-        double s = 0.0;
-        for (int k = lane; k < f; k += 32) s = fma(Fs[(size_t)r * f + k], v[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g[ix[r]] = s;
-      }
+      mf_rows(staged ? M : F, staged ? f + 1 : f, np, f, v, [&](int r, double t) { g[ix[r]] = t; });
       publish(bdone + fid);
     }
   }

@@ -277,7 +277,7 @@ static bool plan_mf(Plan& P) {
     vo += fs;
     P.mf_max_np = std::max(P.mf_max_np, fr.np);
     P.mf_max_f = std::max(P.mf_max_f, fs);
-    P.mf_mcap = std::max(P.mf_mcap, std::min(24576, std::max(fr.np * fs, fr.nu * fr.np)));
+    P.mf_mcap = std::max(P.mf_mcap, std::min(24576, std::max(fr.np * (fs + 1), fr.nu * (fr.np + 1))));
   }
   if (vo > (size_t)INT32_MAX) return false;
   P.mf_fbuf = fo;
