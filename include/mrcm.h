@@ -210,6 +210,15 @@ mrcm_status mrcm_autotune_table(double* buf, size_t cap, size_t* len);
 mrcm_status mrcm_plan_export(const mrcm_problem* problem, const mrcm_params* params, int32_t* buf,
                              size_t cap, size_t* len);
 
+/* The nested-dissection plan of the multifrontal coupling factorisation (coarse_solver = 0, 2-D),
+ * computed on the host without a GPU, as a flat int32 array: header {used (0: the band LU is used),
+ * fronts, levels, 2E nq, kl, ku}; per front in elimination order {np, nu, level, children, child 0,
+ * child 1, parent}; then per front its np + nu unknowns (pivots first); then per front its count of
+ * assembled entries of G followed by their (row, column) pairs.  Writes min(cap, total) entries;
+ * *len receives the total. */
+mrcm_status mrcm_plan_mf_export(const mrcm_problem* problem, const mrcm_params* params, int32_t* buf,
+                                size_t cap, size_t* len);
+
 /* Debug / parity access to internal device arrays, copied to host (synchronises `stream`):
  *   MRCM_DBG_TRANS   face transmissibilities, x faces then y faces
  *   MRCM_DBG_PHI     informed spaces, [S][4 nq functions][4 sides][max(sub0, sub1)]

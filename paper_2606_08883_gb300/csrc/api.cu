@@ -264,6 +264,44 @@ mrcm_status mrcm_plan_export(const mrcm_problem* problem, const mrcm_params* par
   return MRCM_OK;
 }
 
+mrcm_status mrcm_plan_mf_export(const mrcm_problem* problem, const mrcm_params* params, int32_t* buf, size_t cap,
+                                size_t* len) {
+  if (!problem || !params || !len) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
+  Plan P;
+  std::string why = make_plan(*problem, *params, P);
+  if (!why.empty()) return fail(nullptr, MRCM_ERR_INVALID_ARG, why);
+  const int nf = (int)P.mf_front.size();
+  const int levels = P.mf_level.empty() ? 0 : (int)P.mf_level.size() - 1;
+  std::vector<int32_t> out = {P.mf ? 1 : 0, nf, levels, P.NC, P.kl, P.ku};
+  std::vector<int> lev(nf, 0);
+  for (int L = 0; L < levels; ++L)
+    for (int i = P.mf_level[L]; i < P.mf_level[L + 1]; ++i) lev[P.mf_order[i]] = L;
+  for (int f = 0; f < nf; ++f) {
+    const MfFront& fr = P.mf_front[f];
+    out.insert(out.end(), {fr.np, fr.nu, lev[f], fr.nch, fr.nch > 0 ? fr.ch[0] : -1, fr.nch > 1 ? fr.ch[1] : -1,
+                           fr.par});
+  }
+  for (int f = 0; f < nf; ++f) {
+    const MfFront& fr = P.mf_front[f];
+    out.insert(out.end(), P.mf_idx.begin() + fr.io, P.mf_idx.begin() + fr.io + fr.np + fr.nu);
+  }
+  // assembly pairs back to (row, column): the band offset is kl + ku + row - col + col ldab
+  const long long kv = (long long)P.kl + P.ku, ldab = 2LL * P.kl + P.ku + 1;
+  for (int f = 0; f < nf; ++f) {
+    const MfFront& fr = P.mf_front[f];
+    out.push_back(fr.na);
+    for (int t = 0; t < fr.na; ++t) {
+      const long long src = P.mf_asm[2 * (fr.ao + t) + 1];
+      const long long col = src / ldab, row = src % ldab - kv + col;
+      out.push_back((int32_t)row);
+      out.push_back((int32_t)col);
+    }
+  }
+  *len = out.size();
+  if (buf) std::memcpy(buf, out.data(), sizeof(int32_t) * std::min(cap, out.size()));
+  return MRCM_OK;
+}
+
 mrcm_status mrcm_footprint(const mrcm_problem* problem, const mrcm_params* params, size_t* bytes) {
   if (!problem || !params || !bytes) return fail(nullptr, MRCM_ERR_INVALID_ARG, "null argument");
   Plan P;

@@ -67,6 +67,7 @@ _SIGS = {
     "mrcm_status_string": ([C.c_int], C.c_char_p),
     "mrcm_last_error": ([_H], C.c_char_p),
     "mrcm_plan_export": ([_P, _Q, C.POINTER(C.c_int32), C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "mrcm_plan_mf_export": ([_P, _Q, C.POINTER(C.c_int32), C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
     "mrcm_debug_get": ([_H, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t), C.c_void_p], C.c_int),
     "mrcm_profile_enable": ([_H, C.c_int32], C.c_int),
     "mrcm_profile_select": ([_H, C.c_uint32, C.c_int32], C.c_int),
@@ -177,6 +178,34 @@ def plan_export(problem, params):
     buf = np.zeros(n.value, dtype=np.int32)
     _check(mrcm_plan_export(C.byref(p), C.byref(q), buf.ctypes.data_as(C.POINTER(C.c_int32)), n.value, C.byref(n)))
     return buf
+
+
+def plan_mf_export(problem, params):
+    """The multifrontal plan of the coupling factorisation (host only, no GPU needed): a dict with
+    'used', 'NC', 'kl', 'ku', 'fronts' (list of dicts np, nu, level, children, parent, unknowns,
+    entries as (row, column) pairs of G)."""
+    p, q = make_problem(problem), make_params(params)
+    n = C.c_size_t(0)
+    _check(mrcm_plan_mf_export(C.byref(p), C.byref(q), None, 0, C.byref(n)))
+    buf = np.zeros(n.value, dtype=np.int32)
+    _check(mrcm_plan_mf_export(C.byref(p), C.byref(q), buf.ctypes.data_as(C.POINTER(C.c_int32)), n.value,
+                               C.byref(n)))
+    used, nf, levels, NC, kl, ku = (int(v) for v in buf[:6])
+    o = 6
+    fronts = []
+    for f in range(nf):
+        np_, nu, lev, nch, c0, c1, par = (int(v) for v in buf[o:o + 7])
+        fronts.append(dict(np=np_, nu=nu, level=lev, children=[c for c in (c0, c1)[:nch]], parent=par))
+        o += 7
+    for fr in fronts:
+        k = fr["np"] + fr["nu"]
+        fr["unknowns"] = buf[o:o + k].astype(np.int64)
+        o += k
+    for fr in fronts:
+        na = int(buf[o])
+        fr["entries"] = buf[o + 1:o + 1 + 2 * na].reshape(na, 2).astype(np.int64)
+        o += 1 + 2 * na
+    return dict(used=bool(used), NC=NC, kl=kl, ku=ku, levels=levels, fronts=fronts)
 
 
 def footprint(problem, params):

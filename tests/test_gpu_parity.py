@@ -732,3 +732,47 @@ def test_multifrontal_coupling_matches_the_band_lu_and_the_oracle(mrcm, kind):
         assert _rel(z, parts["z"]) < 1e-10
         s.close()
     assert _rel(out[0][0], out[1][0]) < 1e-11
+
+
+# FP32 local solves on boxes of every kind the two-warp steps handle: exact widths 32 and 36 (the
+# 36-wide ones with the corner rows), narrower and intermediate widths (per-column width tests),
+# and 40 (the one-CTA kernels); informed spaces and basis (four right-hand sides, refined) and
+# particular solves and sweeps (one).  The preconditioner z against the FP64 oracle at the FP32
+# level, and the GMRES solution to the solver tolerance.
+@pytest.mark.parametrize("n,sub,l", [((128, 96, 1), (32, 32, 1), 2),    # boxes 36 (hat) and 32
+                                     ((120, 90, 1), (30, 30, 1), 2),    # 34 and 30
+                                     ((96, 72, 1), (24, 24, 1), 2),     # 28 and 24
+                                     ((64, 48, 1), (16, 16, 1), 2),     # 20 and 16
+                                     ((144, 108, 1), (36, 36, 1), 2)])  # 40 and 36
+def test_fp32_two_warp_line_solves_match_the_oracle(mrcm, n, sub, l):
+    prob = W.random_problem(n, seed=17, contrast=1e2)
+    q = W.Params(sub=sub, oversample=l, smooth_steps=1, tol=1e-9, restart=30, max_iter=200,
+                 local_prec=W.PREC_FP32, refine_setup=1)
+    pre = _oracle(prob, q)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    r = np.random.default_rng(19).standard_normal(prob.K.shape)
+    z = s.apply_precond(torch.as_tensor(r.ravel(), device="cuda")).cpu().numpy()
+    assert _rel(z, pre.apply_parts(r)["z"]) < 2e-5
+    p, info = s.solve()
+    assert info["status"] == 0 and info["rel_res"] <= 1e-9
+
+
+def test_multifrontal_coupling_solve_is_repeatable(mrcm):
+    # the dataflow solve (completion flags stamped with an epoch kept in device memory) gives the
+    # same bits on every application, and after a second factorisation
+    prob = W.random_problem((256, 256, 1), seed=23, contrast=1e3)
+    q = W.Params(sub=(4, 4, 1), oversample=2, smooth_steps=1, tol=1e-10, restart=30, max_iter=300)
+    s = mrcm.Solver(prob, q)
+    s.factor()
+    assert s.coarse_method() == "multifrontal"
+    r = torch.as_tensor(np.random.default_rng(31).standard_normal(prob.cells), device="cuda")
+    s.debug(mrcm.MRCM_DBG_ZMRCM, enable_only=True)
+    z1 = s.apply_precond(r).cpu().numpy()
+    c1 = s.debug(mrcm.MRCM_DBG_COARSE)
+    for _ in range(3):
+        z2 = s.apply_precond(r).cpu().numpy()
+        assert np.array_equal(z1, z2)
+    s.factor()
+    z3 = s.apply_precond(r).cpu().numpy()
+    assert np.array_equal(z1, z3) and np.array_equal(c1, s.debug(mrcm.MRCM_DBG_COARSE))
