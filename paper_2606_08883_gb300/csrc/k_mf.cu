@@ -301,9 +301,11 @@ __global__ void k_mf_check(MfDev m, int* flags) {
 cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, int* flags, cudaStream_t st) {
   const size_t sm_front = 8 * ((size_t)P.mf_max_np * P.mf_max_np + 2 * (size_t)P.mf_max_np);
   const size_t sm_tiles = 8 * (2048 + (size_t)P.mf_max_np * MF_TILE);
-  cudaError_t e = cudaFuncSetAttribute(k_mf_front, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_front);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mf_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tiles);
+  // the limits go to the device maximum once (raise_smem_limit): request workers launch these kernels
+  // from several host threads with different sizes, and a per-launch limit could be lowered by
+  // another thread between its set and its launch
+  cudaError_t e = raise_smem_limit<k_mf_front>();
+  if (e == cudaSuccess) e = raise_smem_limit<k_mf_tiles>();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(m.scr + 2, 0, 16, st);   // the statistics; the solve epoch runs on
   if (e != cudaSuccess) return e;
@@ -320,7 +322,7 @@ cudaError_t launch_mf_factor(const MfDev& m, const Plan& P, const double* ab, in
       if (big) {
         const size_t sm_gj = 8 * ((size_t)P.mf_max_np * (P.mf_max_np / MF_GJ_CL) + 3 * (size_t)P.mf_max_np +
                                   P.mf_max_np / MF_GJ_CL);
-        cudaError_t e2 = cudaFuncSetAttribute(k_mf_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_gj);
+        cudaError_t e2 = raise_smem_limit<k_mf_gj_cluster>();
         if (e2 != cudaSuccess) return e2;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -532,7 +534,7 @@ cudaError_t launch_mf_solve(const MfDev& m, const CoarseDev& c, const double* mo
   // about 192 KB (larger fronts read them from global memory)
   int mcap = m.mcap;
   const size_t sm = 12 * (size_t)m.max_f + 8 * (size_t)mcap;
-  e = cudaFuncSetAttribute(k_mf_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  e = raise_smem_limit<k_mf_solve>();
   if (e != cudaSuccess) return e;
   MfDev mm = m;
   double* g = c.g;

@@ -133,3 +133,30 @@ def test_cancel_a_running_request(mrcm):
     st = srv.stats()
     assert st["failed"] == 1 and st["completed"] == 1 and st["running"] == 0
     srv.close()
+
+
+def test_mixed_sizes_under_load_all_converge(mrcm):
+    # many requests of different sizes in flight at once: every kernel's launch limits are set once
+    # per process (workers launch the same kernels with different shared-memory sizes from several
+    # threads), so every request converges as it does alone
+    reqs = []
+    for i in range(32):
+        N = (128, 256, 512, 192)[i % 4]
+        prob, q = W.lognormal(N, seed=500 + i, variance=1.0 + (i % 5), corr=0.1, sub=32, oversample=2,
+                              smooth_steps=1, prec=W.PREC_FP32 if i % 2 else W.PREC_FP64)
+        reqs.append((prob, q))
+    srv = mrcm.Server(8 << 30, max_inflight=8)
+    tickets = [srv.submit(p, q) for p, q in reqs]
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets) and time.time() - t0 < 300:
+        for t in tickets:
+            if t not in res:
+                r = srv.poll(t)
+                if r is not None:
+                    res[t] = r
+        time.sleep(0.001)
+    srv.close()
+    assert len(res) == len(tickets)
+    assert all(r[0] == mrcm.MRCM_OK for r in res.values()), [(t, r[0]) for t, r in res.items() if r[0] != mrcm.MRCM_OK]
+    assert all(r[2]["iterations"] <= 20 for r in res.values())
