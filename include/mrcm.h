@@ -105,7 +105,9 @@ typedef struct mrcm_params {
   int32_t refine_setup;     /* with local_prec = MRCM_PREC_FP32: 1 refines the set-up solves (informed
                                spaces and basis functions) once against the FP64 box operators, which
                                brings the GMRES count to the FP64 one at the cost of a longer set-up;
-                               0 (the default) does not.  Ignored for FP64 local solves. */
+                               2 refines the basis solves only (the informed spaces' FP32 rounding
+                               moved no GMRES count on the workloads measured); 0 (the default) does
+                               not refine.  Ignored for FP64 local solves. */
   int32_t coarse_solver;    /* the coupling matrix G in 2-D: 0 (the default) factors it by nested
                                dissection of the subdomain grid (a multifrontal LU without row
                                interchanges, fronts of dense blocks; Eq. 13-14 solved exactly up to

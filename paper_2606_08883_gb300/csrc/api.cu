@@ -435,11 +435,12 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
   // oversampled factors are submitted first, since the informed spaces wait for them
   CK(h, cudaMemsetAsync(at<double>(h, L.phi), 0, 8 * (size_t)P.S * 16 * P.nq * L.smax, st));
   // FP32 set-up solves refined once against the FP64 box operators (refine_setup)
-  const bool refine = fp32 && h->prm.refine_setup != 0;
+  const bool refine = fp32 && h->prm.refine_setup != 0;           // the basis solves
+  const bool refine_inf = fp32 && h->prm.refine_setup == 1;        // and the informed spaces
   if (P.l > 0) {
     Phase ph(h, MRCM_PH_FACTOR_OHAT_ROBIN, st);
     CK(h, launch_factor(g, BOX_OHAT_ROBIN, L.wo, L.ho, L.LSo, at<void>(h, L.Linv_ohat_r), fp32, flags, st,
-                        refine ? at<double>(h, L.coef_o) : nullptr));
+                        refine_inf ? at<double>(h, L.coef_o) : nullptr));
   }
   const bool smooth = h->prm.smooth_steps > 0;
   {
@@ -457,7 +458,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     Phase ph(h, MRCM_PH_INFORMED, st);
     for (int q = 0; q < P.nq; ++q)
       CK(h, launch_informed(g, at<void>(h, L.Linv_ohat_r), L.LSo, fp32, at<double>(h, L.phi), q, at<int>(h, L.flags), st,
-                            refine ? at<double>(h, L.coef_o) : nullptr));
+                            refine_inf ? at<double>(h, L.coef_o) : nullptr));
   }
   // MRCM-OS step 3: multiscale basis functions from the local Robin factors
   CK(h, cudaStreamWaitEvent(st, h->omega_ev, 0));

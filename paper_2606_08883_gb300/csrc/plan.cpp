@@ -42,7 +42,7 @@ std::string make_plan(const mrcm_problem& p, const mrcm_params& q, Plan& P) {
     return "smooth_kind must be MRCM_SMOOTH_ADDITIVE or MRCM_SMOOTH_MULTIPLICATIVE";
   if (q.iface_degree != 0 && q.iface_degree != 1) return "iface_degree must be 0 or 1";
   if (q.coarse_pivoting != 0 && q.coarse_pivoting != 1) return "coarse_pivoting must be 0 or 1";
-  if (q.refine_setup != 0 && q.refine_setup != 1) return "refine_setup must be 0 or 1";
+  if (q.refine_setup < 0 || q.refine_setup > 2) return "refine_setup must be 0, 1 or 2";
   if (q.coarse_solver != 0 && q.coarse_solver != 1) return "coarse_solver must be 0 or 1";
   bool any_dirichlet = false;
   for (int s = 0; s < 6; ++s) {
@@ -400,7 +400,7 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   // the FP32 informed and basis solves refine once against the FP64 box operator, whose line
   // coefficients the factorisation keeps here
   const bool refine = q.local_prec == MRCM_PREC_FP32 && q.refine_setup;
-  L.coef_o = take(refine && P.l > 0 ? 8 * 3 * S * (size_t)L.wo * L.ho : 0);
+  L.coef_o = take(refine && q.refine_setup == 1 && P.l > 0 ? 8 * 3 * S * (size_t)L.wo * L.ho : 0);
   L.coef_l = take(refine ? 8 * 3 * S * (size_t)L.wl * L.hl : 0);
   L.phi = take(8 * S * 16 * nq * L.smax);
   L.psi = take(8 * 4 * nq * n);

@@ -51,7 +51,7 @@ class Params:
     smooth_kind: int = 0          # 0 additive, 1 multiplicative multicolour Schwarz sweeps
     iface_degree: int = 0         # 0 piecewise-constant, 1 piecewise-linear side functions
     coarse_pivoting: int = 0      # 0 no-pivot coupling LU with a pivoted fallback, 1 always pivoted
-    refine_setup: int = 0         # 1: FP32 set-up solves refined once against the FP64 box operators
+    refine_setup: int = 0         # FP32 set-up solves refined once against the FP64 box operators: 1 all, 2 basis only
     coarse_solver: int = 0        # 0: nested-dissection multifrontal G (large 2-D systems); 1: band LU
 
 
@@ -192,15 +192,15 @@ def channels(N=512, seed=1, sub=32, oversample=4, smooth_steps=2, prec=PREC_FP64
 
 def lognormal(N=2048, seed=1, variance=4.0, corr=0.05, sub=32, oversample=2, smooth_steps=1, prec=PREC_FP32):
     """2-D N x N log-normal field (variance 4, correlation length 0.05), p = 1 / 0 on x = 0 / 1,
-    subdomains of 32 x 32, oversampling 2, 1 smoothing step, FP32 local solves with the set-up
+    subdomains of 32 x 32, oversampling 2, 1 smoothing step, FP32 local solves with the basis
     solves refined once against the FP64 box operators (which keeps the GMRES count at the FP64
-    one)."""
+    one; refining the informed-space solves too changes no count on this field)."""
     h = (1.0 / N, 1.0 / N, 1.0)
     K = lognormal_field((N, N, 1), h, corr, variance, seed)
     prob = _flow_problem(2, (N, N, 1), h, K, f"lognormal-{N}x{N}-var{variance}-seed{seed}")
     params = Params(sub=(sub, sub, 1), oversample=oversample, smooth_steps=smooth_steps, alpha=10.0, tol=1e-8,
                     tol_relative=1, restart=30, max_iter=500, local_prec=prec,
-                    refine_setup=1 if prec == PREC_FP32 else 0)
+                    refine_setup=2 if prec == PREC_FP32 else 0)
     return prob, params
 
 

@@ -581,7 +581,8 @@ def test_full_size_lognormal_2048_matches_oracle(mrcm):
 @pytest.mark.parametrize("name,degree", [("lognormal-128", 0), ("lognormal-128", 1), ("os-96x64-l4s2", 0),
                                          ("uneven-61x45", 0), ("ragged-60x36", 1), ("column-12x96", 0)])
 def test_refined_fp32_setup_solves(mrcm, name, degree):
-    # refine_setup: the FP32 informed and basis solves take one FP64 residual and a second solve.
+    # refine_setup: the FP32 informed and basis solves (1), or the basis solves alone (2), take one
+    # FP64 residual and a second solve.
     # One step contracts the solve error by about cond(box) eps_32: on a smooth field (the
     # log-normal workloads) that is small and the side moments come much closer to the FP64 path's;
     # on the contrast-1e3 white-noise boxes it is near one and the step changes little.  On every
@@ -594,7 +595,7 @@ def test_refined_fp32_setup_solves(mrcm, name, degree):
     T = grid.transmissibilities(prob.K, prob.h, 2, prob.bc_kind)
     b = grid.rhs(prob.K, prob.h, 2, prob.bc_kind, prob.bc_val, prob.f)
     res = {}
-    for prec, ref in ((W.PREC_FP64, 0), (W.PREC_FP32, 0), (W.PREC_FP32, 1)):
+    for prec, ref in ((W.PREC_FP64, 0), (W.PREC_FP32, 0), (W.PREC_FP32, 1), (W.PREC_FP32, 2)):
         q.local_prec, q.refine_setup = prec, ref
         s = mrcm.Solver(prob, q)
         s.factor()
@@ -609,6 +610,8 @@ def test_refined_fp32_setup_solves(mrcm, name, degree):
     if name == "lognormal-128":
         assert _rel(m_ref, m64) < 0.25 * _rel(m_plain, m64), (_rel(m_ref, m64), _rel(m_plain, m64))
     assert it_ref <= it64 + 1, (it64, it_plain, it_ref)
+    # refine_setup = 2: the basis solves alone refined
+    assert res[(W.PREC_FP32, 2)][1] <= it64 + 1, (it64, res[(W.PREC_FP32, 2)][1])
 
 
 @pytest.mark.parametrize("contrast", [1e6, 1e9])
