@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual_norm(Geo g, const doub
 // v_k), plus (w, v_j) and ||A z_j||^2; one sweep for w -= V h and ||w||^2; three grid barriers.
 // Each block owns one contiguous slice of the vectors.  GB300's FP64 rate (2 DFMA/clk/SM, 64-clock
 // latency) bounds both sweeps, so the kernel is laid out to keep that pipe fed:
-//  * dot sweep: one warp per basis vector, DOT_UNROLL loads in flight per lane, both sums of a
-//    warp reduced with one exchange (half the shuffle adds);
+//  * dot sweep: every warp of the block busy at any j (each basis vector's task split over
+//    nw / (j+1) warps), DOT_UNROLL loads in flight per lane, both sums of a warp reduced with one
+//    exchange (half the shuffle adds);
 //  * update sweep: every thread streams its UPD_EL elements of UPD_UU basis vectors per stage
 //    through a UPD_DS-deep cp.async ring in shared memory (each thread reads back only its own
 //    copies, so no block barrier per stage) and keeps each element's MGS order i = 0..j;
@@ -328,6 +329,7 @@ __device__ __forceinline__ void update_ring(const double* __restrict__ V, size_t
 __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi_ls(Geo g, LsArgs a) {
   extern __shared__ double sh[];      // small arrays | ring (update) or staged rows of T
   __shared__ double sm[32];
+  __shared__ double s_dot[2 * (ARN_THREADS / 32)];
   __shared__ double s_hn, s_x;
   constexpr int nt = ARN_THREADS, nw = ARN_THREADS / 32;
   const int j = a.j, G = gridDim.x, b = blockIdx.x;
@@ -368,57 +370,74 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi_ls(Geo g, LsArgs a) 
     }
   }
   __syncthreads();
-  // 2. block partials, one warp per task: task k < j gives a_k = (w, v_k) and r_k = (v_j, v_k) from
-  //    one read of v_k; task j gives a_j = (w, v_j) and ||w||^2.  Slots: a_t at t, r_k at j+1+k,
-  //    ||w||^2 at 2j+1.
+  // 2. block partials: task k < j gives a_k = (w, v_k) and r_k = (v_j, v_k) from one read of v_k;
+  //    task j gives a_j = (w, v_j) and ||w||^2.  Slots: a_t at t, r_k at j+1+k, ||w||^2 at 2j+1.
+  //    Every warp of the block takes part whatever j is: a round of up to nw tasks gives each task
+  //    nw / (tasks in the round) warps over consecutive parts of the slice, and the parts' sums are
+  //    added in part order (deterministic).
   const int nd = 2 * j + 2;
-  // tasks in descending order: the sweep starts on the vectors the previous update read last and
-  // ends on v_0, v_1, ..., which the update below reads first (both while still in L2)
-  for (int u = warp; u <= j; u += nw) {
-    const int t = j - u;
-    double s0 = 0.0, s1 = 0.0;
-    size_t c = lo + lane;
-    if (t < j) {
-      const double* x = a.V + (size_t)t * n;
-      constexpr int U = DOT_UNROLL;
-      const size_t nfull = (hi - lo) / (32 * U);
-      for (size_t k = 0; k < nfull; ++k, c += 32 * U) {
+  for (int u0 = 0; u0 <= j; u0 += nw) {
+    const int nr = min(j + 1 - u0, nw);
+    const int wpt = nw / nr;
+    const size_t sub = (((hi - lo) + wpt - 1) / wpt + 31) & ~(size_t)31;
+    if (warp < nr * wpt) {
+      const int t = j - (u0 + warp / wpt), q = warp % wpt;
+      const size_t plo = lo + (size_t)q * sub < hi ? lo + (size_t)q * sub : hi;
+      const size_t phi = plo + sub < hi ? plo + sub : hi;
+      double s0 = 0.0, s1 = 0.0;
+      size_t c = plo + lane;
+      if (t < j) {
+        const double* x = a.V + (size_t)t * n;
+        constexpr int U = DOT_UNROLL;
+        const size_t nfull = (phi - plo) / (32 * U);
+        for (size_t k = 0; k < nfull; ++k, c += 32 * U) {
+          double xv[U], wv[U], yv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            xv[u] = __ldcg(x + c + 32 * u);
+            wv[u] = w[c + 32 * u];
+            yv[u] = vj[c + 32 * u];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            s0 += wv[u] * xv[u];
+            s1 += yv[u] * xv[u];
+          }
+        }
         double xv[U], wv[U], yv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          xv[u] = __ldcg(x + c + 32 * u);
-          wv[u] = w[c + 32 * u];
-          yv[u] = vj[c + 32 * u];
+          const bool in = c + 32 * u < phi;
+          xv[u] = in ? __ldcg(x + c + 32 * u) : 0.0;
+          wv[u] = in ? w[c + 32 * u] : 0.0;
+          yv[u] = in ? vj[c + 32 * u] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           s0 += wv[u] * xv[u];
           s1 += yv[u] * xv[u];
         }
+      } else {
+        for (; c < phi; c += 32) {
+          const double wc = w[c];
+          s0 += wc * vj[c];
+          s1 += wc * wc;
+        }
       }
-      double xv[U], wv[U], yv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool in = c + 32 * u < hi;
-        xv[u] = in ? __ldcg(x + c + 32 * u) : 0.0;
-        wv[u] = in ? w[c + 32 * u] : 0.0;
-        yv[u] = in ? vj[c + 32 * u] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        s0 += wv[u] * xv[u];
-        s1 += yv[u] * xv[u];
-      }
-    } else {
-      for (; c < hi; c += 32) {
-        const double wc = w[c];
-        s0 += wc * vj[c];
-        s1 += wc * wc;
-      }
+      const double v = warp_sum2(s0, s1, lane);
+      if (lane == 0) s_dot[2 * warp] = v;
+      if (lane == 16) s_dot[2 * warp + 1] = v;
     }
-    const double v = warp_sum2(s0, s1, lane);
-    if (lane == 0) a.part[(size_t)t * G + b] = v;
-    if (lane == 16) a.part[(size_t)(t < j ? j + 1 + t : 2 * j + 1) * G + b] = v;
+    __syncthreads();
+    if (tid < 2 * nr) {
+      const int uu = tid >> 1, which = tid & 1;
+      const int t = j - (u0 + uu);
+      double acc = 0.0;
+      for (int q = 0; q < wpt; ++q) acc += s_dot[2 * (uu * wpt + q) + which];
+      const int slot = which == 0 ? t : (t < j ? j + 1 + t : 2 * j + 1);
+      a.part[(size_t)slot * G + b] = acc;
+    }
+    __syncthreads();
   }
   __threadfence();
   if (!grid_barrier(a.bar, a.flags)) return;
