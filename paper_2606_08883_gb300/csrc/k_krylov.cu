@@ -358,9 +358,12 @@ __global__ void __launch_bounds__(ARN_THREADS, 1) k_arnoldi_ls(Geo g, LsArgs a) 
         const double zn = jj < g.ny - 1 ? z[c + g.nx] : 0.0;
         const double* Tx = g.Tx + (size_t)jj * (g.nx + 1) + i;
         const double* Ty = g.Ty + (size_t)jj * g.nx + i;
-        const double wx = Tx[1] * (zc - ze) - Tx[0] * (zw - zc);
-        const double wy = Ty[g.nx] * (zc - zn) - Ty[0] * (zs - zc);
-        r[e] = wx + wy;
+        // the four face fluxes from the differences (no cancellation against a diagonal term), one
+        // product and three FMAs
+        double f = Tx[1] * (zc - ze);
+        f = fma(Tx[0], zc - zw, f);
+        f = fma(Ty[g.nx], zc - zn, f);
+        r[e] = fma(Ty[0], zc - zs, f);
       }
     }
 #pragma unroll

@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         bad = true;
         dk = 1.f;
       }
-      const float rinv = __frcp_rn(dk);
+      const float rinv = __fdividef(1.f, dk);   // dk is near 1 after the Jacobi scaling
       const bool me = k < 32 && lane == k;
       const float gsc = me ? 1.f - rinv : a[k] * rinv;
 #pragma unroll
@@ -1792,9 +1792,11 @@ __global__ void k_stage32(Geo g, const double* __restrict__ r, const double* __r
     const double zw = gx > 0 ? z[c - 1] : 0.0, ze = gx < g.nx - 1 ? z[c + 1] : 0.0;
     const double zs = gy > 0 ? z[c - g.nx] : 0.0, zn = gy < g.ny - 1 ? z[c + g.nx] : 0.0;
     const size_t cx = (size_t)gy * (g.nx + 1) + gx;
-    const double wx = g.Tx[cx + 1] * (zc - ze) - g.Tx[cx] * (zw - zc);
-    const double wy = g.Ty[c + g.nx] * (zc - zn) - g.Ty[c] * (zs - zc);
-    v -= wx + wy;
+    // r minus the four face fluxes, each from its difference: four subtractions and four FMAs
+    v = fma(-g.Tx[cx + 1], zc - ze, v);
+    v = fma(-g.Tx[cx], zc - zw, v);
+    v = fma(-g.Ty[c + g.nx], zc - zn, v);
+    v = fma(-g.Ty[c], zc - zs, v);
   }
   out[c] = (float)v;
 }
