@@ -375,18 +375,15 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
   bool bad = false;
 
   float a[W];          // row `lane` of the working array
-  float c[C1][C1];     // corner rows / columns 32.. (W > 32), the same in every lane
+  // the corner block (rows and columns 32.., W > 32): entry (cp, cq) held by lane cp C + cq only;
+  // the corner rows' Jacobi scales are shared through sm.rv[32..]
+  const bool cown_on = C > 0 && lane < C * C;
+  const int cp = cown_on ? lane / C1 : 0, cq = cown_on ? lane - (lane / C1) * C1 : 0;
+  float cown = 0.f;
   float r_own = 1.f;   // Jacobi scale of row `lane` of the previous line
-  float rc[C1];        // Jacobi scales of the corner rows
   float ep0 = 0.f, ep1 = 0.f;   // bottom recursion: E_{J+1} of cells lane and 32 + lane
 #pragma unroll
   for (int j = 0; j < W; ++j) a[j] = 0.f;
-#pragma unroll
-  for (int p = 0; p < C1; ++p) {
-    rc[p] = 1.f;
-#pragma unroll
-    for (int q = 0; q < C1; ++q) c[p][q] = 0.f;
-  }
 
   // top lines 0..m-1 (warp 0) and bottom lines h-1..m+1 (warp 1) side by side, then the middle
   // line m on warp 0 once both recursions are done
@@ -425,11 +422,7 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
     if (lane < C) {
       sm.dv[32 + lane] = d1;
       sm.ov[32 + lane] = o1;
-      float rl = 1.f;
-#pragma unroll
-      for (int p = 0; p < C; ++p)
-        if (p == lane) rl = rc[p];
-      sm.uv[32 + lane] = has_prev ? eu1 * rl : 0.f;
+      sm.uv[32 + lane] = has_prev ? eu1 * sm.rv[32 + lane] : 0.f;   // the previous line's corner scale
       sm.vv[32 + lane] = f1;
     }
     __syncwarp();
@@ -447,16 +440,13 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         if (j == lane - 1) v -= om;
         a[j] = v;
       }
-#pragma unroll
-      for (int p = 0; p < C; ++p)
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-          float v = (sm.uv[32 + p] * sm.uv[32 + q]) * c[p][q];
-          if (p == q) v += sm.dv[32 + p];
-          if (q == p + 1) v -= sm.ov[32 + p];
-          if (q == p - 1) v -= sm.ov[32 + q];
-          c[p][q] = v;
-        }
+      if (cown_on) {
+        float v = (sm.uv[32 + cp] * sm.uv[32 + cq]) * cown;
+        if (cp == cq) v += sm.dv[32 + cp];
+        if (cq == cp + 1) v -= sm.ov[32 + cp];
+        if (cq == cp - 1) v -= sm.ov[32 + cq];
+        cown = v;
+      }
       if (dn) {   // - E_{m+1} S_{m+1}^-1 E_{m+1}, from the bottom recursion's staged last block
         const float* sx = sm_all[1].stage;
         const float vi = lane < w ? sm.vv[lane] : 0.f;
@@ -466,14 +456,10 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
             const int hi = j > lane ? j : lane, lo = j > lane ? lane : j;
             a[j] -= (vi * sm.vv[j]) * sx[hi * (hi + 1) / 2 + lo];
           }
-#pragma unroll
-        for (int p = 0; p < C; ++p)
-#pragma unroll
-          for (int q = 0; q < C; ++q)
-            if (32 + p < w && 32 + q < w) {
-              const int hi = p > q ? p : q, lo = p > q ? q : p;
-              c[p][q] -= (sm.vv[32 + p] * sm.vv[32 + q]) * sx[(32 + hi) * (33 + hi) / 2 + 32 + lo];
-            }
+        if (cown_on && 32 + cp < w && 32 + cq < w) {
+          const int hi = cp > cq ? cp : cq, lo = cp > cq ? cq : cp;
+          cown -= (sm.vv[32 + cp] * sm.vv[32 + cq]) * sx[(32 + hi) * (33 + hi) / 2 + 32 + lo];
+        }
       }
     }
     // (3) Jacobi scaling to a unit diagonal
@@ -487,23 +473,19 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         dg = 1.f;
       }
       r_own = lane < W ? rsqrtf(dg) : 1.f;
-#pragma unroll
-      for (int p = 0; p < C; ++p) {
-        float cp = c[p][p];
-        if (!(cp > 0.f && isfinite(cp))) {
-          bad = true;
-          cp = 1.f;
-        }
-        rc[p] = rsqrtf(cp);
-      }
       if (lane < W) sm.rv[lane] = r_own;
+      if (cown_on && cp == cq) {
+        float cd = cown;
+        if (!(cd > 0.f && isfinite(cd))) {
+          bad = true;
+          cd = 1.f;
+        }
+        sm.rv[32 + cp] = rsqrtf(cd);
+      }
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < W; ++j) a[j] *= r_own * (j < 32 ? sm.rv[j] : rc[j - 32]);
-#pragma unroll
-      for (int p = 0; p < C; ++p)
-#pragma unroll
-        for (int q = 0; q < C; ++q) c[p][q] *= rc[p] * rc[q];
+      for (int j = 0; j < W; ++j) a[j] *= r_own * sm.rv[j];
+      if (cown_on) cown *= sm.rv[32 + cp] * sm.rv[32 + cq];
     }
     // (4) symmetric Gauss-Jordan sweep over the W pivots
 #pragma unroll
@@ -517,21 +499,16 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         for (int q = 0; q < C; q += 4)
           *reinterpret_cast<float4*>(bk + 32 + q) = make_float4(a[32 + q], a[33 + q], a[34 + q], a[35 + q]);
       }
+      if (C > 0 && k >= 32 && cown_on && cp == k - 32) bk[32 + cq] = cown;   // corner part of row k
       __syncwarp();
-      const int nr = k < 32 ? W : R0;
       float rowk[W];
 #pragma unroll
-      for (int j = 0; j < W; j += 4)
-        if (j < nr && j < R0 + (k < 32 ? C : 0)) {
-          const float4 t = *reinterpret_cast<const float4*>(bk + j);
-          rowk[j] = t.x;
-          rowk[j + 1] = t.y;
-          rowk[j + 2] = t.z;
-          rowk[j + 3] = t.w;
-        }
-      if (k >= 32) {
-#pragma unroll
-        for (int q = 0; q < C; ++q) rowk[32 + q] = c[k - 32][q];
+      for (int j = 0; j < W; j += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(bk + j);
+        rowk[j] = t.x;
+        rowk[j + 1] = t.y;
+        rowk[j + 2] = t.z;
+        rowk[j + 3] = t.w;
       }
       float dk = rowk[k];
       if (!(dk > 0.f && isfinite(dk))) {
@@ -545,19 +522,14 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
       for (int j = 0; j < W; ++j)
         if (j != k) a[j] = fmaf(-gsc, rowk[j], a[j]);
       a[k] = me ? -rinv : gsc;
-      if (C > 0) {
-        float gk[C1];
-#pragma unroll
-        for (int p = 0; p < C; ++p) gk[p] = rowk[32 + p] * rinv;
-#pragma unroll
-        for (int p = 0; p < C; ++p)
-#pragma unroll
-          for (int q = 0; q < C; ++q) {
-            if (32 + p == k && 32 + q == k) c[p][q] = -rinv;
-            else if (32 + p == k) c[p][q] = gk[q];
-            else if (32 + q == k) c[p][q] = gk[p];
-            else c[p][q] = fmaf(-gk[p], rowk[32 + q], c[p][q]);
-          }
+      if (C > 0 && cown_on) {   // this lane's corner entry, from row k's corner part in shared memory
+        const float rp = bk[32 + cp], rq = bk[32 + cq];
+        if (k < 32) {
+          cown = fmaf(-(rp * rinv), rq, cown);
+        } else {
+          const bool pk = 32 + cp == k, qk = 32 + cq == k;
+          cown = pk && qk ? -rinv : pk ? rq * rinv : qk ? rp * rinv : fmaf(-(rp * rinv), rq, cown);
+        }
       }
     }
     // (5) S^-1 = -R a R, packed lower, through the staging array
@@ -569,15 +541,10 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
         if (j <= lane) sm.stage[base + j] = -(r_own * sm.rv[j]) * a[j];
 #pragma unroll
       for (int p = 0; p < C; ++p)   // rows 32 + p, columns lane < 32
-        if (32 + p < w) sm.stage[(32 + p) * (33 + p) / 2 + lane] = -(r_own * rc[p]) * a[32 + p];
+        if (32 + p < w) sm.stage[(32 + p) * (33 + p) / 2 + lane] = -(r_own * sm.rv[32 + p]) * a[32 + p];
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int p = 0; p < C; ++p)
-#pragma unroll
-        for (int q = 0; q <= p; ++q)
-          if (32 + p < w) sm.stage[(32 + p) * (33 + p) / 2 + 32 + q] = -(rc[p] * rc[q]) * c[p][q];
-    }
+    if (cown_on && cq <= cp && 32 + cp < w)
+      sm.stage[(32 + cp) * (33 + cp) / 2 + 32 + cq] = -(sm.rv[32 + cp] * sm.rv[32 + cq]) * cown;
     __syncwarp();
     const int npk = w * (w + 1) / 2;
     for (int t = lane; t < npk; t += 32) out[(size_t)J * LS + t] = sm.stage[t];
