@@ -125,6 +125,12 @@ Geo geo(mrcm_handle h) {
   g.Tx = at<double>(h, h->lay.Tx);
   g.Ty = at<double>(h, h->lay.Ty);
   g.gtr = at<double>(h, h->lay.gtr);
+  if (h->plan.dim == 2) {
+    g.rto = h->plan.l > 0 ? at<double>(h, h->lay.rto) : nullptr;
+    g.rtl = at<double>(h, h->lay.rtl);
+    g.rlo = std::max(h->lay.wo, h->lay.ho);
+    g.rll = std::max(h->lay.wl, h->lay.hl);
+  }
   return g;
 }
 
@@ -415,6 +421,7 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     CK(h, launch_assemble(g, h->bc_kind, bcp, h->has_f ? at<double>(h, L.f) : nullptr, at<double>(h, L.Tx),
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
     CK(h, launch_gamma_coef(g, st));
+    CK(h, launch_robin_tab(g, at<double>(h, L.rto), at<double>(h, L.rtl), st));
   }
   // The factorisations depend only on A and are latency-bound (a barrier per column), so
   // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 and then the

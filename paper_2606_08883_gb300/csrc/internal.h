@@ -93,6 +93,7 @@ struct Layout {
   size_t rdiag;                           // reciprocals of the diagonal of U
   size_t Ginv;                            // dense inverse of G (when 2E <= COARSE_DENSE_MAX)
   size_t gtr;                             // Robin coefficients of the Gamma faces, k_local.cu
+  size_t rto, rtl;                        // t_R of the Robin box faces of the oversampled / subdomain boxes
   size_t gbML, gbMU, gbX, gbY, gbF, gbC;  // blocked substitution (above COARSE_DENSE_MAX), k_coarse.cu
   size_t mf_fr, mf_ord, mf_lvl, mf_idx, mf_asm, mf_map, mf_task;   // multifrontal tables, k_mf.cu
   size_t mf_F, mf_V, mf_scr, mf_done;     // fronts, solve vectors, scratch words, completion flags
@@ -140,6 +141,9 @@ struct Geo {
   const double* Ky;        // the y component (equal to K for a scalar field)
   const double* Tx;        // ny x (nx+1)
   const double* Ty;        // (ny+1) x nx
+  const double* rto = nullptr;   // [S][4 sides][rlo] t_R of the Robin faces of the oversampled boxes (0 elsewhere)
+  const double* rtl = nullptr;   // [S][4 sides][rll] the same for the subdomain boxes; both written once per set-up
+  int rlo = 0, rll = 0;          // (k_robin_tab) and read by the factorisations and the informed solves
   double* gtr = nullptr;   // [S][4 sides][smax] x (t_R, beta, T_f, |f| / tau) of the Gamma faces: written once per
                            // set-up (k_gamma_coef), read by the informed, basis and particular solves
 };
@@ -243,6 +247,9 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
 cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st);
 // the Robin coefficients of every Gamma face into g.gtr (after the transmissibilities)
 cudaError_t launch_gamma_coef(const Geo& g, cudaStream_t st);
+// t_R of the Robin faces of every box of both kinds into the tables rto / rtl (once per set-up, before
+// any factorisation; needs K only)
+cudaError_t launch_robin_tab(const Geo& g, double* rto, double* rtl, cudaStream_t st);
 cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st,
                             const double* coef = nullptr);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,

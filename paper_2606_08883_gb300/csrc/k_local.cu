@@ -68,10 +68,21 @@ __device__ __forceinline__ double face_tr(const Geo& g, int gx, int gy, int a, i
   return robin_tr(Kc(g, a, gx, gy), Kc(g, a, nx2, ny2), area, ha, Hs, g.alpha, beta, tau);
 }
 
+// t_R table of box s's Robin faces ([4 sides][rl], k_robin_tab), or null before it exists
+__device__ __forceinline__ const double* robin_tab(const Geo& g, int s, bool ohat, int& rl) {
+  rl = ohat ? g.rlo : g.rll;
+  const double* t = ohat ? g.rto : g.rtl;
+  return t ? t + (size_t)s * 4 * rl : nullptr;
+}
+
 // Line-block coefficients at local (x, J): diagonal, coupling to x+1 (value T, entry -T),
-// coupling to line J-1 (value T, entry -T).
+// coupling to line J-1 (value T, entry -T).  The Robin faces' t_R come from the box's table rt
+// when given (the same values, formed once per set-up) instead of per call.
+// TAB_ONLY: rt is known to be present for Robin boxes (the sweep factorisation), so the per-call
+// form is left out.
+template <bool TAB_ONLY = false>
 __device__ __forceinline__ void line_coeffs(const Geo& g, const Box& b, bool robin, int J, int x, double& diag,
-                                            double& offr, double& eup) {
+                                            double& offr, double& eup, const double* rt = nullptr, int rl = 0) {
   const int gx = b.ox + x, gy = b.oy + J;
   if (!active(g, gx, gy)) {
     diag = 1.0;
@@ -83,7 +94,12 @@ __device__ __forceinline__ void line_coeffs(const Geo& g, const Box& b, bool rob
   const double tw = Tx[gx], te = Tx[gx + 1];
   const double ts = g.Ty[(size_t)gy * g.nx + gx], tn = g.Ty[(size_t)(gy + 1) * g.nx + gx];
   double d = (tw + te) + (ts + tn);
-  if (robin) {
+  if (robin && rt) {
+    if (x == 0 && gx - 1 >= 0) d += rt[J] - tw;
+    if (x == b.w - 1 && gx + 1 < g.nx) d += rt[rl + J] - te;
+    if (J == 0 && gy - 1 >= 0) d += rt[2 * rl + x] - ts;
+    if (J == b.h - 1 && gy + 1 < g.ny) d += rt[3 * rl + x] - tn;
+  } else if (!TAB_ONLY && robin) {
     if (x == 0 && gx - 1 >= 0) d += face_tr(g, gx, gy, 0, -1, nullptr, nullptr) - tw;
     if (x == b.w - 1 && gx + 1 < g.nx) d += face_tr(g, gx, gy, 0, +1, nullptr, nullptr) - te;
     if (J == 0 && gy - 1 >= 0) d += face_tr(g, gx, gy, 1, -1, nullptr, nullptr) - ts;
@@ -133,6 +149,8 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
   const bool ohat = kind != BOX_OMEGA_ROBIN;
   const bool robin = kind != BOX_OHAT_DIRICHLET;
   const Box b = box_of(g, s, ohat);
+  int rl;
+  const double* rt = robin_tab(g, s, ohat, rl);
   const int w = b.w, h = b.h, m = h / 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nth = nt / nch, half = tid / nth, tidh = tid - half * nth;
@@ -177,7 +195,7 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
     if (active)
       for (int i = tidh; i < w; i += nth) {
         double d, o, e;
-        line_coeffs(g, b, robin, J, i, d, o, e);
+        line_coeffs(g, b, robin, J, i, d, o, e, rt, rl);
         ec_out[(size_t)J * w + i] = (T)e;
         Sm[i * w + i] = (T)d;
         if (i + 1 < w) Sm[(i + 1) * w + i] = (T)(-o);
@@ -185,12 +203,12 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, int kind, int LS, T* __re
           ev[i] = (T)e;
         } else if (bottom) {
           double d2, o2, e2;
-          line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+          line_coeffs(g, b, robin, J + 1, i, d2, o2, e2, rt, rl);
           ev[i] = (T)e2;
         } else {
           ev[i] = (T)e;                      // E_m (towards line m-1)
           double d2, o2, e2 = 0.0;
-          if (J + 1 < h) line_coeffs(g, b, robin, J + 1, i, d2, o2, e2);
+          if (J + 1 < h) line_coeffs(g, b, robin, J + 1, i, d2, o2, e2, rt, rl);
           ev2[i] = (T)e2;                    // E_{m+1} (towards line m+1)
         }
       }
@@ -336,7 +354,7 @@ struct SweepSmem {
 // coefficients of cell x of line J as floats (identity rows past the box width); with cf, also
 // stored there in FP64 [d, o, e] (the refinement of the FP32 set-up solves reads them)
 __device__ __forceinline__ void line_coeffs_f(const Geo& g, const Box& b, bool robin, int J, int x, float& d, float& o,
-                                              float& e, double* cf = nullptr) {
+                                              float& e, double* cf, const double* rt, int rl) {
   if (x >= b.w) {
     d = 1.f;
     o = 0.f;
@@ -344,7 +362,7 @@ __device__ __forceinline__ void line_coeffs_f(const Geo& g, const Box& b, bool r
     return;
   }
   double dd, oo, ee;
-  line_coeffs(g, b, robin, J, x, dd, oo, ee);
+  line_coeffs<true>(g, b, robin, J, x, dd, oo, ee, rt, rl);
   d = (float)dd;
   o = (float)oo;
   e = (float)ee;
@@ -367,6 +385,8 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
   const bool ohat = kind != BOX_OMEGA_ROBIN;
   const bool robin = kind != BOX_OHAT_DIRICHLET;
   const Box b = box_of(g, s, ohat);
+  int rl;
+  const double* rt = robin_tab(g, s, ohat, rl);
   const int w = b.w, h = b.h, m = h / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   SweepSmem<W>& sm = sm_all[wid];
@@ -400,8 +420,8 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
     // (1) line data: diagonal, right coupling, u_x = E_x r_x towards the previous line
     float d0, o0, e0, d1 = 1.f, o1 = 0.f, e1 = 0.f;
     double* cfl = coef ? coef + (((size_t)s * h + J) * w) * 3 : nullptr;   // this line's FP64 coefficients
-    line_coeffs_f(g, b, robin, J, lane, d0, o0, e0, cfl ? cfl + 3 * lane : nullptr);
-    if (lane < C) line_coeffs_f(g, b, robin, J, 32 + lane, d1, o1, e1, cfl ? cfl + 3 * (32 + lane) : nullptr);
+    line_coeffs_f(g, b, robin, J, lane, d0, o0, e0, cfl ? cfl + 3 * lane : nullptr, rt, rl);
+    if (lane < C) line_coeffs_f(g, b, robin, J, 32 + lane, d1, o1, e1, cfl ? cfl + 3 * (32 + lane) : nullptr, rt, rl);
     if (lane < w) ec_out[(size_t)J * w + lane] = e0;
     if (lane < C && 32 + lane < w) ec_out[(size_t)J * w + 32 + lane] = e1;
     const float eu0 = (top || mid) ? e0 : ep0, eu1 = (top || mid) ? e1 : ep1;
@@ -410,8 +430,8 @@ __global__ void __launch_bounds__(64) k_factor_sweep(Geo g, int kind, int LS, fl
     float f0 = 0.f, f1 = 0.f;
     if (dn) {
       float d_, o_;
-      line_coeffs_f(g, b, robin, m + 1, lane, d_, o_, f0);
-      if (lane < C) line_coeffs_f(g, b, robin, m + 1, 32 + lane, d_, o_, f1);
+      line_coeffs_f(g, b, robin, m + 1, lane, d_, o_, f0, nullptr, rt, rl);
+      if (lane < C) line_coeffs_f(g, b, robin, m + 1, 32 + lane, d_, o_, f1, nullptr, rt, rl);
     }
     if (lane < W) {
       sm.dv[lane] = d0;
@@ -568,10 +588,12 @@ __global__ void k_line_coef(Geo g, int kind, double* __restrict__ coef) {
   const bool ohat = kind != BOX_OMEGA_ROBIN;
   const bool robin = kind != BOX_OHAT_DIRICHLET;
   const Box b = box_of(g, s, ohat);
+  int rl;
+  const double* rt = robin_tab(g, s, ohat, rl);
   for (int c = threadIdx.x; c < b.w * b.h; c += blockDim.x) {
     const int J = c / b.w, x = c - J * b.w;
     double d, o, e;
-    line_coeffs(g, b, robin, J, x, d, o, e);
+    line_coeffs(g, b, robin, J, x, d, o, e, rt, rl);
     double* cf = coef + ((size_t)s * b.w * b.h + c) * 3;
     cf[0] = d;
     cf[1] = o;
@@ -598,6 +620,8 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
   const int nch = factor_smem_bytes(w, fp32, 2) <= 112 * 1024 ? 2 : 1;
   const size_t sm = factor_smem_bytes(w, fp32, nch);
   if (fp32 && w <= 36) {   // register-resident sweep, box width padded to a multiple of 4
+    // it reads the Robin faces' t_R from the box tables only (k_robin_tab, formed with the assembly)
+    if ((kind == BOX_OHAT_ROBIN && !g.rto) || (kind == BOX_OMEGA_ROBIN && !g.rtl)) return cudaErrorInvalidValue;
     float* L = (float*)Linv;
     if (w <= 16) return launch_factor_sweep<16>(g, kind, LS, L, flags, coef, st);
     if (w <= 20) return launch_factor_sweep<20>(g, kind, LS, L, flags, coef, st);
@@ -1290,6 +1314,8 @@ __global__ void __launch_bounds__(NBUF == ENG_NBUF ? 64 : 512, 1) k_solve(Geo g,
     }
   } else if (MODE == MODE_INFORMED) {
     // lambda^r = 1 on the faces of Robin side r of the oversampled box
+    int rl_inf;
+    const double* rt_inf = robin_tab(g, s, true, rl_inf);
     for (int r = 0; r < 4; ++r) {
       if (!robin_side(g, s, r)) continue;
       const int len = (r < 2) ? hgt : w;
@@ -1309,7 +1335,7 @@ __global__ void __launch_bounds__(NBUF == ENG_NBUF ? 64 : 512, 1) k_solve(Geo g,
           const int hi = ax == 0 ? min(b.oy + hgt, g.ny) : min(b.ox + w, g.nx);
           lam = side_fn(a.q, (ax == 0 ? gy : gx) - lo, hi - lo);
         }
-        const double bv = face_tr(g, gx, gy, ax, dir, nullptr, nullptr) * lam;
+        const double bv = (rt_inf ? rt_inf[r * rl_inf + t] : face_tr(g, gx, gy, ax, dir, nullptr, nullptr)) * lam;
         Y[(J * w + x) * NR + r] += (T)bv;
         if (REF) bE[perim_index(x, J, w, hgt) * NR + r] += bv;
       }
@@ -1824,6 +1850,39 @@ __global__ void k_gamma_coef(Geo g) {
 
 cudaError_t launch_gamma_coef(const Geo& g, cudaStream_t st) {
   k_gamma_coef<<<g.mx * g.my, 128, 0, st>>>(g);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// t_R (Eq. 6) of the Robin faces of each box, [S][4 sides][len] by the box's local position along
+// the side (y for the x sides, x for the y sides): the faces from an in-grid cell on the box's
+// outer row or column to an in-grid neighbour outside the box; 0 elsewhere.  Formed once per
+// set-up, so the factorisations (a line per step, the Robin faces on its critical path) and the
+// informed solves read the harmonic means and divisions instead of evaluating them.
+__global__ void k_robin_tab(Geo g, int ohat, double* __restrict__ out, int len) {
+  const int s = blockIdx.x;
+  const Box b = box_of(g, s, ohat != 0);
+  for (int u = threadIdx.x; u < 4 * len; u += blockDim.x) {
+    const int k = u / len, t = u - k * len;
+    const int x = k == 0 ? 0 : k == 1 ? b.w - 1 : t;
+    const int J = k < 2 ? t : k == 2 ? 0 : b.h - 1;
+    const bool on_side = k < 2 ? t < b.h : t < b.w;
+    const int gx = b.ox + x, gy = b.oy + J;
+    const int nx2 = gx + (k == 0 ? -1 : k == 1 ? 1 : 0), ny2 = gy + (k == 2 ? -1 : k == 3 ? 1 : 0);
+    double v = 0.0;
+    if (on_side && active(g, gx, gy) && active(g, nx2, ny2))
+      v = face_tr(g, gx, gy, k / 2, (k & 1) ? 1 : -1, nullptr, nullptr);
+    out[((size_t)s * 4 + k) * len + t] = v;
+  }
+}
+
+cudaError_t launch_robin_tab(const Geo& g, double* rto, double* rtl, cudaStream_t st) {
+  const int S = g.mx * g.my;
+  if (rto) {
+    k_robin_tab<<<S, 128, 0, st>>>(g, 1, rto, g.rlo);
+    count_launch(1);
+  }
+  k_robin_tab<<<S, 128, 0, st>>>(g, 0, rtl, g.rll);
   count_launch(1);
   return cudaGetLastError();
 }

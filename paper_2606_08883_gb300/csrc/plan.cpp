@@ -409,6 +409,8 @@ Layout make_layout(const Plan& P, const mrcm_params& q) {
   L.z0 = take(8 * n);
   L.mom0 = take(8 * S * 8 * nq);
   L.gtr = take(8 * S * 4 * L.smax * 4);
+  L.rto = take(P.l > 0 ? 8 * S * 4 * std::max(L.wo, L.ho) : 0);
+  L.rtl = take(8 * S * 4 * std::max(L.wl, L.hl));
   L.G = take(8 * (size_t)L.ldab * NC);
   L.ipiv = take(4 * NC);
   L.gc = take(8 * NC);
