@@ -375,6 +375,25 @@ NCU_TRAFFIC = {
 }
 
 
+# The Arnoldi step's traffic grows with the inner step j: (bytes, j) of the captured launch, scaled
+# to the solve's average launch by the model's algorithmic bytes (krylov_model), in which the basis
+# sweeps that make the traffic grow in proportion.
+NCU_TRAFFIC_KRYLOV = (576.713984e6 + 62.34112e6, 5, "paper_2606_08883_gb300/csrc/k_krylov.cu",
+                      "97bf265e4b30d16c4335a8ef6753b412892351f7adbec2e54e23ce2f20898f0f")
+
+
+def krylov_traffic(n, iterations, restart):
+    nbytes, jcap, src, sha = NCU_TRAFFIC_KRYLOV
+    try:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    at_cap = (2 * (jcap + 1) + 4) * 8 * n
+    return nbytes * krylov_model(n, iterations, restart)[1] / at_cap
+
+
 def ncu_traffic(name, prec):
     entry = NCU_TRAFFIC.get((name, prec))
     if entry is None:
@@ -411,7 +430,8 @@ def roofline(prof, prob, q, prec, peaks, iterations):
     if name == "krylov":
         achieved = flops / per_launch_s / 1e12
         return name, {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
-                      "frac": achieved / p64, "traffic": None, "kernel": "k_arnoldi_ls",
+                      "frac": achieved / p64, "traffic": krylov_traffic(prob.cells, iterations, q.restart),
+                      "kernel": "k_arnoldi_ls",
                       "launch_ms": per_launch_s * 1e3, "algorithmic_flops_per_launch": flops,
                       "algorithmic_bytes_per_launch": nbytes, "peak_source": p64_src}
     if name in ("residual", "reconstruct") or (prec == "fp32" and name in ("schwarz", "particular")):

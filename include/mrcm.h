@@ -245,7 +245,10 @@ mrcm_status mrcm_debug_get(mrcm_handle h, int32_t what, double* host_out, size_t
 enum { MRCM_PH_ASSEMBLE = 0, MRCM_PH_FACTOR_OHAT_ROBIN = 1, MRCM_PH_INFORMED = 2, MRCM_PH_FACTOR_OMEGA = 3,
        MRCM_PH_BASIS = 4, MRCM_PH_COARSE_FACTOR = 5, MRCM_PH_FACTOR_OHAT_DIRICHLET = 6,
        MRCM_PH_PARTICULAR = 7, MRCM_PH_COARSE_SOLVE = 8, MRCM_PH_RECONSTRUCT = 9, MRCM_PH_RESIDUAL = 10,
-       MRCM_PH_SCHWARZ = 11, MRCM_PH_KRYLOV = 12, MRCM_PHASES = 13 };
+       MRCM_PH_SCHWARZ = 11, MRCM_PH_KRYLOV = 12, MRCM_PH_STAGE = 13, MRCM_PHASES = 14 };
+/* MRCM_PH_STAGE: with FP32 local solves, the FP32 right-hand sides of the particular solves and of
+ * the additive sweeps formed on the grid (the sweep's FP64 residual r - A z rounded once), each
+ * before the solve launch it feeds; MRCM_PH_PARTICULAR and MRCM_PH_SCHWARZ time the solves alone. */
 mrcm_status mrcm_profile_enable(mrcm_handle h, int32_t enable);
 /* Restricts the recording to the phases whose bit (1 << MRCM_PH_*) is set in phase_mask, and to
  * every `every`-th occurrence of each (counted per phase from this call; every >= 1).  After

@@ -31,7 +31,7 @@ namespace {
 const char* const kPhaseName[MRCM_PHASES] = {
     "mrcm assemble", "mrcm factor ohat robin", "mrcm informed spaces", "mrcm factor omega", "mrcm basis",
     "mrcm coupling factor", "mrcm factor ohat dirichlet", "mrcm particular", "mrcm coupling solve",
-    "mrcm reconstruct", "mrcm residual", "mrcm schwarz", "mrcm krylov"};
+    "mrcm reconstruct", "mrcm residual", "mrcm schwarz", "mrcm krylov", "mrcm stage fp32 rhs"};
 
 // Phase brackets: an NVTX range always, and a (start, stop) event pair per kernel group while
 // profiling is enabled.
@@ -421,7 +421,10 @@ mrcm_status mrcm_factor_local(mrcm_handle h, void* stream) {
     CK(h, launch_assemble(g, h->bc_kind, bcp, h->has_f ? at<double>(h, L.f) : nullptr, at<double>(h, L.Tx),
                           at<double>(h, L.Ty), at<double>(h, L.b), st));
     CK(h, launch_gamma_coef(g, st));
-    CK(h, launch_robin_tab(g, at<double>(h, L.rto), at<double>(h, L.rtl), st));
+    // both tables before the fork: a table launch queued on the second stream waits behind the
+    // oversampled factor's CTAs and delays the subdomain factor
+    if (P.l > 0) CK(h, launch_robin_tab(g, true, at<double>(h, L.rto), st));
+    CK(h, launch_robin_tab(g, false, at<double>(h, L.rtl), st));
   }
   // The factorisations depend only on A and are latency-bound (a barrier per column), so
   // independent ones share the SMs: the local Robin factors of MRCM-OS step 3 and then the
@@ -551,14 +554,18 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   const bool fp32 = h->prm.local_prec == MRCM_PREC_FP32;
   Geo g = geo(h);
   // particular solutions and their side moments
+  float* rho32 = fp32 ? at<float>(h, L.rho) : nullptr;   // FP32 right-hand sides, formed on the grid
+  if (fp32) {
+    Phase ph(h, MRCM_PH_STAGE, st);
+    CK(h, launch_stage32(g, r, nullptr, rho32, st));
+  }
   {
     Phase ph(h, MRCM_PH_PARTICULAR, st);
     // on the extended regions' Robin factors when l > 0 (the source term's basis function is built
     // there), on the subdomains' own Robin factors when l = 0
     const bool ext = P.l > 0;
     CK(h, launch_particular(g, at<void>(h, ext ? L.Linv_ohat_r : L.Linv_loc), ext ? L.LSo : L.LSl, fp32, r,
-                            at<double>(h, L.psi0), at<double>(h, L.mom0), at<int>(h, L.flags), st,
-                            at<float>(h, L.rho)));
+                            at<double>(h, L.psi0), at<double>(h, L.mom0), at<int>(h, L.flags), st, rho32));
   }
   // coupling system
   CoarseDev c = coarse(h);
@@ -587,15 +594,20 @@ static mrcm_status apply_T(mrcm_handle h, const double* r, double* z, cudaStream
   // smoothing sweeps (residual fused into the local solve): additive, all boxes from one residual
   // (ping-pong buffers); or multiplicative multicolour, one launch per colour updating z in place
   for (int it = 0; it < s; ++it) {
-    Phase ph(h, MRCM_PH_SCHWARZ, st);
     if (mult) {
+      Phase ph(h, MRCM_PH_SCHWARZ, st);
       for (int colour = 0; colour < (1 << P.dim); ++colour)
         CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, z, z, at<int>(h, L.flags), colour, st));
     } else {
       const double* zin = zb[(s - it) & 1];
       double* zout = zb[(s - it - 1) & 1];
+      if (fp32) {   // additive: every box from the same residual, r - A z formed once on the grid
+        Phase ph(h, MRCM_PH_STAGE, st);
+        CK(h, launch_stage32(g, r, zin, rho32, st));
+      }
+      Phase ph(h, MRCM_PH_SCHWARZ, st);
       CK(h, launch_schwarz(g, at<void>(h, L.Linv_ohat_d), L.LSo, fp32, r, zin, zout, at<int>(h, L.flags), -1, st,
-                           at<float>(h, L.rho)));
+                           rho32));
     }
   }
   return MRCM_OK;

@@ -247,18 +247,22 @@ cudaError_t launch_factor(const Geo& g, int kind, int w, int hgt, int LS, void* 
 cudaError_t launch_line_coef(const Geo& g, int kind, double* coef, cudaStream_t st);
 // the Robin coefficients of every Gamma face into g.gtr (after the transmissibilities)
 cudaError_t launch_gamma_coef(const Geo& g, cudaStream_t st);
-// t_R of the Robin faces of every box of both kinds into the tables rto / rtl (once per set-up, before
-// any factorisation; needs K only)
-cudaError_t launch_robin_tab(const Geo& g, double* rto, double* rtl, cudaStream_t st);
+// t_R of the Robin faces of every oversampled (ohat) or subdomain box into its table, g.rto or g.rtl
+// (once per set-up, before the factorisation of that kind; needs K only)
+cudaError_t launch_robin_tab(const Geo& g, bool ohat, double* out, cudaStream_t st);
 cudaError_t launch_informed(const Geo& g, const void* Linv, int LS, bool fp32, double* phi, int q, int* flags, cudaStream_t st,
                             const double* coef = nullptr);
 cudaError_t launch_basis(const Geo& g, const void* Linv, int LS, bool fp32, const double* phi, int q, double* psi,
                          double* mom, int* flags, cudaStream_t st, const double* coef = nullptr);
-// stage32 (FP32 solves, optional): n floats of scratch for the right-hand side formed once on the grid
+// FP32 right-hand sides formed once on the grid for the FP32 particular solves (z == nullptr: r) and
+// additive sweeps (the residual r - A z in FP64, rounded once): n floats into out
+cudaError_t launch_stage32(const Geo& g, const double* r, const double* z, float* out, cudaStream_t st);
+// in32 (FP32 solves, optional): the right-hand side staged by launch_stage32 for this launch (the
+// particular solve's r, or the additive sweep's residual for the same zin); null: formed per box
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, int* flags, cudaStream_t st, float* stage32 = nullptr);
+                              double* mom0, int* flags, cudaStream_t st, const float* in32 = nullptr);
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, int colour, cudaStream_t st, float* stage32 = nullptr);
+                           double* zout, int* flags, int colour, cudaStream_t st, const float* in32 = nullptr);
 cudaError_t launch_reconstruct(const Geo& g, const double* psi0, const double* psi, const int* coff,
                                const double* c, double* z, cudaStream_t st);
 size_t factor_smem_bytes(int w, bool fp32, int nch);

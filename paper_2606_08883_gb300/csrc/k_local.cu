@@ -1794,7 +1794,7 @@ __global__ void k_stage32(Geo g, const double* __restrict__ r, const double* __r
   out[c] = (float)v;
 }
 
-static cudaError_t launch_stage32(const Geo& g, const double* r, const double* z, float* out, cudaStream_t st) {
+cudaError_t launch_stage32(const Geo& g, const double* r, const double* z, float* out, cudaStream_t st) {
   dim3 grid((g.nx + 255) / 256, g.ny);
   k_stage32<<<grid, 256, 0, st>>>(g, r, z, out);
   count_launch(1);
@@ -1802,13 +1802,9 @@ static cudaError_t launch_stage32(const Geo& g, const double* r, const double* z
 }
 
 cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, double* psi0,
-                              double* mom0, int* flags, cudaStream_t st, float* stage32) {
+                              double* mom0, int* flags, cudaStream_t st, const float* in32) {
   SolveArgs a{Linv, LS, r, psi0, mom0, nullptr, flags, -1};
-  if (fp32 && stage32) {
-    const cudaError_t e = launch_stage32(g, r, nullptr, stage32, st);
-    if (e != cudaSuccess) return e;
-    a.in32 = stage32;
-  }
+  if (fp32 && in32) a.in32 = in32;
   return launch_solve<MODE_PARTICULAR, 1>(g, a, g.l > 0, fp32, st);
 }
 
@@ -1817,13 +1813,9 @@ cudaError_t launch_particular(const Geo& g, const void* Linv, int LS, bool fp32,
 // is narrower than a subdomain, so no box reads (region plus the stencil's one-cell rim) a cell
 // that another box of its colour writes.
 cudaError_t launch_schwarz(const Geo& g, const void* Linv, int LS, bool fp32, const double* r, const double* zin,
-                           double* zout, int* flags, int colour, cudaStream_t st, float* stage32) {
+                           double* zout, int* flags, int colour, cudaStream_t st, const float* in32) {
   SolveArgs a{Linv, LS, r, zout, nullptr, zin, flags, colour};
-  if (fp32 && stage32 && colour < 0) {   // additive: every box from the same residual
-    const cudaError_t e = launch_stage32(g, r, zin, stage32, st);
-    if (e != cudaSuccess) return e;
-    a.in32 = stage32;
-  }
+  if (fp32 && in32 && colour < 0) a.in32 = in32;   // additive: every box from the same staged residual
   return launch_solve<MODE_SCHWARZ, 1>(g, a, true, fp32, st);
 }
 
@@ -1876,13 +1868,8 @@ __global__ void k_robin_tab(Geo g, int ohat, double* __restrict__ out, int len) 
   }
 }
 
-cudaError_t launch_robin_tab(const Geo& g, double* rto, double* rtl, cudaStream_t st) {
-  const int S = g.mx * g.my;
-  if (rto) {
-    k_robin_tab<<<S, 128, 0, st>>>(g, 1, rto, g.rlo);
-    count_launch(1);
-  }
-  k_robin_tab<<<S, 128, 0, st>>>(g, 0, rtl, g.rll);
+cudaError_t launch_robin_tab(const Geo& g, bool ohat, double* out, cudaStream_t st) {
+  k_robin_tab<<<g.mx * g.my, 128, 0, st>>>(g, ohat ? 1 : 0, out, ohat ? g.rlo : g.rll);
   count_launch(1);
   return cudaGetLastError();
 }

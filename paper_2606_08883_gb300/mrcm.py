@@ -87,7 +87,7 @@ _SIGS = {
     "mrcm_autotune_table": ([C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
 }
 PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
-          "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
+          "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov", "stage")
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.argtypes = _args

@@ -14,7 +14,7 @@ import bench  # noqa: E402
 from paper_2606_08883_gb300 import workloads as W  # noqa: E402
 
 PHASES = ("assemble", "factor_ohat_robin", "informed", "factor_omega", "basis", "coarse_factor",
-          "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov")
+          "factor_ohat_dirichlet", "particular", "coarse_solve", "reconstruct", "residual", "schwarz", "krylov", "stage")
 
 
 def _case():
