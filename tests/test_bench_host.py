@@ -104,3 +104,30 @@ def test_particular_solve_modelled_on_the_extended_box():
     S = (prob.n[0] // q.sub[0]) * (prob.n[1] // q.sub[1])
     products = (w - 1) + 1 + (w // 2 - (q.oversample - 1)) + (w - 1 - (q.oversample - 1) - w // 2)
     assert m["particular"][0] == S * products * 2 * w * w
+
+
+def test_krylov_roofline_traffic_scaled_from_the_captured_step(monkeypatch):
+    """The Arnoldi step's ncu traffic was taken at one inner step j; the line reports it scaled to
+    the solve's average step by the model's algorithmic bytes, and drops it (None) once the
+    kernel's source file no longer matches the capture."""
+    prob, q = _case()
+    n, iters = prob.cells, 10
+    nbytes, jcap = bench.NCU_TRAFFIC_KRYLOV[0], bench.NCU_TRAFFIC_KRYLOV[1]
+    want = nbytes * bench.krylov_model(n, iters, q.restart)[1] / ((2 * (jcap + 1) + 4) * 8 * n)
+    assert bench.krylov_traffic(n, iters, q.restart) == pytest.approx(want)
+    # a solve of jcap + 1 steps (j = 0..jcap) averages below the captured step, so its traffic is smaller
+    assert bench.krylov_traffic(n, jcap + 1, q.restart) < nbytes * 1.0001
+    name, roof = bench.roofline(_prof(krylov=(2.0, 10)), prob, q, "fp64", {"hbm_gbs": 6680.0}, iters)
+    assert name == "krylov" and roof["kernel"] == "k_arnoldi_ls"
+    assert roof["traffic"] == pytest.approx(want)
+    stale = (nbytes, jcap, bench.NCU_TRAFFIC_KRYLOV[2], "0" * 64)
+    monkeypatch.setattr(bench, "NCU_TRAFFIC_KRYLOV", stale)
+    assert bench.krylov_traffic(n, iters, q.restart) is None
+
+
+def test_ncu_traffic_follows_the_source_hash(monkeypatch):
+    entry = bench.NCU_TRAFFIC[("schwarz", "fp32")]
+    assert bench.ncu_traffic("schwarz", "fp32") in (entry[0], None)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("schwarz", "fp32"), (entry[0], entry[1], "0" * 64))
+    assert bench.ncu_traffic("schwarz", "fp32") is None
+    assert bench.ncu_traffic("no such phase", "fp32") is None
