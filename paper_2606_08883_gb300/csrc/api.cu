@@ -16,7 +16,13 @@ using namespace mrcm;
 
 namespace mrcm {
 static std::atomic<long long> g_launches{0};
-void count_launch(int kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+// this thread's launches: a phase counts only the kernels its own thread launched, although request
+// workers launch from several threads at once
+static thread_local long long t_launches = 0;
+void count_launch(int kernels) {
+  g_launches.fetch_add(kernels, std::memory_order_relaxed);
+  t_launches += kernels;
+}
 }  // namespace mrcm
 
 static thread_local std::string g_last_error;
@@ -41,7 +47,7 @@ struct Phase {
   cudaStream_t st;
   long long l0;
   long long slot = -1;  // this phase's event pair (reserved at construction, so phases may nest)
-  Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(g_launches.load()) {
+  Phase(mrcm_handle h_, int ph_, cudaStream_t st_) : h(h_), ph(ph_), st(st_), l0(t_launches) {
     nvtxRangePushA(kPhaseName[ph]);
     if (!h->prof || !((h->prof_mask >> ph) & 1u)) return;
     if (h->ph_seen[ph]++ % h->prof_every != 0) return;
@@ -63,7 +69,7 @@ struct Phase {
     nvtxRangePop();
     if (slot < 0) return;
     cudaEventRecord(h->ev_pool[2 * slot + 1], st);
-    h->ph_launch[ph] += g_launches.load() - l0;
+    h->ph_launch[ph] += t_launches - l0;
   }
 };
 
